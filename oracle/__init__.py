@@ -1,0 +1,341 @@
+"""FP64 CPU oracle for the resonant-line Monte Carlo path (test infrastructure).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product (the CUDA library and its
+Python binding) never does, and it shares no code with the C source here
+(``rascas_oracle.c``), which restates the method of Michel-Dansac et al.
+(2020) step by step in double precision.
+
+The wrapper marshals a ``synth.Workload`` into the oracle's own C struct and
+runs packet ranges, optionally on several host threads (ctypes releases the
+GIL for the duration of each C call; each thread has its own tallies, summed
+afterwards in a fixed order, so the result does not depend on the thread
+count up to floating-point summation order of whole-chunk tallies).
+
+Parity status of each function (pins live in tests/test_oracle_*.py):
+  ora_philox4x32_10 .... pinned (published known-answer vectors)
+  ora_voigt ............ pinned (quadrature of the H(a,x) integral, limits)
+  ora_u0/u_par sampler . pinned (chi-square against the normalised density)
+  ora_mu_sample ........ pinned (CDF inversion identities, chi-square, <mu>=g)
+  ora_onb .............. pinned (orthonormality)
+  walk / ray_tau ....... pinned (brute-force leaf lookup, closed-form tau)
+  ora_run / ora_event .. pinned (MFP, conservation, symmetry, pure absorber,
+                         error budget, Neufeld / Dijkstra spectra, Harrington)
+  peeling .............. pinned (4 pi * peeled flux = escape fraction, symmetry)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rascas_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "librascas_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+C_CGS = 2.99792458e10  # oracle-side copy, used only to build frequencies from wavelengths
+
+MAXLINE, MAXCHAN, MAXDIR = 4, 4, 8
+ACTIVE, ESCAPED, ABSORBED, CAPPED, ERROR = 0, 1, 2, 3, 4
+
+
+def build(force=False):
+    """Compile the oracle with gcc (no FP contraction, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class Cfg(C.Structure):
+    _fields_ = [
+        ("son", C.c_void_p), ("n_HI", C.c_void_p), ("vx", C.c_void_p), ("vy", C.c_void_p),
+        ("vz", C.c_void_p), ("T", C.c_void_p), ("n_dust", C.c_void_p), ("n_metal", C.c_void_p),
+        ("noct", C.c_int64), ("nleaf", C.c_int64), ("box_cm", C.c_double),
+        ("dom_kind", C.c_int64), ("dom_c", C.c_double * 3), ("dom_size", C.c_double),
+        ("nline", C.c_int64),
+        ("line_nu", C.c_double * MAXLINE), ("line_A", C.c_double * MAXLINE),
+        ("line_f", C.c_double * MAXLINE), ("line_m", C.c_double * MAXLINE),
+        ("line_abund", C.c_double * MAXLINE),
+        ("line_dens", C.c_int64 * MAXLINE), ("line_phase", C.c_int64 * MAXLINE),
+        ("line_nchan", C.c_int64 * MAXLINE),
+        ("chan_A", (C.c_double * MAXCHAN) * MAXLINE), ("chan_nu", (C.c_double * MAXCHAN) * MAXLINE),
+        ("dust_sigma", C.c_double), ("dust_albedo", C.c_double), ("dust_g", C.c_double),
+        ("recoil", C.c_int64), ("isotropic", C.c_int64), ("keep_dir", C.c_int64),
+        ("max_scatt", C.c_int64), ("max_steps", C.c_int64),
+        ("x_gauss", C.c_double), ("tau_stop", C.c_double), ("seed", C.c_uint64),
+        ("nu_lo", C.c_double), ("nu_hi", C.c_double),
+        ("nbin", C.c_int64), ("ndir", C.c_int64), ("npix", C.c_int64), ("cube", C.c_int64),
+        ("dirs", (C.c_double * 3) * MAXDIR), ("fov", C.c_double), ("img_c", C.c_double * 3),
+    ]
+
+
+class State(C.Structure):
+    _fields_ = [
+        ("p", C.c_double * 3), ("k", C.c_double * 3), ("nu", C.c_double),
+        ("leaf", C.c_int64), ("level", C.c_int64), ("ijk", C.c_int64 * 3),
+        ("pid", C.c_uint64), ("ndraw", C.c_uint64),
+        ("nscatt", C.c_int64), ("nsteps", C.c_int64), ("status", C.c_int64),
+        ("path", C.c_double),
+    ]
+
+
+class Tally(C.Structure):
+    _fields_ = [
+        ("spec", C.c_void_p), ("pspec", C.c_void_p), ("pimg", C.c_void_p), ("pcube", C.c_void_p),
+        ("ncross", C.c_int64), ("nscatt_line", C.c_int64), ("nscatt_dust", C.c_int64),
+        ("npeel", C.c_int64),
+    ]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            dp, i64, u64 = C.POINTER(C.c_double), C.c_int64, C.c_uint64
+            L.ora_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
+            L.ora_word.restype = C.c_uint32
+            L.ora_word.argtypes = [u64, u64, u64]
+            L.ora_voigt.restype = C.c_double
+            L.ora_voigt.argtypes = [C.c_double, C.c_double]
+            L.ora_u0.restype = C.c_double
+            L.ora_u0.argtypes = [C.c_double, C.c_double]
+            L.ora_mu_sample.restype = C.c_double
+            L.ora_mu_sample.argtypes = [C.c_int, C.c_double, C.c_double]
+            L.ora_phase.restype = C.c_double
+            L.ora_phase.argtypes = [C.c_int, C.c_double, C.c_double]
+            L.ora_onb.argtypes = [dp, dp, dp]
+            L.ora_sample_upar_n.argtypes = [C.POINTER(Cfg), u64, C.c_double, C.c_double, i64, dp]
+            L.ora_locate.restype = i64
+            L.ora_locate.argtypes = [C.POINTER(Cfg), dp, dp, C.POINTER(i64), C.POINTER(i64)]
+            L.ora_opacity.restype = C.c_double
+            L.ora_opacity.argtypes = [C.POINTER(Cfg), i64, C.c_double, dp]
+            L.ora_ray_tau.restype = C.c_double
+            L.ora_ray_tau.argtypes = [C.POINTER(Cfg), dp, dp, C.c_double, C.c_double,
+                                      C.POINTER(i64), dp, i64, C.POINTER(i64)]
+            L.ora_init_state.restype = C.c_int
+            L.ora_init_state.argtypes = [C.POINTER(Cfg), C.POINTER(State), dp, dp, C.c_double, u64]
+            L.ora_event.restype = C.c_int
+            L.ora_event.argtypes = [C.POINTER(Cfg), C.POINTER(State), C.POINTER(Tally)]
+            L.ora_run.restype = C.c_int
+            L.ora_run.argtypes = [C.POINTER(Cfg), i64, dp, dp, dp, C.POINTER(u64),
+                                  C.POINTER(C.c_int32), C.POINTER(i64), dp, dp, dp, dp, C.POINTER(Tally)]
+            for f in ("ora_sizeof_cfg", "ora_sizeof_state", "ora_sizeof_tally"):
+                getattr(L, f).restype = i64
+            assert L.ora_sizeof_cfg() == C.sizeof(Cfg)
+            assert L.ora_sizeof_state() == C.sizeof(State)
+            assert L.ora_sizeof_tally() == C.sizeof(Tally)
+            _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+class Oracle:
+    """A workload marshalled into the oracle's configuration."""
+
+    def __init__(self, wl):
+        self.wl = wl
+        m = wl.medium
+        self._keep = {
+            "son": np.ascontiguousarray(m.tree.son, dtype=np.int32),
+            "n_HI": _f32(m.n_HI), "vx": _f32(m.vx), "vy": _f32(m.vy), "vz": _f32(m.vz),
+            "T": _f32(m.T), "n_dust": _f32(m.n_dust), "n_metal": _f32(m.n_metal),
+        }
+        cf = Cfg()
+        for k, v in self._keep.items():
+            setattr(cf, k, v.ctypes.data)
+        cf.noct, cf.nleaf, cf.box_cm = m.tree.noct, m.tree.nleaf, m.box_cm
+        d = wl.domain
+        cf.dom_kind = d.kind
+        cf.dom_c[:] = list(d.centre)
+        cf.dom_size = d.size
+        assert len(wl.lines) <= MAXLINE
+        cf.nline = len(wl.lines)
+        for i, ln in enumerate(wl.lines):
+            cf.line_nu[i] = C_CGS / (ln.lambda_A * 1e-8)
+            cf.line_A[i], cf.line_f[i], cf.line_m[i] = ln.A_ul, ln.f_lu, ln.mass_g
+            cf.line_abund[i] = ln.abundance
+            cf.line_dens[i] = 1 if ln.density == 1 else 0
+            cf.line_phase[i] = ln.phase
+            chans = ln.all_channels()
+            assert len(chans) <= MAXCHAN
+            cf.line_nchan[i] = len(chans)
+            for c, (A, lam) in enumerate(chans):
+                cf.chan_A[i][c] = A
+                cf.chan_nu[i][c] = C_CGS / (lam * 1e-8)
+        cf.dust_sigma, cf.dust_albedo, cf.dust_g = wl.dust.sigma, wl.dust.albedo, wl.dust.g
+        ph = wl.physics
+        cf.recoil, cf.isotropic, cf.keep_dir = ph.recoil, ph.isotropic, ph.keep_direction
+        cf.max_scatt, cf.max_steps = ph.max_scatt, ph.max_steps
+        cf.x_gauss, cf.tau_stop, cf.seed = ph.x_gauss, ph.tau_stop, ph.seed
+        det = wl.detector
+        cf.nu_lo, cf.nu_hi, cf.nbin = det.nu_lo, det.nu_hi, det.nbin
+        dirs = np.asarray(det.dirs, dtype=np.float64).reshape(-1, 3)
+        assert dirs.shape[0] <= MAXDIR
+        cf.ndir = dirs.shape[0]
+        for i in range(dirs.shape[0]):
+            v = dirs[i] / np.linalg.norm(dirs[i])
+            cf.dirs[i][:] = list(v)
+        cf.npix, cf.fov, cf.cube = det.npix, det.fov, det.cube
+        cf.img_c[:] = list(det.centre)
+        self.cfg = cf
+
+    # -------------------------------------------------------------- runs
+    def _alloc_tally(self):
+        c = self.cfg
+        t = {"spec": np.zeros(c.nbin)}
+        t["pspec"] = np.zeros(max(1, c.ndir * c.nbin))
+        t["pimg"] = np.zeros(max(1, c.ndir * c.npix * c.npix))
+        t["pcube"] = np.zeros(max(1, c.ndir * c.npix * c.npix * c.nbin)) if c.cube else None
+        ty = Tally()
+        ty.spec, ty.pspec, ty.pimg = t["spec"].ctypes.data, t["pspec"].ctypes.data, t["pimg"].ctypes.data
+        ty.pcube = t["pcube"].ctypes.data if t["pcube"] is not None else None
+        return ty, t
+
+    def _run_range(self, pk, lo, hi):
+        n = hi - lo
+        pos = np.ascontiguousarray(pk.pos[lo:hi], dtype=np.float64)
+        dr = np.ascontiguousarray(pk.dir[lo:hi], dtype=np.float64)
+        nu = np.ascontiguousarray(pk.nu[lo:hi], dtype=np.float64)
+        ids = np.ascontiguousarray(pk.ids[lo:hi], dtype=np.uint64)
+        out = {"status": np.zeros(n, np.int32), "nscatt": np.zeros(n, np.int64),
+               "nu": np.zeros(n), "pos": np.zeros((n, 3)), "dir": np.zeros((n, 3)), "path": np.zeros(n)}
+        ty, t = self._alloc_tally()
+        lib().ora_run(C.byref(self.cfg), n, _dp(pos), _dp(dr), _dp(nu),
+                      ids.ctypes.data_as(C.POINTER(C.c_uint64)),
+                      out["status"].ctypes.data_as(C.POINTER(C.c_int32)),
+                      out["nscatt"].ctypes.data_as(C.POINTER(C.c_int64)),
+                      _dp(out["nu"]), _dp(out["pos"]), _dp(out["dir"]), _dp(out["path"]), C.byref(ty))
+        t["ncross"], t["nscatt_line"], t["nscatt_dust"], t["npeel"] = (
+            ty.ncross, ty.nscatt_line, ty.nscatt_dust, ty.npeel)
+        return out, t
+
+    def run(self, packets=None, lo=0, hi=None, threads=1, chunk=None):
+        """Propagate packets [lo, hi) of the workload (or of ``packets``)."""
+        pk = packets if packets is not None else self.wl.packets
+        hi = pk.n if hi is None else hi
+        if threads <= 1:
+            parts = [self._run_range(pk, lo, hi)]
+        else:
+            chunk = chunk or max(1, (hi - lo + threads * 4 - 1) // (threads * 4))
+            bounds = [(a, min(hi, a + chunk)) for a in range(lo, hi, chunk)]
+            with ThreadPoolExecutor(threads) as ex:
+                parts = list(ex.map(lambda b: self._run_range(pk, *b), bounds))
+        out = {k: np.concatenate([p[0][k] for p in parts]) for k in parts[0][0]}
+        tal = {}
+        for k in parts[0][1]:
+            if parts[0][1][k] is None:
+                tal[k] = None
+            elif isinstance(parts[0][1][k], np.ndarray):
+                tal[k] = sum(p[1][k] for p in parts)
+            else:
+                tal[k] = sum(p[1][k] for p in parts)
+        c = self.cfg
+        if c.ndir:
+            tal["pspec"] = tal["pspec"].reshape(c.ndir, c.nbin)
+            tal["pimg"] = tal["pimg"].reshape(c.ndir, c.npix, c.npix) if c.npix else None
+            if tal["pcube"] is not None:
+                tal["pcube"] = tal["pcube"].reshape(c.ndir, c.npix, c.npix, c.nbin)
+        return out, tal
+
+    # -------------------------------------------------------------- pieces
+    def locate(self, p, k=(1.0, 1.0, 1.0)):
+        """Leaf entered at p moving along k (the cell containing p + eps k)."""
+        p = np.ascontiguousarray(p, dtype=np.float64)
+        k = np.ascontiguousarray(k, dtype=np.float64)
+        lv = C.c_int64()
+        ijk = (C.c_int64 * 3)()
+        leaf = lib().ora_locate(C.byref(self.cfg), _dp(p), _dp(k), C.byref(lv), ijk)
+        return leaf, lv.value, tuple(ijk)
+
+    def opacity(self, leaf, nu_ext, k):
+        k = np.ascontiguousarray(k, dtype=np.float64)
+        return lib().ora_opacity(C.byref(self.cfg), int(leaf), float(nu_ext), _dp(k))
+
+    def ray_tau(self, p, k, nu_ext, tau_stop=math.inf, cap=0):
+        p = np.ascontiguousarray(p, dtype=np.float64)
+        k = np.ascontiguousarray(k, dtype=np.float64)
+        cells = np.zeros(max(cap, 1), np.int64)
+        lens = np.zeros(max(cap, 1))
+        nc = C.c_int64()
+        tau = lib().ora_ray_tau(C.byref(self.cfg), _dp(p), _dp(k), float(nu_ext), float(tau_stop),
+                                cells.ctypes.data_as(C.POINTER(C.c_int64)) if cap else None,
+                                _dp(lens) if cap else None, cap, C.byref(nc))
+        n = min(nc.value, cap)
+        return tau, cells[:n], lens[:n], nc.value
+
+    def upar_samples(self, x, a, n, pid=0):
+        out = np.zeros(n)
+        lib().ora_sample_upar_n(C.byref(self.cfg), pid, float(x), float(a), n, _dp(out))
+        return out
+
+    def new_state(self, p, k, nu, pid):
+        s = State()
+        p = np.ascontiguousarray(p, dtype=np.float64)
+        k = np.ascontiguousarray(k, dtype=np.float64)
+        lib().ora_init_state(C.byref(self.cfg), C.byref(s), _dp(p), _dp(k), float(nu), int(pid))
+        return s
+
+    def event(self, s):
+        ty, t = self._alloc_tally()
+        r = lib().ora_event(C.byref(self.cfg), C.byref(s), C.byref(ty))
+        return r, t
+
+
+# ---------------------------------------------------------------- helpers
+def philox4x32_10(ctr, key):
+    c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (C.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (C.c_uint32 * 4)()
+    lib().ora_philox4x32_10(c, k, o)
+    return [o[i] for i in range(4)]
+
+
+def word(seed, pid, n):
+    return lib().ora_word(seed, pid, n)
+
+
+def voigt(a, x):
+    return lib().ora_voigt(float(a), float(x))
+
+
+def u0(x, a):
+    return lib().ora_u0(float(x), float(a))
+
+
+def mu_sample(kind, r, g=0.0):
+    return lib().ora_mu_sample(int(kind), float(r), float(g))
+
+
+def phase(kind, mu, g=0.0):
+    return lib().ora_phase(int(kind), float(mu), float(g))
+
+
+def onb(n):
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    b1, b2 = np.zeros(3), np.zeros(3)
+    lib().ora_onb(_dp(n), _dp(b1), _dp(b2))
+    return b1, b2
+
+
+PH_ISO, PH_CORE, PH_WING, PH_HG = 0, 1, 2, 3

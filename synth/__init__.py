@@ -1,0 +1,444 @@
+"""Seeded synthetic inputs for the resonant-line Monte Carlo transfer path.
+
+This package only *generates inputs*: graded octrees, per-leaf gas fields,
+photon-packet initial conditions (the "PPIC" lists of the paper, Sect. 2:
+ID, position, direction, frequency) and the atomic data of Table 1.  It holds
+none of the transfer method's arithmetic (no opacities, no Voigt function,
+no scattering, no walk).  Both the CUDA path and the FP64 oracle consume what
+it returns, so neither depends on the other.
+
+The one place where a physical formula appears is the *recipe* that turns a
+stated line-centre optical depth into a density (``density_for_tau0``): a
+workload is specified by its optical depth, and converting that number into
+the n_HI value written into the leaf arrays is part of defining the input.
+It uses its own copy of the CODATA constants.
+
+Geometry conventions (shared by every consumer):
+  * the simulation box is the unit cube [0,1)^3 in box units, of physical
+    size ``box_cm``;
+  * oct 0 is the root oct at level 1 (its 8 cells have size 1/2);
+  * ``son[8*oct + child]`` with ``child = (ix&1) | (iy&1)<<1 | (iz&1)<<2``
+    (ix,iy,iz the integer coordinates of the cell at its level) holds either
+    the index (>0) of the oct that refines the cell, or ``-(leaf+1)`` for a
+    leaf cell (Sect. 4.3, Fig. "amr_struct": positive son = oct, negative
+    son = leaf index into the physical-property arrays);
+  * octs and leaves are numbered depth-first (Sect. 4.3).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# --------------------------------------------------------------------------
+# CODATA 2018 constants, cgs (the paper prints none).  Used only by the input
+# recipe below (density from a stated optical depth, line frequencies).
+# --------------------------------------------------------------------------
+C_CGS = 2.99792458e10
+KB_CGS = 1.380649e-16
+H_CGS = 6.62607015e-27
+ME_CGS = 9.1093837015e-28
+E_ESU = 4.803204712570263e-10
+MP_CGS = 1.67262192369e-24
+AMU_CGS = 1.66053906660e-24
+KPC_CM = 3.0856775814913673e21
+
+# --------------------------------------------------------------------------
+# Table 1 (Appendix A): atomic data.  Wavelengths are vacuum, in Angstrom.
+# Each absorption line lists its decay channels; channel 0 is the resonant
+# one (same lower level), the others are fluorescent (Sect. 3.2.3).
+# --------------------------------------------------------------------------
+
+
+@dataclass
+class Line:
+    name: str
+    lambda_A: float        # absorption line wavelength (Angstrom)
+    A_ul: float            # Einstein A of the resonant channel (s^-1)
+    f_lu: float            # oscillator strength
+    mass_g: float          # scatterer mass (g)
+    density: int = 0       # 0: n_HI field, 1: n_metal field, 2: n_HI * abundance
+    abundance: float = 1.0  # multiplies the density field (deuterium: D/H)
+    phase: int = 0         # 0: Lya core/wing (Eqs. Pcore/Pwing), 1: isotropic
+    channels: list = field(default_factory=list)  # [(A_ul_i, lambda_i_A)], [0] resonant
+
+    def all_channels(self):
+        return [(self.A_ul, self.lambda_A)] + list(self.channels)
+
+
+def lya():
+    """H I Lyman-alpha, Table 1 row 1 (1215.67 A, A=6.265e8, f=0.416)."""
+    return Line("HI_1216", 1215.67, 6.265e8, 0.416, MP_CGS, density=0, phase=0)
+
+
+def d_lya(d_over_h=3.0e-5):
+    """D Lyman-alpha, Table 1 row 2 (1215.34 A), density n_HI * D/H."""
+    return Line("DI_1215", 1215.34, 6.265e8, 0.416, 2.01410177812 * AMU_CGS,
+                density=2, abundance=d_over_h, phase=0)
+
+
+def siII_1190():
+    """Si II 1190.42 A (A=6.53e8, f=0.277) with fluorescent 1194.50* (A=3.45e9)."""
+    return Line("SiII_1190", 1190.42, 6.53e8, 0.277, 28.0855 * AMU_CGS,
+                density=1, phase=1, channels=[(3.45e9, 1194.50)])
+
+
+def siII_1193():
+    """Si II 1193.28 A (A=2.69e9, f=0.575) with fluorescent 1197.39* (A=1.40e9)."""
+    return Line("SiII_1193", 1193.28, 2.69e9, 0.575, 28.0855 * AMU_CGS,
+                density=1, phase=1, channels=[(1.40e9, 1197.39)])
+
+
+def nu_of(lambda_A):
+    return C_CGS / (lambda_A * 1e-8)
+
+
+def doppler_width(line: Line, T):
+    return nu_of(line.lambda_A) * math.sqrt(2.0 * KB_CGS * T / line.mass_g) / C_CGS
+
+
+def density_for_tau0(line: Line, T, tau0, length_cm):
+    """Recipe: n such that n * sigma0 * length = tau0, with sigma0 the
+    line-centre cross section of Eq. (sigma) taken with H -> 1."""
+    dnu = doppler_width(line, T)
+    sigma0 = math.sqrt(math.pi) * E_ESU ** 2 * line.f_lu / (ME_CGS * C_CGS * dnu)
+    return tau0 / (sigma0 * length_cm)
+
+
+# --------------------------------------------------------------------------
+# Graded octree builder
+# --------------------------------------------------------------------------
+
+
+def _part1by2(v):
+    v = v.astype(np.uint64) & np.uint64(0x1FFFFF)
+    v = (v | (v << np.uint64(32))) & np.uint64(0x1F00000000FFFF)
+    v = (v | (v << np.uint64(16))) & np.uint64(0x1F0000FF0000FF)
+    v = (v | (v << np.uint64(8))) & np.uint64(0x100F00F00F00F00F)
+    v = (v | (v << np.uint64(4))) & np.uint64(0x10C30C30C30C30C3)
+    v = (v | (v << np.uint64(2))) & np.uint64(0x1249249249249249)
+    return v
+
+
+def morton(ix, iy, iz):
+    return _part1by2(ix) | (_part1by2(iy) << np.uint64(1)) | (_part1by2(iz) << np.uint64(2))
+
+
+_CHILD = np.array([[c & 1, (c >> 1) & 1, (c >> 2) & 1] for c in range(8)], dtype=np.int64)
+
+
+@dataclass
+class Octree:
+    son: np.ndarray          # int32 [8*noct]
+    oct_level: np.ndarray    # int32 [noct]
+    oct_origin: np.ndarray   # int64 [noct,3] integer coords of child 0 at the oct's level
+    leaf_level: np.ndarray   # int32 [nleaf]
+    leaf_ijk: np.ndarray     # int64 [nleaf,3] integer coords at the leaf's level
+    max_level: int
+
+    @property
+    def noct(self):
+        return int(self.oct_level.size)
+
+    @property
+    def nleaf(self):
+        return int(self.leaf_level.size)
+
+    def leaf_centres(self):
+        h = np.ldexp(1.0, -self.leaf_level.astype(np.int64))
+        return (self.leaf_ijk.astype(np.float64) + 0.5) * h[:, None]
+
+    def leaf_size(self):
+        return np.ldexp(1.0, -self.leaf_level.astype(np.int64))
+
+
+def build_octree(refine, max_level):
+    """Build a depth-first-numbered octree.
+
+    ``refine(level, i, j, k)`` gets int64 arrays of integer cell coordinates at
+    ``level`` and returns a bool array: which of those cells are split.  Cells
+    at ``max_level`` are never split.
+    """
+    levels, origins = [], []
+    cur = np.zeros((1, 3), dtype=np.int64)  # octs at level 1
+    lvl = 1
+    cell_ref = []  # per level: bool [noct_l*8]
+    while True:
+        levels.append(np.full(cur.shape[0], lvl, dtype=np.int32))
+        origins.append(cur)
+        cells = (cur[:, None, :] + _CHILD[None, :, :]).reshape(-1, 3)
+        if lvl < max_level:
+            r = np.asarray(refine(lvl, cells[:, 0], cells[:, 1], cells[:, 2]), dtype=bool)
+        else:
+            r = np.zeros(cells.shape[0], dtype=bool)
+        cell_ref.append(r)
+        if not r.any():
+            break
+        cur = 2 * cells[r]
+        lvl += 1
+    oct_level = np.concatenate(levels)
+    oct_origin = np.concatenate(origins)
+    refined = np.concatenate(cell_ref)
+    noct = oct_level.size
+    # BFS numbering: octs of level l+1 are created in the order of refined cells.
+    son_bfs = np.empty(8 * noct, dtype=np.int64)
+    child_oct_bfs = np.arange(1, noct, dtype=np.int64)
+    son_bfs[refined] = child_oct_bfs
+    cell_level = np.repeat(oct_level, 8)
+    cell_ijk = (oct_origin[:, None, :] + _CHILD[None, :, :]).reshape(-1, 3)
+    leaf_mask = ~refined
+    leaf_lvl = cell_level[leaf_mask]
+    leaf_ijk = cell_ijk[leaf_mask]
+    # depth-first order == Morton order at the finest level (ties: coarser first)
+    Lm = int(oct_level.max())
+    okey = morton(*(oct_origin << (Lm - oct_level.astype(np.int64))[:, None]).T)
+    oorder = np.lexsort((oct_level, okey))
+    onew = np.empty(noct, dtype=np.int64)
+    onew[oorder] = np.arange(noct)
+    lkey = morton(*(leaf_ijk << (Lm - leaf_lvl.astype(np.int64))[:, None]).T)
+    lorder = np.argsort(lkey, kind="stable")
+    lnew = np.empty(leaf_lvl.size, dtype=np.int64)
+    lnew[lorder] = np.arange(leaf_lvl.size)
+    leaf_bfs_index = np.full(8 * noct, -1, dtype=np.int64)
+    leaf_bfs_index[leaf_mask] = np.arange(leaf_lvl.size)
+    son_new_val = np.where(refined, onew[np.where(refined, son_bfs, 0)],
+                           -(lnew[np.maximum(leaf_bfs_index, 0)] + 1))
+    son = np.empty(8 * noct, dtype=np.int32)
+    cell_oct_new = np.repeat(onew, 8) * 8 + np.tile(np.arange(8), noct)
+    son[cell_oct_new] = son_new_val
+    assert np.all(son[1:8 * noct] != 0)
+    return Octree(son=son,
+                  oct_level=oct_level[oorder].astype(np.int32),
+                  oct_origin=oct_origin[oorder],
+                  leaf_level=leaf_lvl[lorder].astype(np.int32),
+                  leaf_ijk=leaf_ijk[lorder],
+                  max_level=Lm)
+
+
+def uniform_octree(level):
+    """Regular (2^level)^3 grid of leaves."""
+    return build_octree(lambda l, i, j, k: np.full(i.shape, l < level), level)
+
+
+def sphere_octree(base_level, max_level, centre=(0.5, 0.5, 0.5), radius=0.45, grade=2.0):
+    """All cells up to ``base_level``; beyond it, a cell at level l is split
+    while it lies within ``grade`` cell sizes of the ball.  With grade >=
+    sqrt(3)+... >= 2 neighbouring leaves differ by at most one level."""
+    c = np.asarray(centre, dtype=np.float64)
+
+    def refine(l, i, j, k):
+        h = math.ldexp(1.0, -l)
+        lo = np.stack([i, j, k], 1) * h
+        d = np.clip(c[None, :], lo, lo + h) - c[None, :]
+        dist = np.sqrt((d * d).sum(1)) - radius
+        return (l < base_level) | (dist < grade * h)
+
+    return build_octree(refine, max_level)
+
+
+def check_graded(tree: Octree):
+    """True if face-neighbouring leaves differ by at most one level."""
+    Lm = tree.max_level
+    lut = {}
+    for lv, (i, j, k), idx in zip(tree.leaf_level, tree.leaf_ijk, range(tree.nleaf)):
+        lut[(int(lv), int(i), int(j), int(k))] = idx
+    n = 1 << Lm
+    for lv, (i, j, k) in zip(tree.leaf_level, tree.leaf_ijk):
+        s = 1 << (Lm - lv)
+        for ax in range(3):
+            for sgn in (-1, 1):
+                p = [i * s, j * s, k * s]
+                p[ax] = p[ax] + (s if sgn > 0 else -1)
+                if p[ax] < 0 or p[ax] >= n:
+                    continue
+                # leaf containing the fine point p
+                found = None
+                for l2 in range(1, Lm + 1):
+                    key = (l2, p[0] >> (Lm - l2), p[1] >> (Lm - l2), p[2] >> (Lm - l2))
+                    if key in lut:
+                        found = l2
+                        break
+                if found is None or abs(found - int(lv)) > 1:
+                    return False
+    return True
+
+
+# --------------------------------------------------------------------------
+# Gas fields and workloads
+# --------------------------------------------------------------------------
+
+
+@dataclass
+class Medium:
+    tree: Octree
+    box_cm: float
+    n_HI: np.ndarray
+    vx: np.ndarray
+    vy: np.ndarray
+    vz: np.ndarray
+    T: np.ndarray
+    n_dust: np.ndarray
+    n_metal: np.ndarray
+
+
+def uniform_medium(tree, box_cm, n_HI, T, n_dust=0.0, n_metal=0.0):
+    n = tree.nleaf
+    f = lambda v: np.full(n, v, dtype=np.float32)
+    return Medium(tree, float(box_cm), f(n_HI), f(0.0), f(0.0), f(0.0), f(T), f(n_dust), f(n_metal))
+
+
+@dataclass
+class Domain:
+    kind: int            # 0 sphere, 1 slab (periodic x,y), 2 cube
+    centre: tuple = (0.5, 0.5, 0.5)
+    size: float = 0.45   # sphere radius / slab half-thickness / cube half-size (box units)
+
+
+@dataclass
+class Dust:
+    sigma: float = 0.0   # cross section per unit n_dust (cm^2), constant across the line
+    albedo: float = 0.32  # Sect. 3.2.2 default
+    g: float = 0.73       # Henyey-Greenstein asymmetry, Sect. 3.2.2 default
+
+
+@dataclass
+class Physics:
+    recoil: int = 1
+    isotropic: int = 0         # 1: isotropic phase function for every line (test mode)
+    keep_direction: int = 0    # 1: scatterings keep k (error-budget test, Sect. 4.5)
+    x_gauss: float = 8.0       # u_par Gaussian branch threshold (Sect. 3.3.3 default)
+    max_scatt: int = 0         # 0: no cap
+    max_steps: int = 0         # 0: no cap
+    tau_stop: float = 50.0     # peeling rays stop once tau exceeds this (contribution < e^-tau_stop)
+    seed: int = 0
+
+
+@dataclass
+class Detector:
+    """Frequency axis (external frame, Hz) shared by the escape spectrum and
+    the peeled spectra/cubes, plus peeling directions and the image plane."""
+    nu_lo: float
+    nu_hi: float
+    nbin: int
+    dirs: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
+    npix: int = 0
+    fov: float = 1.0                   # image side (box units)
+    centre: tuple = (0.5, 0.5, 0.5)     # image centre (box units)
+    cube: int = 0                      # 1: accumulate spectral cubes
+
+
+@dataclass
+class Packets:
+    pos: np.ndarray   # float64 [n,3] box units
+    dir: np.ndarray   # float64 [n,3] unit vectors
+    nu: np.ndarray    # float64 [n] external-frame frequency (Hz) along dir
+    ids: np.ndarray   # uint64 [n]
+
+    @property
+    def n(self):
+        return int(self.nu.size)
+
+
+def point_source(n, pos, nu, seed, first_id=0):
+    """n packets at ``pos`` with isotropic directions (Sect. 2: isotropic
+    sources) and frequency ``nu``; directions from numpy's PCG64 stream."""
+    rng = np.random.default_rng(seed)
+    mu = 2.0 * rng.random(n) - 1.0
+    phi = 2.0 * math.pi * rng.random(n)
+    s = np.sqrt(np.maximum(0.0, 1.0 - mu * mu))
+    d = np.stack([s * np.cos(phi), s * np.sin(phi), mu], 1)
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    p = np.tile(np.asarray(pos, dtype=np.float64), (n, 1))
+    return Packets(p, d, np.full(n, float(nu)), np.arange(first_id, first_id + n, dtype=np.uint64))
+
+
+@dataclass
+class Workload:
+    name: str
+    medium: Medium
+    domain: Domain
+    lines: list
+    dust: Dust
+    physics: Physics
+    detector: Detector
+    packets: Packets
+
+
+RUN_SEED = 2001_11252
+
+
+def x_axis(line: Line, T, xlo, xhi, nbin):
+    """Detector frequency axis from a range in Doppler units x of ``line`` at T
+    (x = (nu - nu0)/Delta nu_D, Sect. 3.1.1)."""
+    nu0, dnu = nu_of(line.lambda_A), doppler_width(line, T)
+    return nu0 + xlo * dnu, nu0 + xhi * dnu, nbin
+
+
+def slab(tau0=1e4, T=1e4, n_packets=2000, level=4, recoil=0, isotropic=1, seed_offset=0):
+    """Static homogeneous H I slab (Sect. 3.4.2): (2^level)^3 grid, slab
+    domain |z-1/2| <= 1/2 with periodic x,y, half-thickness line-centre
+    optical depth tau0, T, no dust, zero velocity; packets at the mid-plane
+    at x_in = 0, isotropic."""
+    tree = uniform_octree(level)
+    L = 1.0 * KPC_CM
+    line = lya()
+    n = density_for_tau0(line, T, tau0, 0.5 * L)
+    med = uniform_medium(tree, L, n, T)
+    seed = RUN_SEED + 0 + seed_offset
+    pk = point_source(n_packets, (0.5, 0.5, 0.5), nu_of(line.lambda_A), seed ^ 0xA5A5)
+    lo, hi, nb = x_axis(line, T, -60.0, 60.0, 200)
+    return Workload("slab", med, Domain(1, (0.5, 0.5, 0.5), 0.5), [line], Dust(),
+                    Physics(recoil=recoil, isotropic=isotropic, seed=seed), Detector(lo, hi, nb), pk)
+
+
+def sphere(tau0=1e6, T=1e4, tau_dust=0.0, n_packets=1_000_000, base=3, max_level=6,
+           recoil=0, isotropic=0, seed_offset=0, xrange=60.0):
+    """Static homogeneous sphere, H I + dust (Sect. 3.4.2): 8^3 root refined to
+    64^3 equivalent inside the sphere (centre 1/2, R=0.45 box), centre-to-edge
+    line-centre optical depth tau0, dust albedo 0.32, centre-to-edge dust
+    optical depth tau_dust; packets at the centre at x_in = 0."""
+    tree = sphere_octree(base, max_level)
+    L = 1.0 * KPC_CM
+    R = 0.45
+    line = lya()
+    n = density_for_tau0(line, T, tau0, R * L)
+    dust = Dust(sigma=4.0e-22)
+    nd = tau_dust / (dust.sigma * R * L)
+    med = uniform_medium(tree, L, n, T, n_dust=nd)
+    seed = RUN_SEED + 1 + seed_offset
+    pk = point_source(n_packets, (0.5, 0.5, 0.5), nu_of(line.lambda_A), seed ^ 0xA5A5)
+    lo, hi, nb = x_axis(line, T, -xrange, xrange, 200)
+    return Workload("sphere", med, Domain(0, (0.5, 0.5, 0.5), R), [line], dust,
+                    Physics(recoil=recoil, isotropic=isotropic, seed=seed), Detector(lo, hi, nb), pk)
+
+
+PEEL_DIRS_3 = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0],
+                        [1.0 / math.sqrt(3.0)] * 3])
+
+
+def expanding_sphere(N_HI=1e20, T=1e4, v_max_kms=200.0, tau_dust=0.5, n_packets=1_000_000,
+                     base=3, max_level=6, npix=100, nchan=200, seed_offset=0):
+    """Expanding sphere with peeling: the sphere octree, centre-to-edge column
+    N_HI, radial velocity v_max * r/R at leaf centres, dust, core/wing phase
+    functions and recoil; 3 peeling directions into npix^2 x nchan cubes over
+    +-1000 km/s."""
+    tree = sphere_octree(base, max_level)
+    L = 1.0 * KPC_CM
+    R = 0.45
+    line = lya()
+    n = N_HI / (R * L)
+    dust = Dust(sigma=4.0e-22)
+    nd = tau_dust / (dust.sigma * R * L)
+    med = uniform_medium(tree, L, n, T, n_dust=nd)
+    ctr = tree.leaf_centres() - 0.5
+    v = (v_max_kms * 1e5 / R) * ctr
+    med.vx, med.vy, med.vz = (v[:, i].astype(np.float32) for i in range(3))
+    seed = RUN_SEED + 2 + seed_offset
+    nu0 = nu_of(line.lambda_A)
+    pk = point_source(n_packets, (0.5, 0.5, 0.5), nu0, seed ^ 0xA5A5)
+    vmax = 1000e5
+    det = Detector(nu0 * (1 - vmax / C_CGS), nu0 * (1 + vmax / C_CGS), nchan,
+                   dirs=PEEL_DIRS_3.copy(), npix=npix, fov=2 * R, centre=(0.5, 0.5, 0.5), cube=1)
+    return Workload("expanding", med, Domain(0, (0.5, 0.5, 0.5), R), [line], dust,
+                    Physics(recoil=1, isotropic=0, seed=seed), det, pk)
