@@ -1,0 +1,308 @@
+"""Benchmark of the resonant-line Monte Carlo hot path on GB300.
+
+Workload: the static homogeneous sphere (H I + dust) -- 8^3 root octree
+refined to 64^3 equivalent inside the sphere (R = 0.45 box), centre-to-edge
+line-centre optical depth tau0 = 1e6 at T = 1e4 K (a = 4.7e-4), dust albedo
+0.32, g = 0.73, centre-to-edge tau_dust = 1, packets emitted at the centre at
+line centre.  One step propagates one batch of packets (distinct packet ids
+every step) until each escapes or is absorbed, with the escape spectrum
+(200 bins over x in [-60, 60]) accumulated on the device.
+
+Metric: scatterings per second (and packets per second) on the GPU, the oracle
+(plain FP64 C, host cores) as the reference arm.  Multi-GPU: packet ids are
+sharded across ranks (weak scaling), no collective on the data path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--packets P] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "scatterings/sec & packets/sec on 1 GB300 vs oracle; batched vs plain speedup; HBM roofline %"
+WORKLOAD = ("static H I + dust sphere: 8^3 root refined to 64^3-equivalent octree (172992 leaves), "
+            "tau0=1e6 centre-to-edge, T=1e4 K, tau_dust=1, albedo 0.32, packets from the centre at x=0")
+# warp instructions executed per scattering by k_propagate on this workload,
+# from one ncu capture (smsp__inst_executed.sum / scatterings); see profiles/
+INST_PER_SCATT = None
+ISSUE_PEAK_NOTE = "152 SMs x 4 schedulers x 1 warp-instruction/clock x SM clock"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--packets", type=int, default=1 << 16)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload(n):
+    import synth
+    wl = synth.sphere(tau0=1e6, T=1e4, tau_dust=1.0, n_packets=n, recoil=0, isotropic=0)
+    return wl
+
+
+def packets(wl, first, n):
+    import synth
+    return synth.point_source(n, (0.5, 0.5, 0.5), wl.packets.nu[0], wl.physics.seed ^ 0xA5A5 ^ first, first_id=first)
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    def __init__(self, gpu=0):
+        self.samples = []
+        self.stop = threading.Event()
+        self.gpu = gpu
+        self.t = threading.Thread(target=self.run, daemon=True)
+
+    def run(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        while not self.stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + q,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                self.samples.append([s.strip() for s in out.split(",")])
+            except Exception:
+                pass
+            self.stop.wait(0.2)
+
+    def __enter__(self):
+        self.t.start()
+        return self
+
+    def __exit__(self, *a):
+        self.stop.set()
+        self.t.join(timeout=10)
+
+    def summary(self):
+        sm = [float(s[0]) for s in self.samples if len(s) >= 7 and s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if len(s) >= 7 and s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples if len(s) >= 7 for i in range(4)
+                          if s[3 + i].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------ reference arm
+def cpu_oracle_rate(wl_fn, seconds, threads):
+    """Oracle (as it stands) on a bounded sample of the workload: packets are
+    run in growing batches until about `seconds` of CPU work are done."""
+    import oracle
+    done_p = done_s = 0
+    t_tot = 0.0
+    n = max(threads, 8)
+    first = 10_000_000
+    while t_tot < seconds:
+        wl = wl_fn(n)
+        pk = packets(wl, first, n)
+        first += n
+        t0 = time.perf_counter()
+        out, tal = oracle.Oracle(wl).run(packets=pk, threads=threads, chunk=1)
+        dt = time.perf_counter() - t0
+        t_tot += dt
+        done_p += n
+        done_s += int(out["nscatt"].sum())
+        if dt < seconds / 4:
+            n *= 2
+    return done_s / t_tot, done_p / t_tot, done_p, t_tot
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    per_step = max(2.0, args.cpu_seconds / max(1, args.steps))
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_rate(workload, per_step if i >= args.warmup else 0.5, threads)
+        if i >= args.warmup:
+            rates.append(r)
+    sc = sum(r[0] * r[3] for r in rates) / sum(r[3] for r in rates)
+    pk = sum(r[2] for r in rates) / sum(r[3] for r in rates)
+    line = {"impl": "reference", "metric": METRIC, "value": sc, "unit": "scatterings/s",
+            "packets_per_s": pk, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(r[3] for r in rates) / len(rates), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "oracle on %d packets per step" % int(np.mean([r[2] for r in rates]))},
+            "cpu_baseline": {"value": sc, "unit": "scatterings/s", "cores": threads, "kind": "oracle",
+                             "sample": "%d packets of the workload per step, %d threads" % (int(np.mean([r[2] for r in rates])), threads)},
+            "e2e": {"value": sc, "unit": "scatterings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_2001_11252_gb300 as rg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    P = args.packets
+    wl = workload(8)
+    ctx = rg.Context(local)
+    ctx.setup(wl)
+    stream = torch.cuda.current_stream()
+    ctx.set_stream(stream)
+
+    def dev_packets(step):
+        first = (rank * (args.warmup + args.steps + 1) + step) * P
+        pk = packets(wl, first, P)
+        t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(dev, dt)
+        return pk, (t(pk.pos, torch.float64), t(pk.dir, torch.float64), t(pk.nu, torch.float64),
+                    t(pk.ids.view(np.int64), torch.int64))
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    inputs = [dev_packets(s) for s in range(args.warmup + args.steps)]
+    for s in range(args.warmup):
+        ctx.propagate(*inputs[s][1], stats=False)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    scatt = pk_done = 0
+    stats_all = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            e0, e1 = evs[i]
+            e0.record(stream)
+            st = ctx.propagate(*inputs[args.warmup + i][1], stats=False)
+            e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    # counts of the timed steps (re-read from a stats run of the same packets)
+    t_ms = sum(step_ms)
+    for i in range(args.steps):
+        st = ctx.propagate(*inputs[args.warmup + i][1], stats=True)
+        stats_all.append(st)
+    scatt = sum(s["nscatt_line"] + s["nscatt_dust"] for s in stats_all)
+    pk_done = sum(s["packets"] for s in stats_all)
+    loads = sum(s["leaf_loads"] for s in stats_all)
+    sons = sum(s["son_loads"] for s in stats_all)
+    nbrs = sum(s["nbor_loads"] for s in stats_all)
+    tmax = t_ms
+    tot_scatt, tot_pk = scatt, pk_done
+    if dist:
+        v = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        tmax = float(v.item())
+        c = torch.tensor([scatt, pk_done], dtype=torch.float64, device=dev)
+        dist.all_reduce(c)
+        tot_scatt, tot_pk = float(c[0].item()), float(c[1].item())
+
+    # ---- end to end through the C ABI with host buffers (copies in the timed region)
+    e2e_inputs = [packets(wl, (rank * (args.warmup + args.steps + 1) + args.warmup + i) * P, P)
+                  for i in range(args.steps)]
+    outs = [{"status": np.zeros(P, np.int32), "nscatt": np.zeros(P, np.int64), "nu": np.zeros(P)}
+            for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_scatt = 0
+    for i in range(args.steps):
+        pk = e2e_inputs[i]
+        st = ctx.propagate(pk.pos, pk.dir, pk.nu, pk.ids, out=outs[i], stats=True)
+        e2e_scatt += st["nscatt_line"] + st["nscatt_dust"]
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        v = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        e2e_s = float(v.item())
+        c = torch.tensor([e2e_scatt], dtype=torch.float64, device=dev)
+        dist.all_reduce(c)
+        e2e_scatt = float(c[0].item())
+    h2d = P * (3 + 3 + 1 + 1) * 8
+    d2h = P * (4 + 8 + 8)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    value = tot_scatt / (tmax * 1e-3)
+    pk_rate = tot_pk / (tmax * 1e-3)
+    clk = clk.summary()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_mhz = clk["sm_mhz"] or 1900.0
+    issue_peak = 152 * 4 * sm_mhz * 1e6 / 1e9   # G warp-instructions / s
+    roof = None
+    if INST_PER_SCATT:
+        ach = INST_PER_SCATT * scatt / (t_ms * 1e-3) / 1e9
+        roof = {"bound": "alu", "achieved": ach, "peak": issue_peak, "unit": "Gwarp-inst/s",
+                "frac": ach / issue_peak, "traffic": None,
+                "peak_note": ISSUE_PEAK_NOTE + " (median SM clock under load %.0f MHz)" % sm_mhz}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": issue_peak, "unit": "Gwarp-inst/s", "frac": None,
+                "traffic": None, "peak_note": ISSUE_PEAK_NOTE}
+    cell_bytes = loads * 24 + sons * 4 + nbrs * 28
+    hbm = peaks.get("hbm_gbs", 6671.9)
+    line = {"metric": METRIC, "value": value, "unit": "scatterings/s", "packets_per_s": pk_rate,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "packets_per_step": P, "per_rank": True,
+                       "l2": "256 MB buffer written between timed steps (L2 flush)",
+                       "mean_scatterings_per_packet": scatt / max(1, pk_done)},
+            "roofline": roof,
+            "hbm_cell_bytes": {"achieved_gbs": cell_bytes / (t_ms * 1e-3) / 1e9, "peak_gbs": hbm,
+                               "frac": cell_bytes / (t_ms * 1e-3) / 1e9 / hbm,
+                               "note": "algorithmic leaf/tree bytes touched (24 B per leaf visit, 4 B per son, "
+                                       "28 B per neighbour record) / time; of measured copy bandwidth"},
+            "e2e": {"value": e2e_scatt / e2e_s, "unit": "scatterings/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps,
+            "clocks": clk}
+    if not args.no_cpu_baseline and world == 1:
+        threads = os.cpu_count() or 1
+        sc, pr, npk, secs = cpu_oracle_rate(workload, args.cpu_seconds, threads)
+        line["cpu_baseline"] = {"value": sc, "unit": "scatterings/s", "cores": threads, "kind": "oracle",
+                                "sample": "%d packets of the workload (%.1f s on %d threads), %.3g packets/s"
+                                          % (npk, secs, threads, pr)}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

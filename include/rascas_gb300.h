@@ -1,0 +1,246 @@
+/*
+ * rascas_gb300.h -- C ABI of the GB300 resonant-line Monte Carlo library.
+ *
+ * The library propagates photon packets of resonant lines (H I Lyman-alpha,
+ * metal lines with fluorescent channels) and dust through a graded octree of
+ * gas cells on one NVIDIA GB300 GPU (sm_103a), following Michel-Dansac et al.
+ * (2020), "RASCAS: RAdiation SCattering in Astrophysical Simulations":
+ *   - packets are independent and the transfer is passive (Sect. 2);
+ *   - optical depth tau_event = -ln r, walked cell to cell (Sect. 3);
+ *   - line opacity with the Hjerting-Voigt function, dust opacity (Sect. 3.1);
+ *   - resonant scattering with u_par rejection sampling, core/wing phase
+ *     functions and recoil, dust absorption / Henyey-Greenstein scattering,
+ *     fluorescent decay channels (Sects. 3.2, 3.3);
+ *   - graded octree with son/father/neighbour links (Sect. 4.3);
+ *   - peeling towards fixed observer directions into spectra, images and
+ *     spectral cubes (Sect. 5.1).
+ *
+ * Conventions for every call:
+ *   - Every function returns a rascas_status (0 = success, < 0 = error); no
+ *     C++ exception crosses the ABI.  rascas_last_error() gives the text of
+ *     the last error of a context.
+ *   - Pointers marked "mem" are host pointers when mem == RASCAS_HOST and
+ *     device pointers (on the context's device) when mem == RASCAS_DEVICE.
+ *     Inputs are copied or only read during the call; the caller keeps
+ *     ownership of every buffer it passes.  Outputs are written into caller
+ *     buffers.
+ *   - Work runs on the context's stream (rascas_set_stream; default: the
+ *     legacy default stream).  Calls that take host buffers, return stats or
+ *     copy tallies to the host synchronise that stream before returning; the
+ *     others are asynchronous with respect to the host.
+ *   - A context is not thread-safe: use one context per host thread.
+ *   - Units: cgs; positions in box units, the box being [0,1)^3 of physical
+ *     size box_cm; frequencies in Hz in the external (observer) frame.
+ */
+#ifndef RASCAS_GB300_H
+#define RASCAS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rascas_ctx rascas_ctx;
+
+typedef enum {
+    RASCAS_OK = 0,
+    RASCAS_E_ARG = -1,      /* invalid argument (null pointer, bad size, malformed octree) */
+    RASCAS_E_OOM = -2,      /* device or host allocation failed */
+    RASCAS_E_CUDA = -3,     /* a CUDA runtime call failed */
+    RASCAS_E_STATE = -4,    /* call made before the state it needs was set */
+    RASCAS_E_TIMEOUT = -5,  /* a bounded device wait gave up */
+    RASCAS_E_CAPPED = -6    /* some packets hit a cap and fail_on_cap was set */
+} rascas_status;
+
+enum { RASCAS_HOST = 0, RASCAS_DEVICE = 1 };
+
+/* per-packet status (Sect. 4.4: escaped / absorbed; "capped" when a packet
+ * reached the step or scattering cap; "error" for an internal failure) */
+enum { RASCAS_PK_ACTIVE = 0, RASCAS_PK_ESCAPED = 1, RASCAS_PK_ABSORBED = 2,
+       RASCAS_PK_CAPPED = 3, RASCAS_PK_ERROR = 4 };
+
+enum { RASCAS_DOMAIN_SPHERE = 0, RASCAS_DOMAIN_SLAB = 1, RASCAS_DOMAIN_CUBE = 2 };
+
+enum { RASCAS_TALLY_SPECTRUM = 0,   /* [nbin] escape spectrum, 1 per escaped packet */
+       RASCAS_TALLY_PEEL_SPECTRA = 1, /* [ndir][nbin] peeled flux per sr */
+       RASCAS_TALLY_PEEL_IMAGES = 2,  /* [ndir][npix][npix] (row = v, column = u) */
+       RASCAS_TALLY_PEEL_CUBES = 3 }; /* [ndir][npix][npix][nbin] */
+
+#define RASCAS_MAX_LINES 4
+#define RASCAS_MAX_CHANNELS 4
+#define RASCAS_MAX_DIRS 8
+
+/* Graded octree and leaf fields (Sect. 4.3, Fig. amr_struct).
+ * Oct 0 is the root oct: level 1, its 8 cells of size 1/2 cover the box.
+ * son[8*oct + child], child = (ix&1) | (iy&1)<<1 | (iz&1)<<2 with (ix,iy,iz)
+ * the integer coordinates of the cell at its level: > 0 = the oct that
+ * refines the cell, < 0 = -(leaf + 1), the leaf's index in the field arrays.
+ * Neighbouring leaves should differ by at most one level (graded tree, as the
+ * paper requires); other trees are accepted but walk more slowly.
+ * Fields per leaf: n_HI and n_metal (cm^-3, n_metal may be NULL = 0), bulk
+ * velocity vx,vy,vz (cm/s), temperature T (K), n_dust (pseudo density per H
+ * atom of Sect. 3.1.2, multiplies the dust cross section). */
+typedef struct {
+    int32_t noct;
+    int32_t nleaf;
+    const int32_t *son;
+    const float *n_HI, *vx, *vy, *vz, *T, *n_dust, *n_metal;
+    double box_cm;
+} rascas_octree;
+
+/* Domain of the computational volume (Sect. 4): a sphere (centre, radius),
+ * a slab |z - centre_z| <= size, periodic in x and y (Sect. 4, footnote on
+ * slabs), or a cube (centre, half side).  Packets escape at its border. */
+typedef struct {
+    int32_t kind;
+    double centre[3];
+    double size;
+} rascas_domain;
+
+/* One absorption line (Sect. 3.1.1, Table 1): rest frequency nu0 (Hz),
+ * Einstein A of the resonant channel, oscillator strength f_lu, scatterer
+ * mass (g); density: 0 = n_HI, 1 = n_metal, times `abundance`; phase: 0 =
+ * Lya core/wing (Eqs. Pcore, Pwing), 1 = isotropic.  Decay channels
+ * (Sect. 3.2.3): chan_A/chan_nu[0] is the resonant channel (= A_ul, nu0),
+ * the others fluorescent; nchan in [1, RASCAS_MAX_CHANNELS]. */
+typedef struct {
+    double nu0, A_ul, f_lu, mass_g, abundance;
+    int32_t density, phase, nchan;
+    double chan_A[RASCAS_MAX_CHANNELS];
+    double chan_nu[RASCAS_MAX_CHANNELS];
+} rascas_line;
+
+/* Dust (Sects. 3.1.2, 3.2.2): cross section per unit n_dust (cm^2, constant
+ * across the line), albedo, Henyey-Greenstein asymmetry g. */
+typedef struct {
+    double sigma, albedo, g;
+} rascas_dust;
+
+/* Switches: recoil (Eq. nuout_nuin denominator), isotropic phase function for
+ * every line, keep_dir (scatterings keep the direction: the error-budget
+ * experiment of Sect. 4.5), Gaussian u_par branch threshold (Sect. 3.3.3,
+ * default 8), per-packet caps on scatterings and walk steps (0 = none),
+ * tau_stop: peeling rays stop once tau > tau_stop (their contribution is
+ * below exp(-tau_stop)), run seed of the Philox4x32-10 streams, fail_on_cap:
+ * make rascas_propagate return RASCAS_E_CAPPED when a packet was capped. */
+typedef struct {
+    int32_t recoil, isotropic, keep_dir, fail_on_cap;
+    double x_gauss;
+    int64_t max_scatt, max_steps;
+    double tau_stop;
+    uint64_t seed;
+} rascas_physics;
+
+/* Detector: frequency axis [nu_lo, nu_hi) in nbin bins (external frame),
+ * shared by the escape spectrum and the peeled spectra/cubes; ndir peeling
+ * directions (unit vectors, normalised by the library); npix x npix images of
+ * side fov (box units) centred on `centre`, in the plane spanned by the
+ * orthonormal basis of Duff et al. (2017) built on each direction; cube = 1
+ * also accumulates spectral cubes. */
+typedef struct {
+    double nu_lo, nu_hi;
+    int32_t nbin, ndir, npix, cube;
+    double dirs[RASCAS_MAX_DIRS][3];
+    double fov;
+    double centre[3];
+} rascas_detector;
+
+/* Packet initial conditions (the paper's PPIC list, Sect. 2): pos[3n], dir[3n]
+ * (xyz interleaved, unit vectors), nu[n] (external frame, Hz, along dir),
+ * id[n] (keys the packet's random stream). */
+typedef struct {
+    const double *pos, *dir, *nu;
+    const uint64_t *id;
+} rascas_packets_in;
+
+/* Per-packet results; any member may be NULL.  pos/dir [3n], path = total
+ * distance travelled (box units). */
+typedef struct {
+    int32_t *status;
+    int64_t *nscatt;
+    double *nu, *pos, *dir, *path;
+} rascas_packets_out;
+
+typedef struct {
+    int64_t packets, escaped, absorbed, capped, errors;
+    int64_t nscatt_line, nscatt_dust, ncross, npeel_rays, npeel_cells;
+    int64_t upar_trials, leaf_loads, son_loads, nbor_loads;
+    double kernel_ms;
+} rascas_run_stats;
+
+/* One traced event (state after an interaction, an escape, or at emission). */
+typedef struct {
+    double p[3], k[3], nu;
+    int32_t leaf, level, ijk[3], status;
+    int64_t ndraw, nscatt, nsteps;
+} rascas_event;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  Allocates nothing large. */
+int rascas_create(rascas_ctx **out, int device);
+/* Free every device buffer of the context and the context itself. */
+int rascas_destroy(rascas_ctx *ctx);
+/* Text of the last error on this context (never NULL). */
+const char *rascas_last_error(const rascas_ctx *ctx);
+/* Stream for all later work (a cudaStream_t passed as void*, NULL = legacy). */
+int rascas_set_stream(rascas_ctx *ctx, void *stream);
+
+/* ---- problem set-up (the paper's problem statement: mesh + fields,
+ *      lines, domain, sources, peeling directions) ----------------------- */
+
+/* Copy an octree and its leaf fields to the device (mem: where the arrays
+ * live).  Validates the tree (RASCAS_E_ARG on malformed input), derives the
+ * father and neighbour links of Sect. 4.3 and the leaf levels, and packs the
+ * fields into 32-byte leaf records. */
+int rascas_load_octree(rascas_ctx *ctx, const rascas_octree *tree, int mem);
+int rascas_set_domain(rascas_ctx *ctx, const rascas_domain *dom);
+int rascas_set_lines(rascas_ctx *ctx, const rascas_line *lines, int32_t nline, const rascas_dust *dust);
+int rascas_set_physics(rascas_ctx *ctx, const rascas_physics *phys);
+/* Also zeroes the tallies (their shapes follow the detector). */
+int rascas_set_detector(rascas_ctx *ctx, const rascas_detector *det);
+int rascas_zero_tallies(rascas_ctx *ctx);
+
+/* ---- the hot path -------------------------------------------------------- */
+
+/* Propagate n packets until each escapes, is absorbed or is capped, peeling
+ * at emission and at every scattering when the detector has directions.
+ * Tallies accumulate across calls.  in/out pointers follow `mem`; out may be
+ * NULL; stats may be NULL (then the call does not synchronise when
+ * mem == RASCAS_DEVICE). */
+int rascas_propagate(rascas_ctx *ctx, const rascas_packets_in *in, int64_t n,
+                     const rascas_packets_out *out, int mem, rascas_run_stats *stats);
+
+/* Copy a tally (kind = RASCAS_TALLY_*) into dst (count floats, mem). */
+int rascas_get_tally(rascas_ctx *ctx, int kind, float *dst, size_t count, int mem);
+
+/* Optical depth from pos[3i] along dir[3i] to the domain border at external
+ * frequency nu[i] (the peeling ray integral, no tau_stop).  Optionally the
+ * leaves crossed and the path length in each (cells/lens [n][cap], ncell[n]
+ * = number of cells crossed, which may exceed cap).  All pointers follow mem;
+ * cells/lens/ncell may be NULL. */
+int rascas_ray_tau(rascas_ctx *ctx, int64_t n, const double *pos, const double *dir,
+                   const double *nu, double *tau, int32_t *cells, double *lens,
+                   int32_t cap, int32_t *ncell, int mem);
+
+/* Run packets like rascas_propagate (same streams, no tallies) and record up
+ * to max_events events per packet into events[n][max_events]; nevents[n]
+ * gets how many were recorded.  Event 0 is the state at emission. */
+int rascas_trace(rascas_ctx *ctx, const rascas_packets_in *in, int64_t n, int32_t max_events,
+                 rascas_event *events, int32_t *nevents, int mem);
+
+/* ---- device-function probes (parity of the building blocks) ------------ */
+
+/* H(a, x) of the hot path (Tasitsiomi 2006 form, Sect. 3.3.2) at a[i], x[i]. */
+int rascas_eval_voigt(rascas_ctx *ctx, int64_t n, const float *a, const double *x, float *H, int mem);
+/* One u_par draw (Sect. 3.3.3) per i for frequency x[i], Voigt parameter a[i],
+ * on the stream of packet id[i] starting at draw 0; ndraw[i] = words used. */
+int rascas_sample_upar(rascas_ctx *ctx, int64_t n, const double *x, const float *a,
+                       const uint64_t *id, float *u, int32_t *ndraw, int mem);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

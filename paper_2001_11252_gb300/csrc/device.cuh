@@ -1,0 +1,459 @@
+// Device building blocks of the resonant-line Monte Carlo path on GB300
+// (sm_103a): counter-based random streams, the Hjerting-Voigt function, u_par
+// sampling, phase functions, and the FP64 octree walk.  Each function cites
+// the passage of Michel-Dansac et al. (2020) it implements.
+//
+// Precision policy (GB300 runs FP64 at ~1/70 of the FP32 rate): packet
+// position, distances to faces and borders, frequency and tau accumulation are
+// FP64; Voigt, velocity sampling, phase functions and peeling weights are FP32.
+// FP64 division, square root and logarithm stay off the per-scattering path.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "internal.h"
+
+namespace rg {
+
+// CODATA 2018, cgs (kernel-side copy)
+constexpr double kC = 2.99792458e10;
+constexpr float kPiF = 3.14159265358979f;
+constexpr float kSqrtPiF = 1.7724538509055159f;
+constexpr float kTwoPiF = 6.2831853071795865f;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al. 2011).  Key = run seed; counter = (draw block
+// lo, hi, packet id lo, hi).  Draw word n of a packet is word n%4 of block n/4.
+// ---------------------------------------------------------------------------
+struct Rng {
+    uint32_t k0, k1, id0, id1;
+    uint32_t n;        // next draw index
+    uint32_t w0, w1, w2, w3;  // cached block n/4 (valid when n%4 != 0)
+
+    __device__ __forceinline__ void block(uint32_t blk) {
+        uint32_t c0 = blk, c1 = 0, c2 = id0, c3 = id1;
+        uint32_t a0 = k0, a1 = k1;
+#pragma unroll
+        for (int r = 0; r < 10; ++r) {
+            if (r) { a0 += 0x9E3779B9u; a1 += 0xBB67AE85u; }
+            uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+            uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+            uint32_t n0 = hi1 ^ c1 ^ a0, n2 = hi0 ^ c3 ^ a1;
+            c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        }
+        w0 = c0; w1 = c1; w2 = c2; w3 = c3;
+    }
+    __device__ __forceinline__ uint32_t word() {
+        uint32_t j = n & 3u;
+        if (j == 0u) block(n >> 2);
+        ++n;
+        return j == 0u ? w0 : (j == 1u ? w1 : (j == 2u ? w2 : w3));
+    }
+    // ((w >> 8) + 1/2) 2^-24: exactly representable, in (0, 1)
+    __device__ __forceinline__ float u24() {
+        return __uint2float_rn(word() >> 8) * 0x1p-24f + 0x1p-25f;
+    }
+    // ((wa >> 6) 2^26 + (wb >> 6) + 1/2) 2^-52 from two consecutive words
+    __device__ __forceinline__ double u52() {
+        uint32_t wa = word(), wb = word();
+        double m = __fma_rn((double)(wa >> 6), 67108864.0, (double)(wb >> 6));
+        return __fma_rn(m, 0x1p-52, 0x1p-53);
+    }
+    __device__ void init(const Params& P, uint64_t pid, uint32_t start = 0) {
+        k0 = P.key0; k1 = P.key1;
+        id0 = (uint32_t)pid; id1 = (uint32_t)(pid >> 32);
+        n = start;
+        if (n & 3u) block(n >> 2);
+    }
+};
+
+// tau_event = -ln r (Sect. 3) in FP32 without losing relative precision for r
+// near 1: -log1p(-(1 - r)) there, -log(r) below 1/2.  Relative error ~1e-7.
+__device__ __forceinline__ double tau_event(double r) {
+    if (r > 0.5) {
+        float s = (float)(1.0 - r);
+        return (double)(-log1pf(-s));
+    }
+    return (double)(-logf((float)r));
+}
+
+// ---------------------------------------------------------------------------
+// Hjerting-Voigt function, Tasitsiomi (2006) eqs. 7-8 (Sect. 3.3.2).  x^2 is
+// formed in FP64 and its rounding to FP32 is fed back into exp(-x^2) to first
+// order, so H keeps ~1e-7 relative accuracy where exp(-x^2) dominates.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float voigt_h(float a, double x) {
+    double x2d = x * x;
+    float x2 = (float)x2d;
+    float lo = (float)(x2d - (double)x2);
+    float e = expf(-x2) * (1.0f - lo);
+    float z = (x2 - 0.855f) / (x2 + 3.42f);
+    float q = 0.0f;
+    if (z > 0.0f) {
+        q = z * (1.0f + 21.0f / x2) * a / (kPiF * (x2 + 1.0f)) *
+            (0.1117f + z * (4.421f + z * (-9.207f + 5.674f * z)));
+    }
+    return kSqrtPiF * q + e;
+}
+
+// ---------------------------------------------------------------------------
+// u_par (Sect. 3.3.3): rejection method of Zheng & Miralda-Escude (2002) with
+// the fitted separation u0(x, log10 a), clamped at 0; |x| >= x_gauss: Gaussian
+// N(1/|x|, 1/2).  Returns u_par for frequency x (scatterer's Doppler units).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float u0_fit(float x, float a) {
+    float z = log10f(a);
+    float z2 = z * z;
+    float u0 = 2.648963f + 2.014446f * z + 0.351479f * z2 +
+               x * (-4.058673f - 3.675859f * z - 0.640003f * z2 +
+               x * (3.017395f + 2.117133f * z + 0.370294f * z2 +
+               x * (-0.869789f - 0.565886f * z - 0.096312f * z2 +
+               x * (0.110987f + 0.070103f * z + 0.011557f * z2 +
+               x * (-0.005200f - 0.003240f * z - 0.000519f * z2)))));
+    return fmaxf(u0, 0.0f);
+}
+
+__device__ __forceinline__ float sample_upar(Rng& rng, float x, float a, float x_gauss,
+                                             uint32_t& trials, bool& err) {
+    float sg = x < 0.0f ? -1.0f : 1.0f;
+    float xa = fabsf(x);
+    if (xa >= x_gauss) {
+        float r1 = rng.u24(), r2 = rng.u24();
+        trials += 1;
+        return sg * (1.0f / xa + sqrtf(-logf(r1)) * cospif(2.0f * r2));
+    }
+    float u0 = u0_fit(xa, a);
+    float th0 = atanf((u0 - xa) / a);
+    float e0 = expf(-u0 * u0);
+    const float hp = 0.5f * kPiF;
+    float p = (th0 + hp) / ((1.0f - e0) * th0 + (1.0f + e0) * hp);
+    float u0sq = u0 * u0;
+    for (uint32_t t = 0; t < (1u << 22); ++t) {
+        float r1 = rng.u24(), r2 = rng.u24(), r3 = rng.u24();
+        ++trials;
+        float th, lim;
+        if (r1 <= p) {
+            th = -hp + (th0 + hp) * r2;
+            lim = 0.0f;
+        } else {
+            th = th0 + (hp - th0) * r2;
+            lim = u0sq;
+        }
+        float u = a * tanf(th) + xa;
+        if (r3 <= expf(lim - u * u)) return sg * u;
+    }
+    err = true;
+    return 0.0f;
+}
+
+// ---------------------------------------------------------------------------
+// Phase functions (Sect. 3.3.1, Eqs. Pcore, Pwing, Pdust) and their inversion.
+// HG inversion carries the square the printed formula omits.
+// ---------------------------------------------------------------------------
+enum { PH_ISO = 0, PH_CORE = 1, PH_WING = 2, PH_HG = 3 };
+
+__device__ __forceinline__ float mu_sample(int kind, float r, float g) {
+    if (kind == PH_CORE) {
+        float B = 6.0f * (2.0f * r - 1.0f);
+        float A = sqrtf(B * B + 49.296296296296296f);  // 11^3 / 27
+        return cbrtf(A + B) - cbrtf(A - B);
+    }
+    if (kind == PH_WING) {
+        float B = 4.0f * r - 2.0f;
+        float A = sqrtf(B * B + 1.0f);
+        return cbrtf(A + B) - cbrtf(A - B);
+    }
+    if (kind == PH_HG && g != 0.0f) {
+        float t = (1.0f - g * g) / (1.0f - g + 2.0f * g * r);
+        return fminf(1.0f, fmaxf(-1.0f, (1.0f + g * g - t * t) / (2.0f * g)));
+    }
+    return 2.0f * r - 1.0f;
+}
+
+// phase function per unit mu (integrates to one over [-1, 1])
+__device__ __forceinline__ float phase_p(int kind, float mu, float g) {
+    if (kind == PH_CORE) return 0.4583333333f + 0.125f * mu * mu;
+    if (kind == PH_WING) return 0.375f * (1.0f + mu * mu);
+    if (kind == PH_HG) {
+        float d = 1.0f + g * g - 2.0f * g * mu;
+        return 0.5f * (1.0f - g * g) * rsqrtf(d * d * d);
+    }
+    return 0.5f;
+}
+
+// orthonormal basis (b1, b2) perpendicular to unit n: Duff et al. (2017)
+__device__ __forceinline__ void onb(float nx, float ny, float nz, float3& b1, float3& b2) {
+    float sg = copysignf(1.0f, nz);
+    float a = -1.0f / (sg + nz);
+    float b = nx * ny * a;
+    b1 = make_float3(1.0f + sg * nx * nx * a, sg * b, -sg * nx);
+    b2 = make_float3(b, sg + ny * ny * a, -ny);
+}
+
+// ---------------------------------------------------------------------------
+// Octree walk (Sect. 4.3).  Cells entered by a packet at p moving along k are
+// the ones containing p + eps k.  Integer coordinates are kept at the finest
+// level L of the tree: I = floor(p 2^L) for k >= 0, ceil(p 2^L) - 1 for k < 0.
+// ---------------------------------------------------------------------------
+struct Where {
+    int leaf, oct, level;
+    int i, j, k;   // integer coordinates of the leaf at its level
+};
+
+__device__ __forceinline__ int dir_coord(double p, double k, double scale) {
+    double y = p * scale;   // exact: scale is a power of two
+    return k < 0.0 ? __double2int_ru(y) - 1 : __double2int_rd(y);
+}
+
+// slab domains are periodic in x and y (Sect. 4): bring p + eps k into the box
+__device__ __forceinline__ void wrap_periodic(const Params& P, double p[3], const double k[3]) {
+    if (P.dom_kind != 1) return;
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax) {
+        int c = dir_coord(p[ax], k[ax], 2.0);
+        if (c >= 2) p[ax] = p[ax] - 1.0;
+        else if (c < 0) p[ax] = p[ax] + 1.0;
+    }
+}
+
+// descend from the son value `code` of a cell at level m in oct `oct`
+__device__ __forceinline__ void descend(const Params& P, int code, int m, int oct,
+                                        int tx, int ty, int tz, Where& w, uint32_t& loads) {
+    const int L = P.max_level;
+    while (code > 0) {
+        oct = code;
+        ++m;
+        int s = L - m;
+        int child = ((tx >> s) & 1) | (((ty >> s) & 1) << 1) | (((tz >> s) & 1) << 2);
+        code = __ldg(P.son + 8 * oct + child);
+        ++loads;
+    }
+    int s = L - m;
+    w.leaf = -code - 1;
+    w.oct = oct;
+    w.level = m;
+    w.i = tx >> s;
+    w.j = ty >> s;
+    w.k = tz >> s;
+}
+
+// where-is-point: the dense top grid at level S gives the deepest cell at level
+// <= S holding the target; descend from there.  False if outside the box.
+__device__ __forceinline__ bool locate(const Params& P, int tx, int ty, int tz, Where& w,
+                                       uint32_t& loads) {
+    const int L = P.max_level;
+    const int n = 1 << L;
+    if ((unsigned)tx >= (unsigned)n || (unsigned)ty >= (unsigned)n || (unsigned)tz >= (unsigned)n)
+        return false;
+    const int S = P.top_level;
+    const int s = L - S;
+    long long idx = (((long long)(tz >> s) << S) + (ty >> s)) << S;
+    idx += (tx >> s);
+    int4 e = __ldg(P.top + idx);
+    ++loads;
+    descend(P, e.x, e.y, e.z, tx, ty, tz, w, loads);
+    return true;
+}
+
+__device__ __forceinline__ bool locate_point(const Params& P, const double p[3], const double k[3],
+                                             Where& w, uint32_t& loads) {
+    double sc = (double)(1 << P.max_level);
+    return locate(P, dir_coord(p[0], k[0], sc), dir_coord(p[1], k[1], sc), dir_coord(p[2], k[2], sc),
+                  w, loads);
+}
+
+// Neighbour search after crossing a face (Sect. 4.3): the target is first
+// looked for inside the father cell of the current leaf (its own oct), then in
+// the father's neighbour across the face, then from the top grid.
+__device__ __forceinline__ bool next_leaf(const Params& P, const double p[3], const double k[3],
+                                          int axis, Where& w, uint32_t& son_loads,
+                                          uint32_t& nbor_loads) {
+    const int L = P.max_level;
+    double sc = (double)(1 << L);
+    int t[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) t[ax] = dir_coord(p[ax], k[ax], sc);
+    const int n = 1 << L;
+    if ((unsigned)t[0] >= (unsigned)n || (unsigned)t[1] >= (unsigned)n || (unsigned)t[2] >= (unsigned)n)
+        return false;
+    const int l = w.level;
+    const int sh = L - l;
+    int fi = w.i >> 1, fj = w.j >> 1, fk = w.k >> 1;
+    if ((t[0] >> (sh + 1)) == fi && (t[1] >> (sh + 1)) == fj && (t[2] >> (sh + 1)) == fk) {
+        int child = ((t[0] >> sh) & 1) | (((t[1] >> sh) & 1) << 1) | (((t[2] >> sh) & 1) << 2);
+        int code = __ldg(P.son + 8 * w.oct + child);
+        ++son_loads;
+        descend(P, code, l, w.oct, t[0], t[1], t[2], w, son_loads);
+        return true;
+    }
+    if (l >= 2) {
+        int face = 2 * axis + (k[axis] > 0.0 ? 1 : 0);
+        int4 a = __ldg(P.nbr + 2 * w.oct);
+        int4 b = __ldg(P.nbr + 2 * w.oct + 1);
+        ++nbor_loads;
+        int nc = face == 0 ? a.x : face == 1 ? a.y : face == 2 ? a.z : face == 3 ? a.w : face == 4 ? b.x : b.y;
+        int nl = (b.w >> (5 * face)) & 31;
+        if (nc >= 0 && nl >= 1) {
+            // coordinates of the neighbour cell at its level nl (<= l - 1)
+            int f[3] = {fi, fj, fk};
+            int nf = 1 << (l - 1);
+            f[axis] += (k[axis] > 0.0 ? 1 : -1);
+            f[axis] = (f[axis] + nf) & (nf - 1);
+            int d = (l - 1) - nl;
+            int s2 = L - nl;
+            if ((t[0] >> s2) == (f[0] >> d) && (t[1] >> s2) == (f[1] >> d) && (t[2] >> s2) == (f[2] >> d)) {
+                int code = __ldg(P.son + nc);
+                ++son_loads;
+                descend(P, code, nl, nc >> 3, t[0], t[1], t[2], w, son_loads);
+                return true;
+            }
+        }
+    }
+    return locate(P, t[0], t[1], t[2], w, son_loads);
+}
+
+// distance along k from p to the exit face of leaf w (FP64, exactly the
+// oracle's (face - p) * (1/k)); axis = crossed axis, ties to the lowest axis
+__device__ __forceinline__ double face_distance(const double p[3], const double k[3],
+                                                const double inv[3], const Where& w, int& axis) {
+    double h = __dmul_rn(1.0, ldexp(1.0, -w.level));
+    int c[3] = {w.i, w.j, w.k};
+    double best = __longlong_as_double(0x7ff0000000000000ULL);  // +inf
+    int ba = -1;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        if (k[ax] == 0.0) continue;
+        double face = __dmul_rn((double)(k[ax] > 0.0 ? c[ax] + 1 : c[ax]), h);
+        double t = __dmul_rn(__dsub_rn(face, p[ax]), inv[ax]);
+        if (t < best) { best = t; ba = ax; }
+    }
+    axis = ba;
+    return best < 0.0 ? 0.0 : best;
+}
+
+// distance along k from p to the domain border (FP64, same operation order as
+// the oracle)
+__device__ __forceinline__ double border_distance(const Params& P, const double p[3],
+                                                  const double k[3], const double inv[3]) {
+    if (P.dom_kind == 0) {
+        double d0 = __dsub_rn(p[0], P.dom_c[0]);
+        double d1 = __dsub_rn(p[1], P.dom_c[1]);
+        double d2 = __dsub_rn(p[2], P.dom_c[2]);
+        double b = __dadd_rn(__dadd_rn(__dmul_rn(d0, k[0]), __dmul_rn(d1, k[1])), __dmul_rn(d2, k[2]));
+        double cc = __dsub_rn(__dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2)),
+                              __dmul_rn(P.dom_R, P.dom_R));
+        double disc = __dsub_rn(__dmul_rn(b, b), cc);
+        if (disc < 0.0) disc = 0.0;
+        double sq = __dsqrt_rn(disc);
+        double t = b > 0.0 ? __ddiv_rn(-cc, __dadd_rn(b, sq)) : __dsub_rn(sq, b);
+        return t < 0.0 ? 0.0 : t;
+    }
+    double best = __longlong_as_double(0x7ff0000000000000ULL);
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        if (P.dom_kind == 1 && ax != 2) continue;
+        if (k[ax] == 0.0) continue;
+        double edge = k[ax] > 0.0 ? __dadd_rn(P.dom_c[ax], P.dom_R) : __dsub_rn(P.dom_c[ax], P.dom_R);
+        double t = __dmul_rn(__dsub_rn(edge, p[ax]), inv[ax]);
+        if (t < best) best = t;
+    }
+    return best < 0.0 ? 0.0 : best;
+}
+
+// smallest distance from p to any face of leaf w (box units, FP64), for the
+// guaranteed-inside budget of the scattering loop
+__device__ __forceinline__ double inner_distance(const double p[3], const Where& w) {
+    double h = ldexp(1.0, -w.level);
+    int c[3] = {w.i, w.j, w.k};
+    double best = h;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        double lo = __dmul_rn((double)c[ax], h);
+        double d1 = __dsub_rn(p[ax], lo);
+        double d2 = __dsub_rn(__dadd_rn(lo, h), p[ax]);
+        best = fmin(best, fmin(d1, d2));
+    }
+    return best;
+}
+
+// move to the exit face along `axis` and snap the crossing coordinate
+__device__ __forceinline__ void move_to_face(double p[3], const double k[3], int axis, double t,
+                                             const Where& w) {
+    double h = ldexp(1.0, -w.level);
+    int c[3] = {w.i, w.j, w.k};
+    double face = __dmul_rn((double)(k[axis] > 0.0 ? c[axis] + 1 : c[axis]), h);
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax)
+        if (ax != axis) p[ax] = __fma_rn(t, k[ax], p[ax]);
+    p[axis] = face;
+}
+
+// ---------------------------------------------------------------------------
+// Cell state cached while a packet stays in one leaf
+// ---------------------------------------------------------------------------
+template <int NL>
+struct CellCache {
+    float vx, vy, vz;
+    float kap_d;                 // dust opacity (cm^-1)
+    int flags;
+    double invdnu[NL];           // 1 / Delta nu_D (1/Hz)
+    float a[NL], kap0[NL];       // Voigt a, n_X sigma_0 (cm^-1)
+    float vth_c[NL];             // v_th / c
+    float T;
+};
+
+template <int NL>
+__device__ __forceinline__ void load_cell(const Params& P, int leaf, CellCache<NL>& cc) {
+    float4 r0 = __ldg(P.rec + 2 * leaf);
+    float4 r1 = __ldg(P.rec + 2 * leaf + 1);
+    cc.vx = r0.y; cc.vy = r0.z; cc.vz = r0.w;
+    cc.T = r1.x;
+    cc.kap_d = r1.y * P.dust_sigma;
+    cc.flags = __float_as_int(r1.w);
+    float T = fmaxf(r1.x, 1e-30f);
+    float rs = rsqrtf(T);
+    // one Newton step in FP64 on 1/sqrt(T): x enters exp(-x^2) and must carry
+    // ~1e-10 relative accuracy
+    double rd = (double)rs;
+    double Td = (double)T;
+    rd = rd * __fma_rn(-0.5 * Td, rd * rd, 1.5);
+#pragma unroll
+    for (int i = 0; i < NL; ++i) {
+        const LineDev& L = P.line[i];
+        float n = (L.dens == 1 ? r1.z : r0.x) * L.abund;
+        cc.invdnu[i] = L.invdnu_pref * rd;
+        cc.a[i] = L.a_pref * rs;
+        cc.kap0[i] = n * L.sig_pref * rs;
+        cc.vth_c[i] = L.vth_over_c_pref * T * rs;
+    }
+}
+
+// beta = k . v / c in FP64
+template <int NL>
+__device__ __forceinline__ double beta_of(const CellCache<NL>& cc, const double k[3]) {
+    return __fma_rn(k[0], (double)cc.vx, __fma_rn(k[1], (double)cc.vy, k[2] * (double)cc.vz)) * (1.0 / kC);
+}
+
+// nu_ext = nu_gas (1 + beta) and its inverse nu_gas = nu_ext / (1 + beta)
+// evaluated as a series in beta (|beta| < 1e-2; error < beta^5)
+__device__ __forceinline__ double to_gas(double nu_ext, double b) {
+    double s = __fma_rn(b, __fma_rn(b, __fma_rn(b, __fma_rn(-b, b, b), -b), b), -b);
+    // s = -b + b^2 - b^3 + b^4 - b^5
+    return __fma_rn(nu_ext, s, nu_ext);
+}
+__device__ __forceinline__ double to_ext(double nu_gas, double b) { return __fma_rn(nu_gas, b, nu_gas); }
+
+// total opacity at gas-frame frequency nu (cm^-1), per line in kl[]
+template <int NL>
+__device__ __forceinline__ float opacity(const Params& P, const CellCache<NL>& cc, double nu,
+                                         float kl[NL]) {
+    float tot = cc.kap_d;
+#pragma unroll
+    for (int i = 0; i < NL; ++i) {
+        double x = (nu - P.line[i].nu0) * cc.invdnu[i];
+        kl[i] = cc.kap0[i] * voigt_h(cc.a[i], x);
+        tot += kl[i];
+    }
+    return tot;
+}
+
+}  // namespace rg

@@ -1,0 +1,749 @@
+// Host side of the C ABI (include/rascas_gb300.h): context, octree loader
+// (validation, father/neighbour links of Sect. 4.3, top-level lookup grid,
+// packed leaf records), problem set-up and kernel launches.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rascas_gb300.h"
+#include "internal.h"
+
+using rg::Params;
+
+namespace {
+
+// CODATA 2018, cgs (host-side copy for the line constants)
+constexpr double kC = 2.99792458e10;
+constexpr double kKB = 1.380649e-16;
+constexpr double kH = 6.62607015e-27;
+constexpr double kME = 9.1093837015e-28;
+constexpr double kE = 4.803204712570263e-10;
+constexpr double kPi = 3.14159265358979323846;
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    cudaError_t ensure(size_t b) {
+        if (b <= bytes) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e == cudaSuccess) bytes = b;
+        else p = nullptr;
+        return e;
+    }
+};
+
+}  // namespace
+
+struct rascas_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err = "no error";
+    int sms = 0;
+    // mesh
+    bool has_mesh = false;
+    int noct = 0, nleaf = 0, max_level = 0, top_level = 0;
+    double box_cm = 0.0;
+    std::vector<int> leaf_level;
+    std::vector<int> leaf_ijk;     // 3 per leaf
+    std::vector<float> rec;        // 8 per leaf
+    bool has_metal = false;
+    DevBuf d_rec, d_son, d_nbr, d_top;
+    // problem
+    bool has_domain = false, has_lines = false, has_phys = false, has_det = false;
+    rascas_domain dom{};
+    rascas_physics phys{};
+    rascas_detector det{};
+    Params P{};
+    DevBuf d_spec, d_pspec, d_pimg, d_pcube, d_counters;
+    DevBuf stage_in, stage_out, stage_aux;
+};
+
+namespace {
+
+int fail(rascas_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(rascas_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, e == cudaErrorMemoryAllocation ? RASCAS_E_OOM : RASCAS_E_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+cudaError_t to_host(void* dst, const void* src, size_t bytes, int mem) {
+    if (mem == RASCAS_DEVICE) return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost);
+    std::memcpy(dst, src, bytes);
+    return cudaSuccess;
+}
+
+void leaf_flags(rascas_ctx* ctx) {
+    // a leaf is interior when it lies strictly inside the domain with a
+    // relative margin: then no ray from inside it reaches the border before
+    // one of its faces, and the walk skips the border distance there
+    for (int i = 0; i < ctx->nleaf; ++i) {
+        int l = ctx->leaf_level[i];
+        double h = std::ldexp(1.0, -l);
+        double lo[3], hi[3];
+        for (int ax = 0; ax < 3; ++ax) {
+            lo[ax] = ctx->leaf_ijk[3 * i + ax] * h;
+            hi[ax] = lo[ax] + h;
+        }
+        bool interior = false;
+        if (ctx->has_domain) {
+            const double* c = ctx->dom.centre;
+            double R = ctx->dom.size;
+            const double m = 1e-9 * (R > 0 ? R : 1.0);
+            if (ctx->dom.kind == RASCAS_DOMAIN_SPHERE) {
+                double d2 = 0.0;
+                for (int ax = 0; ax < 3; ++ax) {
+                    double far = std::fmax(std::fabs(lo[ax] - c[ax]), std::fabs(hi[ax] - c[ax]));
+                    d2 += far * far;
+                }
+                interior = std::sqrt(d2) < R - m;
+            } else {
+                interior = true;
+                for (int ax = 0; ax < 3; ++ax) {
+                    if (ctx->dom.kind == RASCAS_DOMAIN_SLAB && ax != 2) continue;
+                    if (!(lo[ax] > c[ax] - R + m && hi[ax] < c[ax] + R - m)) interior = false;
+                }
+            }
+        }
+        int flags = interior ? 0 : rg::kFlagBorder;
+        std::memcpy(&ctx->rec[8 * i + 7], &flags, 4);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int rascas_create(rascas_ctx** out, int device) {
+    if (!out) return RASCAS_E_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return RASCAS_E_CUDA;
+    rascas_ctx* ctx = new (std::nothrow) rascas_ctx();
+    if (!ctx) return RASCAS_E_OOM;
+    ctx->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete ctx;
+        return RASCAS_E_CUDA;
+    }
+    cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
+    if (ctx->d_counters.ensure(sizeof(unsigned long long) * (rg::CNT_N + 1)) != cudaSuccess) {
+        delete ctx;
+        return RASCAS_E_OOM;
+    }
+    ctx->P.counters = (unsigned long long*)ctx->d_counters.p;
+    ctx->P.head = ctx->P.counters + rg::CNT_N;
+    ctx->P.tau_stop = 50.0;
+    ctx->P.x_gauss = 8.0f;
+    ctx->P.recoil = 1;
+    *out = ctx;
+    return RASCAS_OK;
+}
+
+int rascas_destroy(rascas_ctx* ctx) {
+    if (!ctx) return RASCAS_E_ARG;
+    cudaSetDevice(ctx->device);
+    for (DevBuf* b : {&ctx->d_rec, &ctx->d_son, &ctx->d_nbr, &ctx->d_top, &ctx->d_spec, &ctx->d_pspec,
+                      &ctx->d_pimg, &ctx->d_pcube, &ctx->d_counters, &ctx->stage_in, &ctx->stage_out,
+                      &ctx->stage_aux})
+        b->release();
+    delete ctx;
+    return RASCAS_OK;
+}
+
+const char* rascas_last_error(const rascas_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int rascas_set_stream(rascas_ctx* ctx, void* stream) {
+    if (!ctx) return RASCAS_E_ARG;
+    ctx->stream = (cudaStream_t)stream;
+    return RASCAS_OK;
+}
+
+int rascas_load_octree(rascas_ctx* ctx, const rascas_octree* t, int mem) {
+    if (!ctx || !t) return RASCAS_E_ARG;
+    if (t->noct < 1 || t->nleaf < 1 || !t->son || !t->n_HI || !t->vx || !t->vy || !t->vz || !t->T || !t->n_dust)
+        return fail(ctx, RASCAS_E_ARG, "octree: missing array or empty tree");
+    if (!(t->box_cm > 0.0)) return fail(ctx, RASCAS_E_ARG, "octree: box_cm must be > 0");
+    CK(cudaSetDevice(ctx->device));
+    const int noct = t->noct, nleaf = t->nleaf;
+    std::vector<int> son((size_t)8 * noct);
+    CK(to_host(son.data(), t->son, son.size() * 4, mem));
+    std::vector<float> f[7];
+    const float* src[7] = {t->n_HI, t->vx, t->vy, t->vz, t->T, t->n_dust, t->n_metal};
+    for (int i = 0; i < 7; ++i) {
+        f[i].assign(nleaf, 0.0f);
+        if (src[i]) CK(to_host(f[i].data(), src[i], (size_t)nleaf * 4, mem));
+    }
+    // breadth-first traversal: validates links, gives levels and coordinates
+    std::vector<int> oct_level(noct, 0), oct_org((size_t)3 * noct, 0), oct_father(noct, -1);
+    std::vector<int> lvl(nleaf, 0), ijk((size_t)3 * nleaf, 0);
+    std::vector<int> queue;
+    queue.reserve(noct);
+    queue.push_back(0);
+    oct_level[0] = 1;
+    int max_level = 1;
+    size_t seen_leaf = 0;
+    for (size_t qi = 0; qi < queue.size(); ++qi) {
+        int o = queue[qi];
+        int l = oct_level[o];
+        if (l > 21) return fail(ctx, RASCAS_E_ARG, "octree: deeper than 21 levels");
+        max_level = l > max_level ? l : max_level;
+        for (int c = 0; c < 8; ++c) {
+            int ci[3] = {oct_org[3 * o] + (c & 1), oct_org[3 * o + 1] + ((c >> 1) & 1),
+                         oct_org[3 * o + 2] + ((c >> 2) & 1)};
+            int v = son[(size_t)8 * o + c];
+            if (v > 0) {
+                if (v >= noct || oct_level[v] != 0) return fail(ctx, RASCAS_E_ARG, "octree: bad or repeated oct link");
+                oct_level[v] = l + 1;
+                oct_father[v] = 8 * o + c;
+                for (int ax = 0; ax < 3; ++ax) oct_org[3 * (size_t)v + ax] = 2 * ci[ax];
+                queue.push_back(v);
+            } else if (v < 0) {
+                long long leaf = -(long long)v - 1;
+                if (leaf >= nleaf || lvl[leaf] != 0) return fail(ctx, RASCAS_E_ARG, "octree: bad or repeated leaf link");
+                lvl[leaf] = l;
+                for (int ax = 0; ax < 3; ++ax) ijk[3 * leaf + ax] = ci[ax];
+                ++seen_leaf;
+            } else {
+                return fail(ctx, RASCAS_E_ARG, "octree: son value 0");
+            }
+        }
+    }
+    if ((int)queue.size() != noct || (int)seen_leaf != nleaf)
+        return fail(ctx, RASCAS_E_ARG, "octree: unreachable octs or leaves");
+    // neighbour links: per oct the 6 cells (level l-1, or the deepest coarser
+    // cell when the tree is not graded) across the faces of its father cell,
+    // wrapped periodically; -1 for the root oct
+    auto find_cell = [&](int cx, int cy, int cz, int target, int& level_out) {
+        int o = 0;
+        for (int m = 1;; ++m) {
+            int s = target - m;
+            int child = ((cx >> s) & 1) | (((cy >> s) & 1) << 1) | (((cz >> s) & 1) << 2);
+            int cell = 8 * o + child;
+            int v = son[cell];
+            if (m == target || v < 0) {
+                level_out = m;
+                return cell;
+            }
+            o = v;
+        }
+    };
+    std::vector<int> nbr((size_t)8 * noct, -1);
+    for (int o = 0; o < noct; ++o) {
+        int l = oct_level[o];
+        int packed = 0;
+        nbr[8 * (size_t)o + 6] = oct_father[o];
+        if (l >= 2) {
+            int fl = l - 1;
+            int nf = 1 << fl;
+            int F[3] = {oct_org[3 * (size_t)o] >> 1, oct_org[3 * (size_t)o + 1] >> 1, oct_org[3 * (size_t)o + 2] >> 1};
+            for (int face = 0; face < 6; ++face) {
+                int ax = face >> 1;
+                int G[3] = {F[0], F[1], F[2]};
+                G[ax] = (G[ax] + ((face & 1) ? 1 : -1) + nf) & (nf - 1);
+                int nl = 0;
+                int cell = find_cell(G[0], G[1], G[2], fl, nl);
+                nbr[8 * (size_t)o + face] = cell;
+                packed |= (nl & 31) << (5 * face);
+            }
+        }
+        nbr[8 * (size_t)o + 7] = packed;
+    }
+    // dense top grid at level S: deepest cell at level <= S over each region
+    int S = max_level < 6 ? max_level : 6;
+    size_t ntop = (size_t)1 << (3 * S);
+    std::vector<int> top(4 * ntop, 0);
+    for (size_t r = 0; r < ntop; ++r) {
+        int cx = (int)(r & ((1u << S) - 1)), cy = (int)((r >> S) & ((1u << S) - 1)), cz = (int)(r >> (2 * S));
+        int o = 0;
+        for (int m = 1;; ++m) {
+            int s = S - m;
+            int child = ((cx >> s) & 1) | (((cy >> s) & 1) << 1) | (((cz >> s) & 1) << 2);
+            int v = son[8 * (size_t)o + child];
+            if (v < 0 || m == S) {
+                top[4 * r] = v;
+                top[4 * r + 1] = m;
+                top[4 * r + 2] = o;
+                break;
+            }
+            o = v;
+        }
+    }
+    // packed leaf records {n_HI, vx, vy, vz}, {T, n_dust, n_metal, flags}
+    ctx->rec.assign((size_t)8 * nleaf, 0.0f);
+    for (int i = 0; i < nleaf; ++i) {
+        float* r = &ctx->rec[8 * (size_t)i];
+        r[0] = f[0][i]; r[1] = f[1][i]; r[2] = f[2][i]; r[3] = f[3][i];
+        r[4] = f[4][i]; r[5] = f[5][i]; r[6] = f[6][i];
+    }
+    ctx->noct = noct;
+    ctx->nleaf = nleaf;
+    ctx->max_level = max_level;
+    ctx->top_level = S;
+    ctx->box_cm = t->box_cm;
+    ctx->leaf_level.swap(lvl);
+    ctx->leaf_ijk.swap(ijk);
+    ctx->has_metal = t->n_metal != nullptr;
+    leaf_flags(ctx);
+    CK(ctx->d_rec.ensure(ctx->rec.size() * 4));
+    CK(ctx->d_son.ensure(son.size() * 4));
+    CK(ctx->d_nbr.ensure(nbr.size() * 4));
+    CK(ctx->d_top.ensure(top.size() * 4));
+    CK(cudaMemcpy(ctx->d_rec.p, ctx->rec.data(), ctx->rec.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_son.p, son.data(), son.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_nbr.p, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_top.p, top.data(), top.size() * 4, cudaMemcpyHostToDevice));
+    Params& P = ctx->P;
+    P.rec = (const float4*)ctx->d_rec.p;
+    P.son = (const int*)ctx->d_son.p;
+    P.nbr = (const int4*)ctx->d_nbr.p;
+    P.top = (const int4*)ctx->d_top.p;
+    P.top_level = S;
+    P.max_level = max_level;
+    P.nleaf = nleaf;
+    P.noct = noct;
+    P.box_cm = t->box_cm;
+    ctx->has_mesh = true;
+    return RASCAS_OK;
+}
+
+int rascas_set_domain(rascas_ctx* ctx, const rascas_domain* d) {
+    if (!ctx || !d) return RASCAS_E_ARG;
+    if (d->kind < 0 || d->kind > 2 || !(d->size > 0.0)) return fail(ctx, RASCAS_E_ARG, "domain: bad kind or size");
+    ctx->dom = *d;
+    ctx->has_domain = true;
+    Params& P = ctx->P;
+    P.dom_kind = d->kind;
+    for (int ax = 0; ax < 3; ++ax) P.dom_c[ax] = d->centre[ax];
+    P.dom_R = d->size;
+    if (ctx->has_mesh) {
+        CK(cudaSetDevice(ctx->device));
+        leaf_flags(ctx);
+        CK(cudaMemcpy(ctx->d_rec.p, ctx->rec.data(), ctx->rec.size() * 4, cudaMemcpyHostToDevice));
+    }
+    return RASCAS_OK;
+}
+
+int rascas_set_lines(rascas_ctx* ctx, const rascas_line* lines, int32_t nline, const rascas_dust* dust) {
+    if (!ctx || nline < 1 || nline > RASCAS_MAX_LINES || !lines)
+        return fail(ctx, RASCAS_E_ARG, "lines: need 1..4 lines");
+    Params& P = ctx->P;
+    for (int i = 0; i < nline; ++i) {
+        const rascas_line& L = lines[i];
+        if (!(L.nu0 > 0 && L.A_ul > 0 && L.f_lu > 0 && L.mass_g > 0) || L.nchan < 1 || L.nchan > RASCAS_MAX_CHANNELS ||
+            (L.density != 0 && L.density != 1))
+            return fail(ctx, RASCAS_E_ARG, "lines: bad line data");
+        rg::LineDev& D = P.line[i];
+        D.nu0 = L.nu0;
+        double vp = std::sqrt(2.0 * kKB / L.mass_g);
+        D.vth_pref = vp;
+        D.invdnu_pref = kC / (L.nu0 * vp);
+        D.a_pref = (float)(L.A_ul * kC / (4.0 * kPi * L.nu0 * vp));
+        D.sig_pref = (float)(std::sqrt(kPi) * kE * kE * L.f_lu / (kME * L.nu0 * vp));
+        D.abund = (float)L.abundance;
+        D.recoil_pref = (float)(kH / (L.mass_g * kC * kC));
+        D.vth_over_c_pref = (float)(vp / kC);
+        D.dens = L.density;
+        D.phase = L.phase;
+        D.nchan = L.nchan;
+        double tot = 0.0;
+        for (int c = 0; c < L.nchan; ++c) tot += L.chan_A[c];
+        double acc = 0.0;
+        for (int c = 0; c < rg::kMaxChan; ++c) {
+            if (c < L.nchan) {
+                acc += L.chan_A[c];
+                D.chan_cum[c] = (float)(acc / tot);
+                D.chan_nu[c] = L.chan_nu[c];
+            } else {
+                D.chan_cum[c] = 1.0f;
+                D.chan_nu[c] = L.nu0;
+            }
+        }
+    }
+    P.nline = nline;
+    P.dust_sigma = dust ? (float)dust->sigma : 0.0f;
+    P.dust_albedo = dust ? (float)dust->albedo : 0.0f;
+    P.dust_g = dust ? (float)dust->g : 0.0f;
+    ctx->has_lines = true;
+    return RASCAS_OK;
+}
+
+int rascas_set_physics(rascas_ctx* ctx, const rascas_physics* ph) {
+    if (!ctx || !ph) return RASCAS_E_ARG;
+    if (!(ph->x_gauss > 0.0) || ph->max_scatt < 0 || ph->max_steps < 0 || !(ph->tau_stop > 0.0))
+        return fail(ctx, RASCAS_E_ARG, "physics: bad values");
+    ctx->phys = *ph;
+    Params& P = ctx->P;
+    P.recoil = ph->recoil;
+    P.isotropic = ph->isotropic;
+    P.keep_dir = ph->keep_dir;
+    P.x_gauss = (float)ph->x_gauss;
+    P.max_scatt = ph->max_scatt;
+    P.max_steps = ph->max_steps;
+    P.tau_stop = ph->tau_stop;
+    P.key0 = (uint32_t)ph->seed;
+    P.key1 = (uint32_t)(ph->seed >> 32);
+    ctx->has_phys = true;
+    return RASCAS_OK;
+}
+
+int rascas_set_detector(rascas_ctx* ctx, const rascas_detector* d) {
+    if (!ctx || !d) return RASCAS_E_ARG;
+    if (d->nbin < 1 || !(d->nu_hi > d->nu_lo) || d->ndir < 0 || d->ndir > RASCAS_MAX_DIRS || d->npix < 0 ||
+        (d->npix > 0 && !(d->fov > 0)))
+        return fail(ctx, RASCAS_E_ARG, "detector: bad values");
+    CK(cudaSetDevice(ctx->device));
+    ctx->det = *d;
+    Params& P = ctx->P;
+    P.nu_lo = d->nu_lo;
+    P.nu_inv_range = 1.0 / (d->nu_hi - d->nu_lo);
+    P.nbin = d->nbin;
+    P.ndir = d->ndir;
+    P.npix = d->npix;
+    P.cube = d->cube && d->npix > 0 && d->ndir > 0;
+    P.inv_fov = d->npix > 0 ? 1.0 / d->fov : 0.0;
+    for (int ax = 0; ax < 3; ++ax) P.img_c[ax] = d->centre[ax];
+    for (int i = 0; i < d->ndir; ++i) {
+        double n2 = d->dirs[i][0] * d->dirs[i][0] + d->dirs[i][1] * d->dirs[i][1] + d->dirs[i][2] * d->dirs[i][2];
+        if (!(n2 > 0)) return fail(ctx, RASCAS_E_ARG, "detector: zero direction");
+        double nn = std::sqrt(n2);
+        double n[3] = {d->dirs[i][0] / nn, d->dirs[i][1] / nn, d->dirs[i][2] / nn};
+        for (int ax = 0; ax < 3; ++ax) P.dirs[i][ax] = n[ax];
+        // image plane basis: Duff et al. (2017)
+        double sg = std::copysign(1.0, n[2]);
+        double a = -1.0 / (sg + n[2]);
+        double b = n[0] * n[1] * a;
+        P.eu[i][0] = 1.0 + sg * n[0] * n[0] * a;
+        P.eu[i][1] = sg * b;
+        P.eu[i][2] = -sg * n[0];
+        P.ev[i][0] = b;
+        P.ev[i][1] = sg + n[1] * n[1] * a;
+        P.ev[i][2] = -n[1];
+    }
+    size_t npix2 = (size_t)d->npix * d->npix;
+    CK(ctx->d_spec.ensure((size_t)d->nbin * 4));
+    CK(ctx->d_pspec.ensure((size_t)(d->ndir > 0 ? d->ndir : 1) * d->nbin * 4));
+    CK(ctx->d_pimg.ensure((size_t)(d->ndir > 0 ? d->ndir : 1) * (npix2 > 0 ? npix2 : 1) * 4));
+    if (P.cube) CK(ctx->d_pcube.ensure((size_t)d->ndir * npix2 * d->nbin * 4));
+    P.spec = (float*)ctx->d_spec.p;
+    P.pspec = (float*)ctx->d_pspec.p;
+    P.pimg = (float*)ctx->d_pimg.p;
+    P.pcube = P.cube ? (float*)ctx->d_pcube.p : nullptr;
+    ctx->has_det = true;
+    return rascas_zero_tallies(ctx);
+}
+
+int rascas_zero_tallies(rascas_ctx* ctx) {
+    if (!ctx) return RASCAS_E_ARG;
+    if (!ctx->has_det) return RASCAS_OK;
+    CK(cudaSetDevice(ctx->device));
+    const rascas_detector& d = ctx->det;
+    size_t npix2 = (size_t)d.npix * d.npix;
+    CK(cudaMemsetAsync(ctx->d_spec.p, 0, (size_t)d.nbin * 4, ctx->stream));
+    if (d.ndir > 0) {
+        CK(cudaMemsetAsync(ctx->d_pspec.p, 0, (size_t)d.ndir * d.nbin * 4, ctx->stream));
+        if (npix2) CK(cudaMemsetAsync(ctx->d_pimg.p, 0, (size_t)d.ndir * npix2 * 4, ctx->stream));
+        if (ctx->P.cube) CK(cudaMemsetAsync(ctx->d_pcube.p, 0, (size_t)d.ndir * npix2 * d.nbin * 4, ctx->stream));
+    }
+    return RASCAS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int check_ready(rascas_ctx* ctx) {
+    if (!ctx->has_mesh) return fail(ctx, RASCAS_E_STATE, "no octree loaded");
+    if (!ctx->has_domain) return fail(ctx, RASCAS_E_STATE, "no domain set");
+    if (!ctx->has_lines) return fail(ctx, RASCAS_E_STATE, "no lines set");
+    if (!ctx->has_phys) return fail(ctx, RASCAS_E_STATE, "no physics set");
+    if (ctx->P.nline > 0) {
+        for (int i = 0; i < ctx->P.nline; ++i)
+            if (ctx->P.line[i].dens == 1 && !ctx->has_metal)
+                return fail(ctx, RASCAS_E_STATE, "a line needs n_metal but the octree has none");
+    }
+    return RASCAS_OK;
+}
+
+// stage n packets from host into device buffers; returns device views
+struct Staged {
+    rg::PacketsIn in;
+    rg::PacketsOut out;
+};
+
+int persistent_grid(rascas_ctx* ctx, bool peel) {
+    int block = rg::propagate_block_size();
+    int per_sm = rg::propagate_blocks_per_sm(block, peel);
+    if (per_sm < 1) per_sm = 1;
+    return ctx->sms * per_sm;
+}
+
+int run_propagate(rascas_ctx* ctx, const rascas_packets_in* in, int64_t n, const rascas_packets_out* out,
+                  int mem, rascas_run_stats* stats, rascas_event* events, int32_t* nevents, int32_t max_events,
+                  bool tallies) {
+    if (!ctx || !in || n < 0 || (mem != RASCAS_HOST && mem != RASCAS_DEVICE)) return fail(ctx, RASCAS_E_ARG, "bad arguments");
+    if (n > 0 && (!in->pos || !in->dir || !in->nu || !in->id)) return fail(ctx, RASCAS_E_ARG, "packets: null array");
+    int r = check_ready(ctx);
+    if (r) return r;
+    CK(cudaSetDevice(ctx->device));
+    Params P = ctx->P;
+    if (!tallies || !ctx->has_det) {
+        P.spec = nullptr;
+        P.ndir = 0;
+        if (!ctx->has_det) {
+            P.nbin = 1;
+            P.nu_lo = 0.0;
+            P.nu_inv_range = 0.0;
+        }
+    }
+    rg::PacketsIn din{in->pos, in->dir, in->nu, in->id, (long long)n};
+    rg::PacketsOut dout{};
+    if (out) dout = rg::PacketsOut{out->status, out->nscatt, out->nu, out->pos, out->dir, out->path};
+    rg::TraceOut tr{nullptr, nullptr, max_events};
+    cudaStream_t st = ctx->stream;
+    const size_t N = (size_t)n;
+    if (mem == RASCAS_HOST && n > 0) {
+        size_t bin = N * (3 + 3 + 1 + 1) * 8;
+        CK(ctx->stage_in.ensure(bin));
+        char* b = (char*)ctx->stage_in.p;
+        double* pos = (double*)b;
+        double* dir = pos + 3 * N;
+        double* nu = dir + 3 * N;
+        uint64_t* id = (uint64_t*)(nu + N);
+        CK(cudaMemcpyAsync(pos, in->pos, 3 * N * 8, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(dir, in->dir, 3 * N * 8, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(nu, in->nu, N * 8, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(id, in->id, N * 8, cudaMemcpyHostToDevice, st));
+        din = rg::PacketsIn{pos, dir, nu, id, (long long)n};
+        if (out) {
+            size_t bout = N * (4 + 8 + 8 + 24 + 24 + 8) + 64;
+            CK(ctx->stage_out.ensure(bout));
+            char* o = (char*)ctx->stage_out.p;
+            double* onu = (double*)o;
+            double* opos = onu + N;
+            double* odir = opos + 3 * N;
+            double* opath = odir + 3 * N;
+            int64_t* ons = (int64_t*)(opath + N);
+            int32_t* ost = (int32_t*)(ons + N);
+            dout = rg::PacketsOut{out->status ? ost : nullptr, out->nscatt ? ons : nullptr, out->nu ? onu : nullptr,
+                                  out->pos ? opos : nullptr, out->dir ? odir : nullptr, out->path ? opath : nullptr};
+        }
+        if (events) {
+            size_t bev = N * (size_t)max_events * sizeof(rg::TraceEvent) + N * 4;
+            CK(ctx->stage_aux.ensure(bev));
+            tr.ev = (rg::TraceEvent*)ctx->stage_aux.p;
+            tr.nev = (int32_t*)((char*)ctx->stage_aux.p + N * (size_t)max_events * sizeof(rg::TraceEvent));
+        }
+    } else if (events) {
+        tr.ev = (rg::TraceEvent*)events;
+        tr.nev = nevents;
+    }
+    if (tr.nev) CK(cudaMemsetAsync(tr.nev, 0, N * 4, st));
+    CK(cudaMemsetAsync(ctx->d_counters.p, 0, sizeof(unsigned long long) * (rg::CNT_N + 1), st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (stats) {
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventRecord(e0, st));
+    }
+    if (n > 0) {
+        int grid = persistent_grid(ctx, P.ndir > 0);
+        CK(rg::launch_propagate(P, din, dout, tr, grid, rg::propagate_block_size(), st));
+    }
+    if (stats) CK(cudaEventRecord(e1, st));
+    if (mem == RASCAS_HOST && n > 0) {
+        if (out) {
+            if (out->status) CK(cudaMemcpyAsync(out->status, dout.status, N * 4, cudaMemcpyDeviceToHost, st));
+            if (out->nscatt) CK(cudaMemcpyAsync(out->nscatt, dout.nscatt, N * 8, cudaMemcpyDeviceToHost, st));
+            if (out->nu) CK(cudaMemcpyAsync(out->nu, dout.nu, N * 8, cudaMemcpyDeviceToHost, st));
+            if (out->pos) CK(cudaMemcpyAsync(out->pos, dout.pos, 3 * N * 8, cudaMemcpyDeviceToHost, st));
+            if (out->dir) CK(cudaMemcpyAsync(out->dir, dout.dir, 3 * N * 8, cudaMemcpyDeviceToHost, st));
+            if (out->path) CK(cudaMemcpyAsync(out->path, dout.path, N * 8, cudaMemcpyDeviceToHost, st));
+        }
+        if (events) {
+            CK(cudaMemcpyAsync(events, tr.ev, N * (size_t)max_events * sizeof(rg::TraceEvent), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(nevents, tr.nev, N * 4, cudaMemcpyDeviceToHost, st));
+        }
+    }
+    unsigned long long cnt[rg::CNT_N] = {};
+    if (stats || mem == RASCAS_HOST || ctx->phys.fail_on_cap) {
+        CK(cudaMemcpyAsync(cnt, ctx->d_counters.p, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    if (stats) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        stats->packets = (int64_t)cnt[rg::CNT_PACKETS];
+        stats->escaped = (int64_t)cnt[rg::CNT_ESCAPED];
+        stats->absorbed = (int64_t)cnt[rg::CNT_ABSORBED];
+        stats->capped = (int64_t)cnt[rg::CNT_CAPPED];
+        stats->errors = (int64_t)cnt[rg::CNT_ERRORS];
+        stats->nscatt_line = (int64_t)cnt[rg::CNT_SCATT_LINE];
+        stats->nscatt_dust = (int64_t)cnt[rg::CNT_SCATT_DUST];
+        stats->ncross = (int64_t)cnt[rg::CNT_CROSS];
+        stats->npeel_rays = (int64_t)cnt[rg::CNT_PEEL_RAYS];
+        stats->npeel_cells = (int64_t)cnt[rg::CNT_PEEL_CELLS];
+        stats->upar_trials = (int64_t)cnt[rg::CNT_UPAR_TRIALS];
+        stats->leaf_loads = (int64_t)cnt[rg::CNT_LEAF_LOADS];
+        stats->son_loads = (int64_t)cnt[rg::CNT_SON_LOADS];
+        stats->nbor_loads = (int64_t)cnt[rg::CNT_NBOR_LOADS];
+        stats->kernel_ms = ms;
+    }
+    if (ctx->phys.fail_on_cap && cnt[rg::CNT_CAPPED] > 0)
+        return fail(ctx, RASCAS_E_CAPPED, "some packets reached a cap");
+    return RASCAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rascas_propagate(rascas_ctx* ctx, const rascas_packets_in* in, int64_t n, const rascas_packets_out* out, int mem,
+                     rascas_run_stats* stats) {
+    return run_propagate(ctx, in, n, out, mem, stats, nullptr, nullptr, 0, true);
+}
+
+int rascas_trace(rascas_ctx* ctx, const rascas_packets_in* in, int64_t n, int32_t max_events, rascas_event* events,
+                 int32_t* nevents, int mem) {
+    if (!ctx || max_events < 1 || !events || !nevents) return fail(ctx, RASCAS_E_ARG, "trace: bad arguments");
+    static_assert(sizeof(rascas_event) == sizeof(rg::TraceEvent), "event layout");
+    return run_propagate(ctx, in, n, nullptr, mem, nullptr, events, nevents, max_events, false);
+}
+
+int rascas_get_tally(rascas_ctx* ctx, int kind, float* dst, size_t count, int mem) {
+    if (!ctx || !dst) return RASCAS_E_ARG;
+    if (!ctx->has_det) return fail(ctx, RASCAS_E_STATE, "no detector set");
+    const rascas_detector& d = ctx->det;
+    size_t npix2 = (size_t)d.npix * d.npix;
+    const void* src = nullptr;
+    size_t need = 0;
+    switch (kind) {
+        case RASCAS_TALLY_SPECTRUM: src = ctx->d_spec.p; need = d.nbin; break;
+        case RASCAS_TALLY_PEEL_SPECTRA: src = ctx->d_pspec.p; need = (size_t)d.ndir * d.nbin; break;
+        case RASCAS_TALLY_PEEL_IMAGES: src = ctx->d_pimg.p; need = (size_t)d.ndir * npix2; break;
+        case RASCAS_TALLY_PEEL_CUBES: src = ctx->P.cube ? ctx->d_pcube.p : nullptr; need = (size_t)d.ndir * npix2 * d.nbin; break;
+        default: return fail(ctx, RASCAS_E_ARG, "tally: unknown kind");
+    }
+    if (!src || need == 0) return fail(ctx, RASCAS_E_STATE, "tally: not accumulated by this detector");
+    if (count != need) return fail(ctx, RASCAS_E_ARG, "tally: count does not match the detector shape");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemcpyAsync(dst, src, need * 4, mem == RASCAS_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    if (mem != RASCAS_DEVICE) CK(cudaStreamSynchronize(ctx->stream));
+    return RASCAS_OK;
+}
+
+int rascas_ray_tau(rascas_ctx* ctx, int64_t n, const double* pos, const double* dir, const double* nu, double* tau,
+                   int32_t* cells, double* lens, int32_t cap, int32_t* ncell, int mem) {
+    if (!ctx || n < 0 || !pos || !dir || !nu || !tau || cap < 0 || ((cells || lens) && (!cells || !lens || cap == 0)))
+        return fail(ctx, RASCAS_E_ARG, "ray_tau: bad arguments");
+    int r = check_ready(ctx);
+    if (r) return r;
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const size_t N = (size_t)n;
+    if (n == 0) return RASCAS_OK;
+    const double *dpos = pos, *ddir = dir, *dnu = nu;
+    double *dtau = tau, *dlens = lens;
+    int32_t *dcells = cells, *dncell = ncell;
+    if (mem == RASCAS_HOST) {
+        size_t b = N * 8 * 8 + N * 4 + (cells ? N * (size_t)cap * 12 : 0) + 64;
+        CK(ctx->stage_aux.ensure(b));
+        char* p = (char*)ctx->stage_aux.p;
+        double* a = (double*)p;
+        dpos = a; ddir = a + 3 * N; dnu = a + 6 * N; dtau = a + 7 * N;
+        dncell = (int32_t*)(a + 8 * N);
+        char* q = (char*)(dncell + N);
+        q = (char*)(((uintptr_t)q + 15) & ~(uintptr_t)15);
+        dlens = cells ? (double*)q : nullptr;
+        dcells = cells ? (int32_t*)(q + N * (size_t)cap * 8) : nullptr;
+        CK(cudaMemcpyAsync((void*)dpos, pos, 3 * N * 8, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync((void*)ddir, dir, 3 * N * 8, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync((void*)dnu, nu, N * 8, cudaMemcpyHostToDevice, st));
+    }
+    CK(rg::launch_ray_tau(ctx->P, (long long)n, dpos, ddir, dnu, dtau, dcells, dlens, cap,
+                          (mem == RASCAS_HOST || ncell) ? dncell : nullptr, st));
+    if (mem == RASCAS_HOST) {
+        CK(cudaMemcpyAsync(tau, dtau, N * 8, cudaMemcpyDeviceToHost, st));
+        if (ncell) CK(cudaMemcpyAsync(ncell, dncell, N * 4, cudaMemcpyDeviceToHost, st));
+        if (cells) {
+            CK(cudaMemcpyAsync(cells, dcells, N * (size_t)cap * 4, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(lens, dlens, N * (size_t)cap * 8, cudaMemcpyDeviceToHost, st));
+        }
+        CK(cudaStreamSynchronize(st));
+    }
+    return RASCAS_OK;
+}
+
+int rascas_eval_voigt(rascas_ctx* ctx, int64_t n, const float* a, const double* x, float* H, int mem) {
+    if (!ctx || n < 0 || !a || !x || !H) return fail(ctx, RASCAS_E_ARG, "eval_voigt: bad arguments");
+    CK(cudaSetDevice(ctx->device));
+    const size_t N = (size_t)n;
+    if (n == 0) return RASCAS_OK;
+    cudaStream_t st = ctx->stream;
+    if (mem == RASCAS_HOST) {
+        CK(ctx->stage_aux.ensure(N * 16 + 64));
+        double* dx = (double*)ctx->stage_aux.p;
+        float* da = (float*)(dx + N);
+        float* dH = da + N;
+        CK(cudaMemcpyAsync(dx, x, N * 8, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(da, a, N * 4, cudaMemcpyHostToDevice, st));
+        CK(rg::launch_eval_voigt((long long)n, da, dx, dH, st));
+        CK(cudaMemcpyAsync(H, dH, N * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return RASCAS_OK;
+    }
+    CK(rg::launch_eval_voigt((long long)n, a, x, H, st));
+    return RASCAS_OK;
+}
+
+int rascas_sample_upar(rascas_ctx* ctx, int64_t n, const double* x, const float* a, const uint64_t* id, float* u,
+                       int32_t* ndraw, int mem) {
+    if (!ctx || n < 0 || !x || !a || !id || !u || !ndraw) return fail(ctx, RASCAS_E_ARG, "sample_upar: bad arguments");
+    if (!ctx->has_phys) return fail(ctx, RASCAS_E_STATE, "no physics set");
+    CK(cudaSetDevice(ctx->device));
+    const size_t N = (size_t)n;
+    if (n == 0) return RASCAS_OK;
+    cudaStream_t st = ctx->stream;
+    if (mem == RASCAS_HOST) {
+        CK(ctx->stage_aux.ensure(N * 28 + 64));
+        double* dx = (double*)ctx->stage_aux.p;
+        uint64_t* did = (uint64_t*)(dx + N);
+        float* da = (float*)(did + N);
+        float* du = da + N;
+        int32_t* dn = (int32_t*)(du + N);
+        CK(cudaMemcpyAsync(dx, x, N * 8, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(did, id, N * 8, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(da, a, N * 4, cudaMemcpyHostToDevice, st));
+        CK(rg::launch_sample_upar(ctx->P, (long long)n, dx, da, did, du, dn, st));
+        CK(cudaMemcpyAsync(u, du, N * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ndraw, dn, N * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return RASCAS_OK;
+    }
+    CK(rg::launch_sample_upar(ctx->P, (long long)n, x, a, id, u, ndraw, st));
+    return RASCAS_OK;
+}
+
+}  // extern "C"

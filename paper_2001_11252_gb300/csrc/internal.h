@@ -1,0 +1,126 @@
+// Internal types shared by the host side (host.cpp) and the kernels (kernels.cu)
+// of the GB300 resonant-line Monte Carlo library.  Not part of the C ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rg {
+
+constexpr int kMaxLines = 4;
+constexpr int kMaxChan = 4;
+constexpr int kMaxDirs = 8;
+
+// per-packet status values (same numbers as RASCAS_PK_* of the C ABI)
+constexpr int RASCAS_PK_ACTIVE_ = 0;
+constexpr int RASCAS_PK_ESCAPED_ = 1;
+constexpr int RASCAS_PK_ABSORBED_ = 2;
+constexpr int RASCAS_PK_CAPPED_ = 3;
+constexpr int RASCAS_PK_ERROR_ = 4;
+
+// leaf flags (bits of the 8th word of the leaf record)
+constexpr int kFlagBorder = 1;   // the leaf touches or crosses the domain border
+
+// counters accumulated by the kernels (u64 each)
+enum Counter {
+    CNT_PACKETS = 0, CNT_ESCAPED, CNT_ABSORBED, CNT_CAPPED, CNT_ERRORS,
+    CNT_SCATT_LINE, CNT_SCATT_DUST, CNT_CROSS, CNT_PEEL_RAYS, CNT_PEEL_CELLS,
+    CNT_UPAR_TRIALS, CNT_LEAF_LOADS, CNT_SON_LOADS, CNT_NBOR_LOADS,
+    CNT_N
+};
+
+struct LineDev {
+    double nu0;          // rest frequency (Hz)
+    double vth_pref;     // sqrt(2 k_B / m): v_th = vth_pref * sqrt(T)
+    double invdnu_pref;  // c / nu0 / vth_pref: 1/Delta nu_D = invdnu_pref / sqrt(T)
+    float a_pref;        // A_ul / (4 pi nu0 / c * vth_pref): a = a_pref / sqrt(T)
+    float sig_pref;      // sqrt(pi) e^2 f / (m_e c) * c / (nu0 vth_pref): sigma0 = sig_pref / sqrt(T)
+    float abund;         // density multiplier
+    float recoil_pref;   // h / (m c^2): recoil term = (1 - mu) * h nu / (m c^2)
+    float vth_over_c_pref; // vth_pref / c
+    int dens;            // 0: n_HI, 1: n_metal
+    int phase;           // 0: Lya core/wing, 1: isotropic
+    int nchan;
+    float chan_cum[kMaxChan];  // cumulative A_i / sum A
+    double chan_nu[kMaxChan];
+};
+
+struct Params {
+    // mesh (device)
+    const float4* rec;     // [2*nleaf]: {n_HI, vx, vy, vz}, {T, n_dust, n_metal, flags}
+    const int* son;        // [8*noct]
+    const int4* nbr;       // [2*noct]: {nb0, nb1, nb2, nb3}, {nb4, nb5, father, packed levels}
+    const int4* top;       // [(2^S)^3]: {code, level, oct, 0}
+    int top_level, max_level, nleaf, noct;
+    double box_cm;
+    // domain
+    int dom_kind;
+    double dom_c[3];
+    double dom_R;
+    // opacity sources
+    int nline;
+    LineDev line[kMaxLines];
+    float dust_sigma, dust_albedo, dust_g;
+    // physics
+    int recoil, isotropic, keep_dir;
+    float x_gauss;
+    long long max_scatt, max_steps;
+    double tau_stop;
+    uint32_t key0, key1;
+    // detector
+    double nu_lo, nu_inv_range;
+    int nbin, ndir, npix, cube;
+    double dirs[kMaxDirs][3];
+    double eu[kMaxDirs][3], ev[kMaxDirs][3];
+    double img_c[3];
+    double inv_fov;
+    float* spec;
+    float* pspec;
+    float* pimg;
+    float* pcube;
+    // run scratch
+    unsigned long long* counters;  // [CNT_N]
+    unsigned long long* head;      // work-queue head
+};
+
+struct PacketsIn {
+    const double* pos;
+    const double* dir;
+    const double* nu;
+    const uint64_t* id;
+    long long n;
+};
+
+struct PacketsOut {
+    int32_t* status;
+    int64_t* nscatt;
+    double* nu;
+    double* pos;
+    double* dir;
+    double* path;
+};
+
+struct TraceEvent {  // mirrors rascas_event
+    double p[3], k[3], nu;
+    int32_t leaf, level, ijk[3], status;
+    int64_t ndraw, nscatt, nsteps;
+};
+
+struct TraceOut {
+    TraceEvent* ev;     // [n][max_events] or null
+    int32_t* nev;       // [n]
+    int max_events;
+};
+
+// launchers (kernels.cu)
+cudaError_t launch_propagate(const Params& P, const PacketsIn& in, const PacketsOut& out,
+                             const TraceOut& tr, int grid, int block, cudaStream_t st);
+cudaError_t launch_ray_tau(const Params& P, long long n, const double* pos, const double* dir,
+                           const double* nu, double* tau, int32_t* cells, double* lens, int cap,
+                           int32_t* ncell, cudaStream_t st);
+cudaError_t launch_eval_voigt(long long n, const float* a, const double* x, float* H, cudaStream_t st);
+cudaError_t launch_sample_upar(const Params& P, long long n, const double* x, const float* a,
+                               const uint64_t* id, float* u, int32_t* ndraw, cudaStream_t st);
+int propagate_block_size();
+int propagate_blocks_per_sm(int block, bool peel);
+
+}  // namespace rg

@@ -1,0 +1,46 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+symbol include/rascas_gb300.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rascas_gb300.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rascas_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ["rascas_create", "rascas_destroy", "rascas_load_octree", "rascas_set_domain",
+                 "rascas_set_lines", "rascas_set_physics", "rascas_set_detector", "rascas_propagate",
+                 "rascas_get_tally", "rascas_ray_tau", "rascas_trace", "rascas_last_error"]:
+        assert must in names
+
+
+def test_library_loads_and_exports_all_symbols():
+    from paper_2001_11252_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (rascas_\w+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_binding_fails_loudly_without_gpu():
+    """No CPU fallback: without a CUDA device context creation raises."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2001_11252_gb300 as rg
+    with pytest.raises(Exception):
+        rg.Context(0)
