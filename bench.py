@@ -200,17 +200,14 @@ def main():
             flush.zero_()
             e0, e1 = evs[i]
             e0.record(stream)
-            st = ctx.propagate(*inputs[args.warmup + i][1], stats=False)
+            st = ctx.propagate(*inputs[args.warmup + i][1], stats=True)
             e1.record(stream)
+            stats_all.append(st)
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    # counts of the timed steps (re-read from a stats run of the same packets)
     t_ms = sum(step_ms)
-    for i in range(args.steps):
-        st = ctx.propagate(*inputs[args.warmup + i][1], stats=True)
-        stats_all.append(st)
     scatt = sum(s["nscatt_line"] + s["nscatt_dust"] for s in stats_all)
     pk_done = sum(s["packets"] for s in stats_all)
     loads = sum(s["leaf_loads"] for s in stats_all)

@@ -112,6 +112,12 @@ __device__ __forceinline__ float u0_fit(float x, float a) {
     return fmaxf(u0, 0.0f);
 }
 
+// The two branches of the comparison function are sampled through their
+// angular variable theta = atan((u - x)/a): branch 1 covers theta in
+// (-pi/2, theta0], branch 2 (theta0, pi/2).  In FP32 theta itself cannot
+// resolve the poles, so the code works with the distances to the poles,
+// A = theta0 + pi/2 and B = pi/2 - theta0 (formed without cancellation), and
+// u = x - a / tan(A r) or u = x + a / tan(B (1 - r)).
 __device__ __forceinline__ float sample_upar(Rng& rng, float x, float a, float x_gauss,
                                              uint32_t& trials, bool& err) {
     float sg = x < 0.0f ? -1.0f : 1.0f;
@@ -122,23 +128,31 @@ __device__ __forceinline__ float sample_upar(Rng& rng, float x, float a, float x
         return sg * (1.0f / xa + sqrtf(-logf(r1)) * cospif(2.0f * r2));
     }
     float u0 = u0_fit(xa, a);
-    float th0 = atanf((u0 - xa) / a);
+    float t = (u0 - xa) / a;
+    float A, B;
+    if (t < 0.0f) {
+        A = atanf(-1.0f / t);
+        B = kPiF - A;
+    } else if (t > 0.0f) {
+        B = atanf(1.0f / t);
+        A = kPiF - B;
+    } else {
+        A = B = 0.5f * kPiF;
+    }
     float e0 = expf(-u0 * u0);
-    const float hp = 0.5f * kPiF;
-    float p = (th0 + hp) / ((1.0f - e0) * th0 + (1.0f + e0) * hp);
+    float p = A / (A + e0 * B);
     float u0sq = u0 * u0;
-    for (uint32_t t = 0; t < (1u << 22); ++t) {
+    for (uint32_t n = 0; n < (1u << 22); ++n) {
         float r1 = rng.u24(), r2 = rng.u24(), r3 = rng.u24();
         ++trials;
-        float th, lim;
+        float u, lim;
         if (r1 <= p) {
-            th = -hp + (th0 + hp) * r2;
+            u = xa - a / tanf(A * r2);
             lim = 0.0f;
         } else {
-            th = th0 + (hp - th0) * r2;
+            u = xa + a / tanf(B * (1.0f - r2));
             lim = u0sq;
         }
-        float u = a * tanf(th) + xa;
         if (r3 <= expf(lim - u * u)) return sg * u;
     }
     err = true;
@@ -151,22 +165,34 @@ __device__ __forceinline__ float sample_upar(Rng& rng, float x, float a, float x
 // ---------------------------------------------------------------------------
 enum { PH_ISO = 0, PH_CORE = 1, PH_WING = 2, PH_HG = 3 };
 
-__device__ __forceinline__ float mu_sample(int kind, float r, float g) {
+// mu and sin(theta) = sqrt(1 - mu^2), the latter formed from (1 - mu)(1 + mu)
+// so that it stays accurate near forward / backward scattering
+__device__ __forceinline__ float mu_sample(int kind, float r, float g, float& st) {
+    float mu;
     if (kind == PH_CORE) {
         float B = 6.0f * (2.0f * r - 1.0f);
         float A = sqrtf(B * B + 49.296296296296296f);  // 11^3 / 27
-        return cbrtf(A + B) - cbrtf(A - B);
-    }
-    if (kind == PH_WING) {
+        mu = cbrtf(A + B) - cbrtf(A - B);
+    } else if (kind == PH_WING) {
         float B = 4.0f * r - 2.0f;
         float A = sqrtf(B * B + 1.0f);
-        return cbrtf(A + B) - cbrtf(A - B);
-    }
-    if (kind == PH_HG && g != 0.0f) {
+        mu = cbrtf(A + B) - cbrtf(A - B);
+    } else if (kind == PH_HG && g != 0.0f) {
         float t = (1.0f - g * g) / (1.0f - g + 2.0f * g * r);
-        return fminf(1.0f, fmaxf(-1.0f, (1.0f + g * g - t * t) / (2.0f * g)));
+        float inv2g = 0.5f / g;
+        float omu = (t - (1.0f - g)) * (t + (1.0f - g)) * inv2g;   // 1 - mu
+        float opu = ((1.0f + g) - t) * ((1.0f + g) + t) * inv2g;   // 1 + mu
+        omu = fminf(2.0f, fmaxf(0.0f, omu));
+        opu = fminf(2.0f, fmaxf(0.0f, opu));
+        st = sqrtf(omu * opu);
+        return fminf(1.0f, fmaxf(-1.0f, 1.0f - omu));
+    } else {
+        st = 2.0f * sqrtf(r * (1.0f - r));
+        return 2.0f * r - 1.0f;
     }
-    return 2.0f * r - 1.0f;
+    mu = fminf(1.0f, fmaxf(-1.0f, mu));
+    st = sqrtf(fmaxf(0.0f, (1.0f - mu) * (1.0f + mu)));
+    return mu;
 }
 
 // phase function per unit mu (integrates to one over [-1, 1])
@@ -286,7 +312,8 @@ __device__ __forceinline__ bool next_leaf(const Params& P, const double p[3], co
         return true;
     }
     if (l >= 2) {
-        int face = 2 * axis + (k[axis] > 0.0 ? 1 : 0);
+        const bool up = axis == 0 ? k[0] > 0.0 : (axis == 1 ? k[1] > 0.0 : k[2] > 0.0);
+        int face = 2 * axis + (up ? 1 : 0);
         int4 a = __ldg(P.nbr + 2 * w.oct);
         int4 b = __ldg(P.nbr + 2 * w.oct + 1);
         ++nbor_loads;
@@ -296,8 +323,9 @@ __device__ __forceinline__ bool next_leaf(const Params& P, const double p[3], co
             // coordinates of the neighbour cell at its level nl (<= l - 1)
             int f[3] = {fi, fj, fk};
             int nf = 1 << (l - 1);
-            f[axis] += (k[axis] > 0.0 ? 1 : -1);
-            f[axis] = (f[axis] + nf) & (nf - 1);
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax)
+                if (ax == axis) f[ax] = (f[ax] + (up ? 1 : -1) + nf) & (nf - 1);
             int d = (l - 1) - nl;
             int s2 = L - nl;
             if ((t[0] >> s2) == (f[0] >> d) && (t[1] >> s2) == (f[1] >> d) && (t[2] >> s2) == (f[2] >> d)) {
@@ -315,8 +343,8 @@ __device__ __forceinline__ bool next_leaf(const Params& P, const double p[3], co
 // oracle's (face - p) * (1/k)); axis = crossed axis, ties to the lowest axis
 __device__ __forceinline__ double face_distance(const double p[3], const double k[3],
                                                 const double inv[3], const Where& w, int& axis) {
-    double h = __dmul_rn(1.0, ldexp(1.0, -w.level));
-    int c[3] = {w.i, w.j, w.k};
+    double h = ldexp(1.0, -w.level);
+    const int c[3] = {w.i, w.j, w.k};
     double best = __longlong_as_double(0x7ff0000000000000ULL);  // +inf
     int ba = -1;
 #pragma unroll
@@ -379,12 +407,12 @@ __device__ __forceinline__ double inner_distance(const double p[3], const Where&
 __device__ __forceinline__ void move_to_face(double p[3], const double k[3], int axis, double t,
                                              const Where& w) {
     double h = ldexp(1.0, -w.level);
-    int c[3] = {w.i, w.j, w.k};
-    double face = __dmul_rn((double)(k[axis] > 0.0 ? c[axis] + 1 : c[axis]), h);
+    const int c[3] = {w.i, w.j, w.k};
 #pragma unroll
-    for (int ax = 0; ax < 3; ++ax)
-        if (ax != axis) p[ax] = __fma_rn(t, k[ax], p[ax]);
-    p[axis] = face;
+    for (int ax = 0; ax < 3; ++ax) {
+        if (ax == axis) p[ax] = __dmul_rn((double)(k[ax] > 0.0 ? c[ax] + 1 : c[ax]), h);
+        else p[ax] = __fma_rn(t, k[ax], p[ax]);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -64,7 +64,7 @@ struct rascas_ctx {
     rascas_physics phys{};
     rascas_detector det{};
     Params P{};
-    DevBuf d_spec, d_pspec, d_pimg, d_pcube, d_counters;
+    DevBuf d_spec, d_pspec, d_pimg, d_pcube, d_counters, d_params;
     DevBuf stage_in, stage_out, stage_aux;
 };
 
@@ -146,10 +146,13 @@ int rascas_create(rascas_ctx** out, int device) {
         return RASCAS_E_CUDA;
     }
     cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
-    if (ctx->d_counters.ensure(sizeof(unsigned long long) * (rg::CNT_N + 1)) != cudaSuccess) {
+    if (ctx->d_counters.ensure(sizeof(unsigned long long) * (rg::CNT_N + 1)) != cudaSuccess ||
+        ctx->d_params.ensure(sizeof(Params)) != cudaSuccess) {
+        ctx->d_counters.release();
         delete ctx;
         return RASCAS_E_OOM;
     }
+    ctx->P.self = (const Params*)ctx->d_params.p;
     ctx->P.counters = (unsigned long long*)ctx->d_counters.p;
     ctx->P.head = ctx->P.counters + rg::CNT_N;
     ctx->P.tau_stop = 50.0;
@@ -163,8 +166,8 @@ int rascas_destroy(rascas_ctx* ctx) {
     if (!ctx) return RASCAS_E_ARG;
     cudaSetDevice(ctx->device);
     for (DevBuf* b : {&ctx->d_rec, &ctx->d_son, &ctx->d_nbr, &ctx->d_top, &ctx->d_spec, &ctx->d_pspec,
-                      &ctx->d_pimg, &ctx->d_pcube, &ctx->d_counters, &ctx->stage_in, &ctx->stage_out,
-                      &ctx->stage_aux})
+                      &ctx->d_pimg, &ctx->d_pcube, &ctx->d_counters, &ctx->d_params, &ctx->stage_in,
+                      &ctx->stage_out, &ctx->stage_aux})
         b->release();
     delete ctx;
     return RASCAS_OK;
@@ -565,6 +568,7 @@ int run_propagate(rascas_ctx* ctx, const rascas_packets_in* in, int64_t n, const
         CK(cudaEventCreate(&e1));
         CK(cudaEventRecord(e0, st));
     }
+    CK(cudaMemcpyAsync(ctx->d_params.p, &P, sizeof(Params), cudaMemcpyHostToDevice, st));
     if (n > 0) {
         int grid = persistent_grid(ctx, P.ndir > 0);
         CK(rg::launch_propagate(P, din, dout, tr, grid, rg::propagate_block_size(), st));
@@ -682,6 +686,7 @@ int rascas_ray_tau(rascas_ctx* ctx, int64_t n, const double* pos, const double* 
         CK(cudaMemcpyAsync((void*)ddir, dir, 3 * N * 8, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync((void*)dnu, nu, N * 8, cudaMemcpyHostToDevice, st));
     }
+    CK(cudaMemcpyAsync(ctx->d_params.p, &ctx->P, sizeof(Params), cudaMemcpyHostToDevice, st));
     CK(rg::launch_ray_tau(ctx->P, (long long)n, dpos, ddir, dnu, dtau, dcells, dlens, cap,
                           (mem == RASCAS_HOST || ncell) ? dncell : nullptr, st));
     if (mem == RASCAS_HOST) {

@@ -45,6 +45,7 @@ struct LineDev {
 };
 
 struct Params {
+    const Params* self;    // device-side copy of these parameters (read by the peeling walk)
     // mesh (device)
     const float4* rec;     // [2*nleaf]: {n_HI, vx, vy, vz}, {T, n_dust, n_metal, flags}
     const int* son;        // [8*noct]

@@ -7,6 +7,12 @@
 // refills itself from a global work queue with one warp-aggregated atomic, so
 // packets with 1 or 1e6 scatterings share the machine without tail effects
 // (the role of the master-worker bundles of Sect. 4.4).
+//
+// The packet state lives in registers: every function on the per-step path is
+// inlined and indexes its arrays with compile-time constants (the loops over
+// lines and peeling directions are unrolled).  The peeling ray walk, which is
+// long and called from several places, is a separate function that reads the
+// problem description through a device-side copy of the parameters.
 #include <cstdint>
 #include <cuda_runtime.h>
 #include "device.cuh"
@@ -24,51 +30,59 @@ struct Tallies {
 
 template <int NL>
 struct Packet {
-    double p[3], k[3], inv[3];
-    double nu;     // gas-frame frequency in the current leaf
-    double tau;    // optical depth left to the next interaction
+    double p0, p1, p2;     // position (box units)
+    double k0, k1, k2;     // direction
+    double i0, i1, i2;     // 1/k per axis (valid when inv_ok)
+    double nu;             // gas-frame frequency in the current leaf
+    double tau;            // optical depth left to the next interaction
     double path;
     long long idx;
     long long nscatt, nsteps;
     Where w;
     Rng rng;
-    float budget;  // path length guaranteed to stay inside the leaf
+    float budget;          // path length guaranteed to stay inside the leaf
     int status;
-    int zero_run;  // consecutive zero-length crossings (guards against a stuck walk)
+    int zero_run;          // consecutive zero-length crossings (guards against a stuck walk)
     bool inv_ok;
     CellCache<NL> cc;
 };
 
-__device__ __forceinline__ void dir_from(float kx, float ky, float kz, float mu, float r_phi, double out[3]) {
+__device__ __forceinline__ void dir_from(float kx, float ky, float kz, float mu, float st, float r_phi,
+                                         double& o0, double& o1, double& o2) {
     float3 e1, e2;
     onb(kx, ky, kz, e1, e2);
-    float st = sqrtf(fmaxf(0.0f, 1.0f - mu * mu));
     float s, c;
     sincospif(2.0f * r_phi, &s, &c);
     float ox = mu * kx + st * (c * e1.x + s * e2.x);
     float oy = mu * ky + st * (c * e1.y + s * e2.y);
     float oz = mu * kz + st * (c * e1.z + s * e2.z);
-    float nn = 1.0f / sqrtf(ox * ox + oy * oy + oz * oz);
-    out[0] = (double)(ox * nn);
-    out[1] = (double)(oy * nn);
-    out[2] = (double)(oz * nn);
+    float nn = rsqrtf(ox * ox + oy * oy + oz * oz);
+    o0 = (double)(ox * nn);
+    o1 = (double)(oy * nn);
+    o2 = (double)(oz * nn);
 }
 
 // ---------------------------------------------------------------------------
-// peeling ray: optical depth from p (in leaf w) along direction d to the
-// domain border at external frequency nu_ext; stops once tau > tau_stop
+// peeling ray: optical depth from p (in leaf w) along direction k to the
+// domain border at external frequency nu_ext; stops once tau > tau_stop.
+// G is the device-side copy of the parameters.
 // ---------------------------------------------------------------------------
 template <int NL>
-__device__ double ray_walk(const Params& P, const double p0[3], Where w, const double k[3],
-                           const double inv[3], double nu_ext, double tau_stop, Tallies& tl,
-                           int32_t* cells, double* lens, int cap, int32_t* ncell) {
-    double p[3] = {p0[0], p0[1], p0[2]};
+__device__ __noinline__ double ray_walk(const Params* __restrict__ G, double p0, double p1, double p2,
+                                        Where w, double k0, double k1, double k2, double nu_ext,
+                                        double tau_stop, Tallies* tl, int32_t* cells, double* lens, int cap,
+                                        int32_t* ncell) {
+    const Params& P = *G;
+    double p[3] = {p0, p1, p2};
+    const double k[3] = {k0, k1, k2};
+    const double inv[3] = {k0 != 0.0 ? 1.0 / k0 : 0.0, k1 != 0.0 ? 1.0 / k1 : 0.0, k2 != 0.0 ? 1.0 / k2 : 0.0};
     double tau = 0.0;
     int n = 0, zero_run = 0;
+    uint32_t sl = 0, nl = 0, ll = 0;
     for (int guard = 0; guard < (1 << 26); ++guard) {
         CellCache<NL> cc;
         load_cell<NL>(P, w.leaf, cc);
-        ++tl.leaf_loads;
+        ++ll;
         double nu = to_gas(nu_ext, beta_of(cc, k));
         float kl[NL];
         float kap = opacity<NL>(P, cc, nu, kl);
@@ -88,30 +102,39 @@ __device__ double ray_walk(const Params& P, const double p0[3], Where w, const d
         if (zero_run > 64) break;
         move_to_face(p, k, axis, tf, w);
         wrap_periodic(P, p, k);
-        if (!next_leaf(P, p, k, axis, w, tl.son_loads, tl.nbor_loads)) break;
+        if (!next_leaf(P, p, k, axis, w, sl, nl)) break;
     }
-    tl.peel_cells += n;
+    if (tl) {
+        tl->peel_cells += n;
+        tl->leaf_loads += ll;
+        tl->son_loads += sl;
+        tl->nbor_loads += nl;
+    }
     if (ncell) *ncell = n;
     return tau;
 }
 
+// one peeled contribution towards direction d (weight w per sr, gas-frame
+// frequency nu_o_gas of the event's leaf) into spectra, images and cubes
 template <int NL>
-__device__ void peel(const Params& P, const Packet<NL>& s, int d, float w, double nu_o_gas, Tallies& tl) {
-    double ko[3] = {P.dirs[d][0], P.dirs[d][1], P.dirs[d][2]};
-    double inv[3];
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) inv[ax] = ko[ax] != 0.0 ? 1.0 / ko[ax] : 0.0;
-    double nu_ext = to_ext(nu_o_gas, beta_of(s.cc, ko));
-    ++tl.peel_rays;
-    double tau = ray_walk<NL>(P, s.p, s.w, ko, inv, nu_ext, P.tau_stop, tl, nullptr, nullptr, 0, nullptr);
+__device__ __noinline__ void peel_add(const Params* __restrict__ G, double p0, double p1, double p2, Where w,
+                                      float vx, float vy, float vz, int d, float wt, double nu_o_gas,
+                                      Tallies* tl) {
+    const Params& P = *G;
+    const double k0 = P.dirs[d][0], k1 = P.dirs[d][1], k2 = P.dirs[d][2];
+    double b = __fma_rn(k0, (double)vx, __fma_rn(k1, (double)vy, k2 * (double)vz)) * (1.0 / kC);
+    double nu_ext = to_ext(nu_o_gas, b);
+    ++tl->peel_rays;
+    double tau = ray_walk<NL>(G, p0, p1, p2, w, k0, k1, k2, nu_ext, P.tau_stop, tl, nullptr, nullptr, 0, nullptr);
     if (tau > P.tau_stop) return;
-    float f = w * expf(-(float)tau);
+    float f = wt * expf(-(float)tau);
     double t = __dmul_rn(__dsub_rn(nu_ext, P.nu_lo), P.nu_inv_range);
-    int ch = (int)floor(t * (double)P.nbin);
-    bool chok = t >= 0.0 && ch >= 0 && ch < P.nbin;
+    double fb = floor(t * (double)P.nbin);
+    bool chok = fb >= 0.0 && fb < (double)P.nbin;
+    int ch = chok ? (int)fb : 0;
     if (chok) atomicAdd(P.pspec + d * P.nbin + ch, f);
     if (P.npix > 0) {
-        double r0 = s.p[0] - P.img_c[0], r1 = s.p[1] - P.img_c[1], r2 = s.p[2] - P.img_c[2];
+        double r0 = p0 - P.img_c[0], r1 = p1 - P.img_c[1], r2 = p2 - P.img_c[2];
         double u = r0 * P.eu[d][0] + r1 * P.eu[d][1] + r2 * P.eu[d][2];
         double v = r0 * P.ev[d][0] + r1 * P.ev[d][1] + r2 * P.ev[d][2];
         double fu = floor((u * P.inv_fov + 0.5) * (double)P.npix);
@@ -129,43 +152,52 @@ __device__ void peel(const Params& P, const Packet<NL>& s, int d, float w, doubl
 // interactions (Sect. 3.2)
 // ---------------------------------------------------------------------------
 template <int NL, bool PEEL>
-__device__ void scatter_dust(const Params& P, Packet<NL>& s, Tallies& tl) {
+__device__ __forceinline__ void scatter_dust(const Params& P, Packet<NL>& s, Tallies& tl) {
     float r_alb = s.rng.u24();
     if (r_alb > P.dust_albedo) {
         s.status = RASCAS_PK_ABSORBED_;
         return;
     }
     float r_mu = s.rng.u24(), r_phi = s.rng.u24();
-    float mu = mu_sample(PH_HG, r_mu, P.dust_g);
-    float kx = (float)s.k[0], ky = (float)s.k[1], kz = (float)s.k[2];
+    float st;
+    float mu = mu_sample(PH_HG, r_mu, P.dust_g, st);
+    float kx = (float)s.k0, ky = (float)s.k1, kz = (float)s.k2;
     if (PEEL) {
-        for (int d = 0; d < P.ndir; ++d) {
-            float muo = kx * (float)P.dirs[d][0] + ky * (float)P.dirs[d][1] + kz * (float)P.dirs[d][2];
-            float w = phase_p(PH_HG, muo, P.dust_g) * (1.0f / kTwoPiF);
-            peel<NL>(P, s, d, w, s.nu, tl);
+#pragma unroll
+        for (int d = 0; d < kMaxDirs; ++d) {
+            if (d < P.ndir) {
+                float muo = kx * (float)P.dirs[d][0] + ky * (float)P.dirs[d][1] + kz * (float)P.dirs[d][2];
+                float wt = phase_p(PH_HG, muo, P.dust_g) * (1.0f / kTwoPiF);
+                peel_add<NL>(P.self, s.p0, s.p1, s.p2, s.w, s.cc.vx, s.cc.vy, s.cc.vz, d, wt, s.nu, &tl);
+            }
         }
     }
     if (!P.keep_dir) {
-        dir_from(kx, ky, kz, mu, r_phi, s.k);
+        dir_from(kx, ky, kz, mu, st, r_phi, s.k0, s.k1, s.k2);
         s.inv_ok = false;
     }
     ++tl.scatt_dust;
 }
 
-template <int NL, bool PEEL>
-__device__ void scatter_line(const Params& P, Packet<NL>& s, int il, Tallies& tl) {
-    const LineDev& L = P.line[il];
-    float x_in = (float)((s.nu - L.nu0) * s.cc.invdnu[il]);
+template <int NL, bool PEEL, int IL>
+__device__ __forceinline__ void scatter_line(const Params& P, Packet<NL>& s, Tallies& tl) {
+    const LineDev& L = P.line[IL];
+    float x_in = (float)((s.nu - L.nu0) * s.cc.invdnu[IL]);
     int ch = 0;
+    double chnu = L.nu0;
     if (L.nchan > 1) {
         float r = s.rng.u24();
         ch = L.nchan - 1;
-        for (int c = 0; c < L.nchan - 1; ++c)
-            if (r < L.chan_cum[c]) { ch = c; break; }
+#pragma unroll
+        for (int c = kMaxChan - 2; c >= 0; --c)
+            if (c < L.nchan - 1 && r < L.chan_cum[c]) ch = c;
+#pragma unroll
+        for (int c = 1; c < kMaxChan; ++c)
+            if (c == ch) chnu = L.chan_nu[c];
     }
     bool err = false;
     uint32_t trials = 0;
-    float upar = sample_upar(s.rng, x_in, s.cc.a[il], P.x_gauss, trials, err);
+    float upar = sample_upar(s.rng, x_in, s.cc.a[IL], P.x_gauss, trials, err);
     tl.trials += trials;
     if (err) {
         s.status = RASCAS_PK_ERROR_;
@@ -176,7 +208,7 @@ __device__ void scatter_line(const Params& P, Packet<NL>& s, int il, Tallies& tl
     float sn, cs;
     sincospif(2.0f * r2, &sn, &cs);
     float up1 = rho * cs, up2 = rho * sn;
-    float kx = (float)s.k[0], ky = (float)s.k[1], kz = (float)s.k[2];
+    float kx = (float)s.k0, ky = (float)s.k1, kz = (float)s.k2;
     float3 e1, e2;
     onb(kx, ky, kz, e1, e2);
     float vx = upar * kx + up1 * e1.x + up2 * e2.x;   // scatterer velocity / v_th
@@ -186,43 +218,47 @@ __device__ void scatter_line(const Params& P, Packet<NL>& s, int il, Tallies& tl
     if (ch > 0 || P.isotropic || L.phase != 0) kind = PH_ISO;
     else kind = fabsf(x_in - upar) < 0.2f ? PH_CORE : PH_WING;
     float r_mu = s.rng.u24(), r_phi = s.rng.u24();
-    float mu = mu_sample(kind, r_mu, 0.0f);
-    double kout[3];
+    float st;
+    float mu = mu_sample(kind, r_mu, 0.0f, st);
+    double ko0, ko1, ko2;
     if (P.keep_dir) {
-        kout[0] = s.k[0]; kout[1] = s.k[1]; kout[2] = s.k[2];
+        ko0 = s.k0; ko1 = s.k1; ko2 = s.k2;
         mu = 1.0f;
     } else {
-        dir_from(kx, ky, kz, mu, r_phi, kout);
+        dir_from(kx, ky, kz, mu, st, r_phi, ko0, ko1, ko2);
     }
-    const float vthc = s.cc.vth_c[il];
+    const float vthc = s.cc.vth_c[IL];
     const float recp = P.recoil ? L.recoil_pref * (float)s.nu : 0.0f;
     if (PEEL) {
-        for (int d = 0; d < P.ndir; ++d) {
-            float ox = (float)P.dirs[d][0], oy = (float)P.dirs[d][1], oz = (float)P.dirs[d][2];
-            float muo = kx * ox + ky * oy + kz * oz;
-            float uo = ox * vx + oy * vy + oz * vz;
-            double nu_o;
-            if (ch > 0) {
-                nu_o = __fma_rn(L.chan_nu[ch], (double)(uo * vthc), L.chan_nu[ch]);
-            } else {
-                float rec = (1.0f - muo) * recp;
-                float f = ((uo - upar) * vthc - rec) / (1.0f + rec);
-                nu_o = __fma_rn(s.nu, (double)f, s.nu);
+#pragma unroll
+        for (int d = 0; d < kMaxDirs; ++d) {
+            if (d < P.ndir) {
+                float ox = (float)P.dirs[d][0], oy = (float)P.dirs[d][1], oz = (float)P.dirs[d][2];
+                float muo = kx * ox + ky * oy + kz * oz;
+                float uo = ox * vx + oy * vy + oz * vz;
+                double nu_o;
+                if (ch > 0) {
+                    nu_o = __fma_rn(chnu, (double)(uo * vthc), chnu);
+                } else {
+                    float rec = (1.0f - muo) * recp;
+                    float f = ((uo - upar) * vthc - rec) / (1.0f + rec);
+                    nu_o = __fma_rn(s.nu, (double)f, s.nu);
+                }
+                float wt = phase_p(kind, muo, 0.0f) * (1.0f / kTwoPiF);
+                peel_add<NL>(P.self, s.p0, s.p1, s.p2, s.w, s.cc.vx, s.cc.vy, s.cc.vz, d, wt, nu_o, &tl);
             }
-            float w = phase_p(kind, muo, 0.0f) * (1.0f / kTwoPiF);
-            peel<NL>(P, s, d, w, nu_o, tl);
         }
     }
-    float uout = (float)kout[0] * vx + (float)kout[1] * vy + (float)kout[2] * vz;
+    float uout = (float)ko0 * vx + (float)ko1 * vy + (float)ko2 * vz;
     if (ch > 0) {
-        s.nu = __fma_rn(L.chan_nu[ch], (double)(uout * vthc), L.chan_nu[ch]);
+        s.nu = __fma_rn(chnu, (double)(uout * vthc), chnu);
     } else {
         float rec = (1.0f - mu) * recp;
         float f = ((uout - upar) * vthc - rec) / (1.0f + rec);
         s.nu = __fma_rn(s.nu, (double)f, s.nu);
     }
     if (!P.keep_dir) {
-        s.k[0] = kout[0]; s.k[1] = kout[1]; s.k[2] = kout[2];
+        s.k0 = ko0; s.k1 = ko1; s.k2 = ko2;
         s.inv_ok = false;
     }
     ++tl.scatt_line;
@@ -234,9 +270,11 @@ __device__ __forceinline__ void trace_record(const Params& P, const Packet<NL>& 
     int32_t c = tr.nev[s.idx];
     if (c >= tr.max_events) return;
     TraceEvent& e = tr.ev[(long long)s.idx * tr.max_events + c];
-    double b = beta_of(s.cc, s.k);
-    for (int ax = 0; ax < 3; ++ax) { e.p[ax] = s.p[ax]; e.k[ax] = s.k[ax]; }
-    e.nu = s.status == RASCAS_PK_ERROR_ ? s.nu : to_ext(s.nu, b);
+    const double k[3] = {s.k0, s.k1, s.k2};
+    double b = beta_of(s.cc, k);
+    e.p[0] = s.p0; e.p[1] = s.p1; e.p[2] = s.p2;
+    e.k[0] = s.k0; e.k[1] = s.k1; e.k[2] = s.k2;
+    e.nu = (s.status == RASCAS_PK_ERROR_ && s.w.leaf < 0) ? s.nu : to_ext(s.nu, b);
     e.leaf = s.w.leaf; e.level = s.w.level; e.ijk[0] = s.w.i; e.ijk[1] = s.w.j; e.ijk[2] = s.w.k;
     e.status = s.status;
     e.ndraw = s.rng.n;
@@ -246,13 +284,15 @@ __device__ __forceinline__ void trace_record(const Params& P, const Packet<NL>& 
 }
 
 template <int NL, bool PEEL>
-__device__ void interact(const Params& P, Packet<NL>& s, double li, bool exact, float kap,
-                         const float kl[NL], Tallies& tl, const TraceOut& tr) {
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) s.p[ax] = __fma_rn(li, s.k[ax], s.p[ax]);
+__device__ __forceinline__ void interact(const Params& P, Packet<NL>& s, double li, bool exact, float kap,
+                                         const float kl[NL], Tallies& tl, const TraceOut& tr) {
+    s.p0 = __fma_rn(li, s.k0, s.p0);
+    s.p1 = __fma_rn(li, s.k1, s.p1);
+    s.p2 = __fma_rn(li, s.k2, s.p2);
     s.path += li;
     if (exact) {
-        double D = inner_distance(s.p, s.w);
+        const double p[3] = {s.p0, s.p1, s.p2};
+        double D = inner_distance(p, s.w);
         s.budget = __fsub_rd(__double2float_rd(D * (1.0 - 0x1p-20)), 4e-16f);
     }
     // Sect. 3.2: dust with P = tau_d / tau, else line X with P = tau_X / tau
@@ -264,11 +304,16 @@ __device__ void interact(const Params& P, Packet<NL>& s, double li, bool exact, 
         float acc = s.cc.kap_d;
         int il = NL - 1;
 #pragma unroll
-        for (int i = 0; i < NL - 1; ++i) {
-            acc += kl[i];
-            if (rk < acc) { il = i; break; }
+        for (int i = NL - 2; i >= 0; --i) {
+            float ai = acc;
+#pragma unroll
+            for (int j = 0; j <= i; ++j) ai += kl[j];
+            if (rk < ai) il = i;
         }
-        scatter_line<NL, PEEL>(P, s, il, tl);
+        if (il == 0) scatter_line<NL, PEEL, 0>(P, s, tl);
+        if (NL > 1 && il == 1) scatter_line<NL, PEEL, (NL > 1 ? 1 : 0)>(P, s, tl);
+        if (NL > 2 && il == 2) scatter_line<NL, PEEL, (NL > 2 ? 2 : 0)>(P, s, tl);
+        if (NL > 3 && il == 3) scatter_line<NL, PEEL, (NL > 3 ? 3 : 0)>(P, s, tl);
     }
     if (s.status == RASCAS_PK_ACTIVE_) {
         ++s.nscatt;
@@ -281,7 +326,7 @@ __device__ void interact(const Params& P, Packet<NL>& s, double li, bool exact, 
 // one walk step: an interaction inside the current leaf, a face crossing, or
 // the escape through the domain border (Sect. 3, Sect. 4.3)
 template <int NL, bool PEEL>
-__device__ void step(const Params& P, Packet<NL>& s, Tallies& tl, const TraceOut& tr) {
+__device__ __forceinline__ void step(const Params& P, Packet<NL>& s, Tallies& tl, const TraceOut& tr) {
     if (P.max_steps > 0 && s.nsteps >= P.max_steps) {
         s.status = RASCAS_PK_CAPPED_;
         trace_record<NL>(P, s, tr);
@@ -301,13 +346,17 @@ __device__ void step(const Params& P, Packet<NL>& s, Tallies& tl, const TraceOut
         }
     }
     if (!s.inv_ok) {
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax) s.inv[ax] = s.k[ax] != 0.0 ? 1.0 / s.k[ax] : 0.0;
+        s.i0 = s.k0 != 0.0 ? 1.0 / s.k0 : 0.0;
+        s.i1 = s.k1 != 0.0 ? 1.0 / s.k1 : 0.0;
+        s.i2 = s.k2 != 0.0 ? 1.0 / s.k2 : 0.0;
         s.inv_ok = true;
     }
+    double p[3] = {s.p0, s.p1, s.p2};
+    const double k[3] = {s.k0, s.k1, s.k2};
+    const double inv[3] = {s.i0, s.i1, s.i2};
     int axis;
-    double tf = face_distance(s.p, s.k, s.inv, s.w, axis);
-    double tb = border_leaf ? border_distance(P, s.p, s.k, s.inv) : kInf;
+    double tf = face_distance(p, k, inv, s.w, axis);
+    double tb = border_leaf ? border_distance(P, p, k, inv) : kInf;
     bool border = tb <= tf;
     double l = border ? tb : tf;
     double tau_cell = __dmul_rn(__dmul_rn((double)kap, l), P.box_cm);
@@ -319,8 +368,9 @@ __device__ void step(const Params& P, Packet<NL>& s, Tallies& tl, const TraceOut
     s.tau = __dsub_rn(s.tau, tau_cell);
     s.path += l;
     if (border) {
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax) s.p[ax] = __fma_rn(l, s.k[ax], s.p[ax]);
+        s.p0 = __fma_rn(l, s.k0, s.p0);
+        s.p1 = __fma_rn(l, s.k1, s.p1);
+        s.p2 = __fma_rn(l, s.k2, s.p2);
         s.status = RASCAS_PK_ESCAPED_;
         trace_record<NL>(P, s, tr);
         return;
@@ -332,11 +382,12 @@ __device__ void step(const Params& P, Packet<NL>& s, Tallies& tl, const TraceOut
         trace_record<NL>(P, s, tr);
         return;
     }
-    double nu_ext = to_ext(s.nu, beta_of(s.cc, s.k));
-    move_to_face(s.p, s.k, axis, tf, s.w);
-    wrap_periodic(P, s.p, s.k);
+    double nu_ext = to_ext(s.nu, beta_of(s.cc, k));
+    move_to_face(p, k, axis, tf, s.w);
+    wrap_periodic(P, p, k);
+    s.p0 = p[0]; s.p1 = p[1]; s.p2 = p[2];
     Where nw = s.w;
-    if (!next_leaf(P, s.p, s.k, axis, nw, tl.son_loads, tl.nbor_loads)) {
+    if (!next_leaf(P, p, k, axis, nw, tl.son_loads, tl.nbor_loads)) {
         s.status = RASCAS_PK_ESCAPED_;   // left the box
         trace_record<NL>(P, s, tr);
         return;
@@ -344,18 +395,17 @@ __device__ void step(const Params& P, Packet<NL>& s, Tallies& tl, const TraceOut
     s.w = nw;
     load_cell<NL>(P, s.w.leaf, s.cc);
     ++tl.leaf_loads;
-    s.nu = to_gas(nu_ext, beta_of(s.cc, s.k));
+    s.nu = to_gas(nu_ext, beta_of(s.cc, k));
     s.budget = 0.0f;
 }
 
 template <int NL, bool PEEL>
-__device__ void start_packet(const Params& P, const PacketsIn& in, long long idx, Packet<NL>& s,
-                             Tallies& tl, const TraceOut& tr) {
+__device__ __forceinline__ void start_packet(const Params& P, const PacketsIn& in, long long idx, Packet<NL>& s,
+                                             Tallies& tl, const TraceOut& tr) {
     s.idx = idx;
-    for (int ax = 0; ax < 3; ++ax) {
-        s.p[ax] = in.pos[3 * idx + ax];
-        s.k[ax] = in.dir[3 * idx + ax];
-    }
+    double p[3] = {in.pos[3 * idx], in.pos[3 * idx + 1], in.pos[3 * idx + 2]};
+    const double k[3] = {in.dir[3 * idx], in.dir[3 * idx + 1], in.dir[3 * idx + 2]};
+    s.k0 = k[0]; s.k1 = k[1]; s.k2 = k[2];
     double nu_ext = in.nu[idx];
     s.rng.init(P, in.id[idx]);
     s.nscatt = 0;
@@ -365,40 +415,48 @@ __device__ void start_packet(const Params& P, const PacketsIn& in, long long idx
     s.inv_ok = false;
     s.zero_run = 0;
     s.status = RASCAS_PK_ACTIVE_;
-    wrap_periodic(P, s.p, s.k);
-    if (!locate_point(P, s.p, s.k, s.w, tl.son_loads)) {
+    wrap_periodic(P, p, k);
+    s.p0 = p[0]; s.p1 = p[1]; s.p2 = p[2];
+    if (!locate_point(P, p, k, s.w, tl.son_loads)) {
         s.status = RASCAS_PK_ERROR_;
         s.nu = nu_ext;
-        s.w.leaf = -1; s.w.level = 0; s.w.i = s.w.j = s.w.k = 0;
+        s.w.leaf = -1; s.w.oct = 0; s.w.level = 0; s.w.i = s.w.j = s.w.k = 0;
         s.cc.vx = s.cc.vy = s.cc.vz = 0.0f;
         trace_record<NL>(P, s, tr);
         return;
     }
     load_cell<NL>(P, s.w.leaf, s.cc);
     ++tl.leaf_loads;
-    s.nu = to_gas(nu_ext, beta_of(s.cc, s.k));
+    s.nu = to_gas(nu_ext, beta_of(s.cc, k));
     if (PEEL) {
-        for (int d = 0; d < P.ndir; ++d) peel<NL>(P, s, d, 1.0f / (2.0f * kTwoPiF), s.nu, tl);
+#pragma unroll
+        for (int d = 0; d < kMaxDirs; ++d)
+            if (d < P.ndir)
+                peel_add<NL>(P.self, s.p0, s.p1, s.p2, s.w, s.cc.vx, s.cc.vy, s.cc.vz, d,
+                             1.0f / (2.0f * kTwoPiF), s.nu, &tl);
     }
     trace_record<NL>(P, s, tr);
     s.tau = tau_event(s.rng.u52());
 }
 
 template <int NL>
-__device__ void finish_packet(const Params& P, const Packet<NL>& s, const PacketsOut& out,
-                              uint32_t cnt[5]) {
-    double nu_ext = s.status == RASCAS_PK_ERROR_ && s.w.leaf < 0 ? s.nu : to_ext(s.nu, beta_of(s.cc, s.k));
+__device__ __forceinline__ void finish_packet(const Params& P, const Packet<NL>& s, const PacketsOut& out,
+                                              uint32_t& c_pk, uint32_t& c_esc, uint32_t& c_abs, uint32_t& c_cap,
+                                              uint32_t& c_err) {
+    const double k[3] = {s.k0, s.k1, s.k2};
+    double nu_ext = (s.status == RASCAS_PK_ERROR_ && s.w.leaf < 0) ? s.nu : to_ext(s.nu, beta_of(s.cc, k));
     long long i = s.idx;
     if (out.status) out.status[i] = s.status;
     if (out.nscatt) out.nscatt[i] = s.nscatt;
     if (out.nu) out.nu[i] = nu_ext;
     if (out.path) out.path[i] = s.path;
-    for (int ax = 0; ax < 3; ++ax) {
-        if (out.pos) out.pos[3 * i + ax] = s.p[ax];
-        if (out.dir) out.dir[3 * i + ax] = s.k[ax];
-    }
-    ++cnt[0];
-    if (s.status >= 1 && s.status <= 4) ++cnt[s.status];
+    if (out.pos) { out.pos[3 * i] = s.p0; out.pos[3 * i + 1] = s.p1; out.pos[3 * i + 2] = s.p2; }
+    if (out.dir) { out.dir[3 * i] = s.k0; out.dir[3 * i + 1] = s.k1; out.dir[3 * i + 2] = s.k2; }
+    ++c_pk;
+    c_esc += s.status == RASCAS_PK_ESCAPED_;
+    c_abs += s.status == RASCAS_PK_ABSORBED_;
+    c_cap += s.status == RASCAS_PK_CAPPED_;
+    c_err += s.status == RASCAS_PK_ERROR_;
     if (s.status == RASCAS_PK_ESCAPED_ && P.spec != nullptr) {
         double t = __dmul_rn(__dsub_rn(nu_ext, P.nu_lo), P.nu_inv_range);
         double fb = floor(t * (double)P.nbin);
@@ -416,7 +474,7 @@ template <int NL, bool PEEL>
 __global__ void __launch_bounds__(128) k_propagate(Params P, PacketsIn in, PacketsOut out, TraceOut tr) {
     Packet<NL> s;
     Tallies tl = {};
-    uint32_t cnt[5] = {0, 0, 0, 0, 0};
+    uint32_t c_pk = 0, c_esc = 0, c_abs = 0, c_cap = 0, c_err = 0;
     const unsigned lane = threadIdx.x & 31u;
     bool have = false, drained = false;
     for (;;) {
@@ -432,7 +490,7 @@ __global__ void __launch_bounds__(128) k_propagate(Params P, PacketsIn in, Packe
                 if (idx < in.n) {
                     start_packet<NL, PEEL>(P, in, idx, s, tl, tr);
                     if (s.status == RASCAS_PK_ACTIVE_) have = true;
-                    else finish_packet<NL>(P, s, out, cnt);
+                    else finish_packet<NL>(P, s, out, c_pk, c_esc, c_abs, c_cap, c_err);
                 } else {
                     drained = true;
                 }
@@ -445,16 +503,16 @@ __global__ void __launch_bounds__(128) k_propagate(Params P, PacketsIn in, Packe
         if (have) {
             step<NL, PEEL>(P, s, tl, tr);
             if (s.status != RASCAS_PK_ACTIVE_) {
-                finish_packet<NL>(P, s, out, cnt);
+                finish_packet<NL>(P, s, out, c_pk, c_esc, c_abs, c_cap, c_err);
                 have = false;
             }
         }
     }
-    flush(P, cnt[0], CNT_PACKETS);
-    flush(P, cnt[1], CNT_ESCAPED);
-    flush(P, cnt[2], CNT_ABSORBED);
-    flush(P, cnt[3], CNT_CAPPED);
-    flush(P, cnt[4], CNT_ERRORS);
+    flush(P, c_pk, CNT_PACKETS);
+    flush(P, c_esc, CNT_ESCAPED);
+    flush(P, c_abs, CNT_ABSORBED);
+    flush(P, c_cap, CNT_CAPPED);
+    flush(P, c_err, CNT_ERRORS);
     flush(P, tl.scatt_line, CNT_SCATT_LINE);
     flush(P, tl.scatt_dust, CNT_SCATT_DUST);
     flush(P, tl.cross, CNT_CROSS);
@@ -470,24 +528,24 @@ __global__ void __launch_bounds__(128) k_propagate(Params P, PacketsIn in, Packe
 // ray optical depths (peeling integral without cut-off) and probes
 // ---------------------------------------------------------------------------
 template <int NL>
-__global__ void k_ray_tau(Params P, long long n, const double* pos, const double* dir, const double* nu,
-                          double* tau, int32_t* cells, double* lens, int cap, int32_t* ncell) {
+__global__ void k_ray_tau(const Params* __restrict__ G, long long n, const double* pos, const double* dir,
+                          const double* nu, double* tau, int32_t* cells, double* lens, int cap, int32_t* ncell) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const Params& P = *G;
     double p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
-    double k[3] = {dir[3 * i], dir[3 * i + 1], dir[3 * i + 2]};
-    double inv[3];
-    for (int ax = 0; ax < 3; ++ax) inv[ax] = k[ax] != 0.0 ? 1.0 / k[ax] : 0.0;
-    Tallies tl = {};
+    const double k[3] = {dir[3 * i], dir[3 * i + 1], dir[3 * i + 2]};
+    uint32_t loads = 0;
     wrap_periodic(P, p, k);
     Where w;
-    if (!locate_point(P, p, k, w, tl.son_loads)) {
+    if (!locate_point(P, p, k, w, loads)) {
         tau[i] = 0.0;
         if (ncell) ncell[i] = 0;
         return;
     }
-    tau[i] = ray_walk<NL>(P, p, w, k, inv, nu[i], kInf, tl, cells ? cells + i * cap : nullptr,
-                          lens ? lens + i * cap : nullptr, cap, ncell ? ncell + i : nullptr);
+    tau[i] = ray_walk<NL>(G, p[0], p[1], p[2], w, k[0], k[1], k[2], nu[i], kInf, nullptr,
+                          cells ? cells + i * cap : nullptr, lens ? lens + i * cap : nullptr, cap,
+                          ncell ? ncell + i : nullptr);
 }
 
 __global__ void k_eval_voigt(long long n, const float* a, const double* x, float* H) {
@@ -546,12 +604,13 @@ cudaError_t launch_ray_tau(const Params& P, long long n, const double* pos, cons
                            double* tau, int32_t* cells, double* lens, int cap, int32_t* ncell, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     int block = 128;
-    long long grid = (n + block - 1) / block;
+    unsigned grid = (unsigned)((n + block - 1) / block);
+    const Params* G = P.self;
     switch (P.nline) {
-        case 1: k_ray_tau<1><<<(unsigned)grid, block, 0, st>>>(P, n, pos, dir, nu, tau, cells, lens, cap, ncell); break;
-        case 2: k_ray_tau<2><<<(unsigned)grid, block, 0, st>>>(P, n, pos, dir, nu, tau, cells, lens, cap, ncell); break;
-        case 3: k_ray_tau<3><<<(unsigned)grid, block, 0, st>>>(P, n, pos, dir, nu, tau, cells, lens, cap, ncell); break;
-        case 4: k_ray_tau<4><<<(unsigned)grid, block, 0, st>>>(P, n, pos, dir, nu, tau, cells, lens, cap, ncell); break;
+        case 1: k_ray_tau<1><<<grid, block, 0, st>>>(G, n, pos, dir, nu, tau, cells, lens, cap, ncell); break;
+        case 2: k_ray_tau<2><<<grid, block, 0, st>>>(G, n, pos, dir, nu, tau, cells, lens, cap, ncell); break;
+        case 3: k_ray_tau<3><<<grid, block, 0, st>>>(G, n, pos, dir, nu, tau, cells, lens, cap, ncell); break;
+        case 4: k_ray_tau<4><<<grid, block, 0, st>>>(G, n, pos, dir, nu, tau, cells, lens, cap, ncell); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
