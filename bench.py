@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--max-scatt", type=int, default=0,
+                    help="cap scatterings per packet (profiling runs only; 0 = the full workload)")
     return ap.parse_args()
 
 
@@ -172,6 +174,10 @@ def main():
     wl = workload(8)
     ctx = rg.Context(local)
     ctx.setup(wl)
+    if args.max_scatt:
+        ph = wl.physics
+        ctx.set_physics(ph.recoil, ph.isotropic, ph.keep_direction, ph.x_gauss, args.max_scatt, 0, ph.tau_stop,
+                        ph.seed)
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream)
 

@@ -100,16 +100,30 @@ __device__ __forceinline__ float voigt_h(float a, double x) {
 // the fitted separation u0(x, log10 a), clamped at 0; |x| >= x_gauss: Gaussian
 // N(1/|x|, 1/2).  Returns u_par for frequency x (scatterer's Doppler units).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float u0_fit(float x, float a) {
-    float z = log10f(a);
-    float z2 = z * z;
-    float u0 = 2.648963f + 2.014446f * z + 0.351479f * z2 +
-               x * (-4.058673f - 3.675859f * z - 0.640003f * z2 +
-               x * (3.017395f + 2.117133f * z + 0.370294f * z2 +
-               x * (-0.869789f - 0.565886f * z - 0.096312f * z2 +
-               x * (0.110987f + 0.070103f * z + 0.011557f * z2 +
-               x * (-0.005200f - 0.003240f * z - 0.000519f * z2)))));
-    return fmaxf(u0, 0.0f);
+// The x-polynomial of u0 cancels heavily for x ~ 5-8 (terms of a few hundred
+// summing to O(1)) and u_par moves one-for-one with u0, so both the
+// coefficients in zeta = log10 a and the Horner sum in x are FP64.  The six
+// coefficients depend only on a (the line and the cell's T); the propagation
+// kernel computes them once per leaf and line and keeps them in shared memory.
+struct U0Coef {
+    double c[6];
+};
+
+__device__ __forceinline__ void u0_coeffs(double a, U0Coef& k) {
+    double z = log10(a);
+    k.c[0] = __fma_rn(z, __fma_rn(z, 0.351479, 2.014446), 2.648963);
+    k.c[1] = __fma_rn(z, __fma_rn(z, -0.640003, -3.675859), -4.058673);
+    k.c[2] = __fma_rn(z, __fma_rn(z, 0.370294, 2.117133), 3.017395);
+    k.c[3] = __fma_rn(z, __fma_rn(z, -0.096312, -0.565886), -0.869789);
+    k.c[4] = __fma_rn(z, __fma_rn(z, 0.011557, 0.070103), 0.110987);
+    k.c[5] = __fma_rn(z, __fma_rn(z, -0.000519, -0.003240), -0.005200);
+}
+
+__device__ __forceinline__ float u0_eval(const U0Coef& k, float x) {
+    double xd = (double)x;
+    double u0 = __fma_rn(xd, __fma_rn(xd, __fma_rn(xd, __fma_rn(xd, __fma_rn(xd, k.c[5], k.c[4]), k.c[3]),
+                                                   k.c[2]), k.c[1]), k.c[0]);
+    return fmaxf((float)u0, 0.0f);
 }
 
 // The two branches of the comparison function are sampled through their
@@ -118,7 +132,7 @@ __device__ __forceinline__ float u0_fit(float x, float a) {
 // resolve the poles, so the code works with the distances to the poles,
 // A = theta0 + pi/2 and B = pi/2 - theta0 (formed without cancellation), and
 // u = x - a / tan(A r) or u = x + a / tan(B (1 - r)).
-__device__ __forceinline__ float sample_upar(Rng& rng, float x, float a, float x_gauss,
+__device__ __forceinline__ float sample_upar(Rng& rng, float x, float a, const U0Coef& u0c, float x_gauss,
                                              uint32_t& trials, bool& err) {
     float sg = x < 0.0f ? -1.0f : 1.0f;
     float xa = fabsf(x);
@@ -127,7 +141,7 @@ __device__ __forceinline__ float sample_upar(Rng& rng, float x, float a, float x
         trials += 1;
         return sg * (1.0f / xa + sqrtf(-logf(r1)) * cospif(2.0f * r2));
     }
-    float u0 = u0_fit(xa, a);
+    float u0 = u0_eval(u0c, xa);
     float t = (u0 - xa) / a;
     float A, B;
     if (t < 0.0f) {
@@ -427,6 +441,7 @@ struct CellCache {
     float a[NL], kap0[NL];       // Voigt a, n_X sigma_0 (cm^-1)
     float vth_c[NL];             // v_th / c
     float T;
+    unsigned u0mask;             // lines whose u0 coefficients are cached for this leaf
 };
 
 template <int NL>
@@ -437,6 +452,7 @@ __device__ __forceinline__ void load_cell(const Params& P, int leaf, CellCache<N
     cc.T = r1.x;
     cc.kap_d = r1.y * P.dust_sigma;
     cc.flags = __float_as_int(r1.w);
+    cc.u0mask = 0u;
     float T = fmaxf(r1.x, 1e-30f);
     float rs = rsqrtf(T);
     // one Newton step in FP64 on 1/sqrt(T): x enters exp(-x^2) and must carry

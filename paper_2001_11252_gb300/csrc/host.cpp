@@ -361,6 +361,7 @@ int rascas_set_lines(rascas_ctx* ctx, const rascas_line* lines, int32_t nline, c
         D.vth_pref = vp;
         D.invdnu_pref = kC / (L.nu0 * vp);
         D.a_pref = (float)(L.A_ul * kC / (4.0 * kPi * L.nu0 * vp));
+        D.a_over_invdnu = L.A_ul / (4.0 * kPi);
         D.sig_pref = (float)(std::sqrt(kPi) * kE * kE * L.f_lu / (kME * L.nu0 * vp));
         D.abund = (float)L.abundance;
         D.recoil_pref = (float)(kH / (L.mass_g * kC * kC));

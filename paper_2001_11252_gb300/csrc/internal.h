@@ -33,6 +33,7 @@ struct LineDev {
     double vth_pref;     // sqrt(2 k_B / m): v_th = vth_pref * sqrt(T)
     double invdnu_pref;  // c / nu0 / vth_pref: 1/Delta nu_D = invdnu_pref / sqrt(T)
     float a_pref;        // A_ul / (4 pi nu0 / c * vth_pref): a = a_pref / sqrt(T)
+    double a_over_invdnu; // A_ul / (4 pi): a = a_over_invdnu * (1 / Delta nu_D)
     float sig_pref;      // sqrt(pi) e^2 f / (m_e c) * c / (nu0 vth_pref): sigma0 = sig_pref / sqrt(T)
     float abund;         // density multiplier
     float recoil_pref;   // h / (m c^2): recoil term = (1 - mu) * h nu / (m c^2)
@@ -122,6 +123,7 @@ cudaError_t launch_eval_voigt(long long n, const float* a, const double* x, floa
 cudaError_t launch_sample_upar(const Params& P, long long n, const double* x, const float* a,
                                const uint64_t* id, float* u, int32_t* ndraw, cudaStream_t st);
 int propagate_block_size();
+size_t propagate_smem(int nline, int block);
 int propagate_blocks_per_sm(int block, bool peel);
 
 }  // namespace rg

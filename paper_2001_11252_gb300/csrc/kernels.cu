@@ -195,9 +195,25 @@ __device__ __forceinline__ void scatter_line(const Params& P, Packet<NL>& s, Tal
         for (int c = 1; c < kMaxChan; ++c)
             if (c == ch) chnu = L.chan_nu[c];
     }
+    // u0 coefficients of this line for this leaf: computed at the first
+    // scattering in the leaf, then read from shared memory
+    U0Coef u0c;
+    {
+        extern __shared__ double s_u0[];
+        double* col = s_u0 + (size_t)IL * 6 * blockDim.x + threadIdx.x;
+        if (!(s.cc.u0mask & (1u << IL))) {
+            u0_coeffs(L.a_over_invdnu * s.cc.invdnu[IL], u0c);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) col[c * blockDim.x] = u0c.c[c];
+            s.cc.u0mask |= 1u << IL;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) u0c.c[c] = col[c * blockDim.x];
+        }
+    }
     bool err = false;
     uint32_t trials = 0;
-    float upar = sample_upar(s.rng, x_in, s.cc.a[IL], P.x_gauss, trials, err);
+    float upar = sample_upar(s.rng, x_in, s.cc.a[IL], u0c, P.x_gauss, trials, err);
     tl.trials += trials;
     if (err) {
         s.status = RASCAS_PK_ERROR_;
@@ -561,7 +577,9 @@ __global__ void k_sample_upar(Params P, long long n, const double* x, const floa
     rng.init(P, id[i]);
     uint32_t trials = 0;
     bool err = false;
-    u[i] = sample_upar(rng, (float)x[i], a[i], P.x_gauss, trials, err);
+    U0Coef c;
+    u0_coeffs((double)a[i], c);
+    u[i] = sample_upar(rng, (float)x[i], a[i], c, P.x_gauss, trials, err);
     nd[i] = err ? -1 : (int32_t)rng.n;
 }
 
@@ -570,10 +588,12 @@ __global__ void k_sample_upar(Params P, long long n, const double* x, const floa
 // ---------------------------------------------------------------------------
 int propagate_block_size() { return 128; }
 
+size_t propagate_smem(int nline, int block) { return (size_t)nline * 6 * block * sizeof(double); }
+
 template <int NL, bool PEEL>
 static int occ(int block) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate<NL, PEEL>, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate<NL, PEEL>, block, propagate_smem(NL, block));
     return nb;
 }
 
@@ -584,8 +604,9 @@ int propagate_blocks_per_sm(int block, bool peel) {
 template <int NL>
 static cudaError_t launch_nl(const Params& P, const PacketsIn& in, const PacketsOut& out, const TraceOut& tr,
                              int grid, int block, cudaStream_t st) {
-    if (P.ndir > 0) k_propagate<NL, true><<<grid, block, 0, st>>>(P, in, out, tr);
-    else k_propagate<NL, false><<<grid, block, 0, st>>>(P, in, out, tr);
+    size_t smem = propagate_smem(NL, block);
+    if (P.ndir > 0) k_propagate<NL, true><<<grid, block, smem, st>>>(P, in, out, tr);
+    else k_propagate<NL, false><<<grid, block, smem, st>>>(P, in, out, tr);
     return cudaGetLastError();
 }
 

@@ -127,7 +127,10 @@ def _replay(wl, n_packets, max_events):
                 continue
             step = np.linalg.norm(np.array(b["p"]) - np.array(a["p"])) + 1e-300
             stats["pos"] = max(stats["pos"], np.abs(np.array(s.p) - b["p"]).max() / step)
-            stats["dir"] = max(stats["dir"], np.abs(np.array(s.k) - b["k"]).max())
+            de = np.abs(np.array(s.k) - b["k"]).max()
+            if de > stats["dir"]:
+                stats["dir"] = de
+                stats["dir_case"] = (list(a["k"]), list(b["k"]), list(s.k), int(a["ndraw"]), int(b["ndraw"]))
             dnu = synth.doppler_width(ln, float(wl.medium.T[b["leaf"]]))
             stats["x"] = max(stats["x"], abs(s.nu - b["nu"]) / dnu)
     return stats
