@@ -24,23 +24,29 @@ constexpr float kTwoPiF = 6.2831853071795865f;
 // Philox4x32-10 (Salmon et al. 2011).  Key = run seed; counter = (draw block
 // lo, hi, packet id lo, hi).  Draw word n of a packet is word n%4 of block n/4.
 // ---------------------------------------------------------------------------
+// one Philox4x32-10 block; kept out of line so that the many draw sites of
+// the transport loop share one copy of the ten rounds
+__device__ __noinline__ uint4 philox_block(uint32_t blk, uint32_t id0, uint32_t id1, uint32_t k0, uint32_t k1) {
+    uint32_t c0 = blk, c1 = 0, c2 = id0, c3 = id1;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
 struct Rng {
     uint32_t k0, k1, id0, id1;
     uint32_t n;        // next draw index
     uint32_t w0, w1, w2, w3;  // cached block n/4 (valid when n%4 != 0)
 
     __device__ __forceinline__ void block(uint32_t blk) {
-        uint32_t c0 = blk, c1 = 0, c2 = id0, c3 = id1;
-        uint32_t a0 = k0, a1 = k1;
-#pragma unroll
-        for (int r = 0; r < 10; ++r) {
-            if (r) { a0 += 0x9E3779B9u; a1 += 0xBB67AE85u; }
-            uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-            uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
-            uint32_t n0 = hi1 ^ c1 ^ a0, n2 = hi0 ^ c3 ^ a1;
-            c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
-        }
-        w0 = c0; w1 = c1; w2 = c2; w3 = c3;
+        uint4 w = philox_block(blk, id0, id1, k0, k1);
+        w0 = w.x; w1 = w.y; w2 = w.z; w3 = w.w;
     }
     __device__ __forceinline__ uint32_t word() {
         uint32_t j = n & 3u;
@@ -58,6 +64,17 @@ struct Rng {
         double m = __fma_rn((double)(wa >> 6), 67108864.0, (double)(wb >> 6));
         return __fma_rn(m, 0x1p-52, 0x1p-53);
     }
+    // tau_event = -ln r (Sect. 3) for r = u52 of the next two words, in FP32:
+    // r = (ma 2^26 + mb + 1/2) 2^-52; below 1/2 -log(r), above it
+    // -log1p(-(1 - r)) with 1 - r formed exactly from the complemented
+    // integers, so the relative error stays ~1e-7 over the whole range
+    __device__ __forceinline__ float tau_event() {
+        uint32_t ma = word() >> 6, mb = word() >> 6;
+        const bool hi = ma >= (1u << 25);
+        if (hi) { ma = (1u << 26) - 1u - ma; mb = (1u << 26) - 1u - mb; }
+        float v = fmaf(__uint2float_rn(ma), 0x1p-26f, (__uint2float_rn(mb) + 0.5f) * 0x1p-52f);
+        return hi ? -log1pf(-v) : -logf(v);
+    }
     __device__ void init(const Params& P, uint64_t pid, uint32_t start = 0) {
         k0 = P.key0; k1 = P.key1;
         id0 = (uint32_t)pid; id1 = (uint32_t)(pid >> 32);
@@ -65,16 +82,6 @@ struct Rng {
         if (n & 3u) block(n >> 2);
     }
 };
-
-// tau_event = -ln r (Sect. 3) in FP32 without losing relative precision for r
-// near 1: -log1p(-(1 - r)) there, -log(r) below 1/2.  Relative error ~1e-7.
-__device__ __forceinline__ double tau_event(double r) {
-    if (r > 0.5) {
-        float s = (float)(1.0 - r);
-        return (double)(-log1pf(-s));
-    }
-    return (double)(-logf((float)r));
-}
 
 // ---------------------------------------------------------------------------
 // Hjerting-Voigt function, Tasitsiomi (2006) eqs. 7-8 (Sect. 3.3.2).  x^2 is
@@ -85,6 +92,21 @@ __device__ __forceinline__ float voigt_h(float a, double x) {
     double x2d = x * x;
     float x2 = (float)x2d;
     float lo = (float)(x2d - (double)x2);
+    float e = expf(-x2) * (1.0f - lo);
+    float z = (x2 - 0.855f) / (x2 + 3.42f);
+    float q = 0.0f;
+    if (z > 0.0f) {
+        q = z * (1.0f + 21.0f / x2) * a / (kPiF * (x2 + 1.0f)) *
+            (0.1117f + z * (4.421f + z * (-9.207f + 5.674f * z)));
+    }
+    return kSqrtPiF * q + e;
+}
+
+// Same function for x carried as an unevaluated FP32 pair x = xh + xl: x^2 is
+// xh^2 plus its exact rounding error plus 2 xh xl, all in FP32.
+__device__ __forceinline__ float voigt_h2(float a, float xh, float xl) {
+    float x2 = xh * xh;
+    float lo = fmaf(xh, xh, -x2) + 2.0f * xh * xl;
     float e = expf(-x2) * (1.0f - lo);
     float z = (x2 - 0.855f) / (x2 + 3.42f);
     float q = 0.0f;
@@ -159,14 +181,10 @@ __device__ __forceinline__ float sample_upar(Rng& rng, float x, float a, const U
     for (uint32_t n = 0; n < (1u << 22); ++n) {
         float r1 = rng.u24(), r2 = rng.u24(), r3 = rng.u24();
         ++trials;
-        float u, lim;
-        if (r1 <= p) {
-            u = xa - a / tanf(A * r2);
-            lim = 0.0f;
-        } else {
-            u = xa + a / tanf(B * (1.0f - r2));
-            lim = u0sq;
-        }
+        const bool b1 = r1 <= p;
+        float tn = tanf(b1 ? A * r2 : B * (1.0f - r2));
+        float u = b1 ? xa - a / tn : xa + a / tn;
+        float lim = b1 ? 0.0f : u0sq;
         if (r3 <= expf(lim - u * u)) return sg * u;
     }
     err = true;
@@ -438,8 +456,11 @@ struct CellCache {
     float kap_d;                 // dust opacity (cm^-1)
     int flags;
     double invdnu[NL];           // 1 / Delta nu_D (1/Hz)
+    double dnu0;                 // Delta nu_D of line 0 (Hz)
+    double xa[NL], xb[NL];       // x_i = xa_i + xb_i x_0 (line i's Doppler units from line 0's)
     float a[NL], kap0[NL];       // Voigt a, n_X sigma_0 (cm^-1)
     float vth_c[NL];             // v_th / c
+    float q0;                    // nu0_0 / Delta nu_D,0 = c / v_th,0
     float T;
     unsigned u0mask;             // lines whose u0 coefficients are cached for this leaf
 };
@@ -469,6 +490,43 @@ __device__ __forceinline__ void load_cell(const Params& P, int leaf, CellCache<N
         cc.kap0[i] = n * L.sig_pref * rs;
         cc.vth_c[i] = L.vth_over_c_pref * T * rs;
     }
+    cc.dnu0 = P.line[0].dnu_pref * (Td * rd);
+    cc.q0 = 1.0f / cc.vth_c[0];
+#pragma unroll
+    for (int i = 1; i < NL; ++i) {
+        cc.xa[i] = P.line[i].nu0_gap * cc.invdnu[i];
+        cc.xb[i] = cc.dnu0 * cc.invdnu[i];
+    }
+}
+
+// gas-frame frequency from the line-0 Doppler offset x = xh + xl, and back
+template <int NL>
+__device__ __forceinline__ double nu_of_x(const Params& P, const CellCache<NL>& cc, float xh, float xl) {
+    return __fma_rn((double)xh + (double)xl, cc.dnu0, P.line[0].nu0);
+}
+template <int NL>
+__device__ __forceinline__ void x_of_nu(const Params& P, const CellCache<NL>& cc, double nu, float& xh, float& xl) {
+    double x = (nu - P.line[0].nu0) * cc.invdnu[0];
+    xh = (float)x;
+    xl = (float)(x - (double)xh);
+}
+
+// total opacity (cm^-1) at the line-0 Doppler offset x = xh + xl; per-line
+// opacities in kl[], each line's own Doppler offset (FP32) in xin[]
+template <int NL>
+__device__ __forceinline__ float opacity_x(const Params& P, const CellCache<NL>& cc, float xh, float xl,
+                                           float kl[NL], float xin[NL]) {
+    kl[0] = cc.kap0[0] * voigt_h2(cc.a[0], xh, xl);
+    xin[0] = xh;
+    float tot = cc.kap_d + kl[0];
+#pragma unroll
+    for (int i = 1; i < NL; ++i) {
+        double x = __fma_rn((double)xh + (double)xl, cc.xb[i], cc.xa[i]);
+        xin[i] = (float)x;
+        kl[i] = cc.kap0[i] * voigt_h(cc.a[i], x);
+        tot += kl[i];
+    }
+    return tot;
 }
 
 // beta = k . v / c in FP64

@@ -360,6 +360,8 @@ int rascas_set_lines(rascas_ctx* ctx, const rascas_line* lines, int32_t nline, c
         double vp = std::sqrt(2.0 * kKB / L.mass_g);
         D.vth_pref = vp;
         D.invdnu_pref = kC / (L.nu0 * vp);
+        D.dnu_pref = L.nu0 * vp / kC;
+        D.nu0_gap = lines[0].nu0 - L.nu0;
         D.a_pref = (float)(L.A_ul * kC / (4.0 * kPi * L.nu0 * vp));
         D.a_over_invdnu = L.A_ul / (4.0 * kPi);
         D.sig_pref = (float)(std::sqrt(kPi) * kE * kE * L.f_lu / (kME * L.nu0 * vp));

@@ -32,6 +32,8 @@ struct LineDev {
     double nu0;          // rest frequency (Hz)
     double vth_pref;     // sqrt(2 k_B / m): v_th = vth_pref * sqrt(T)
     double invdnu_pref;  // c / nu0 / vth_pref: 1/Delta nu_D = invdnu_pref / sqrt(T)
+    double dnu_pref;     // nu0 vth_pref / c: Delta nu_D = dnu_pref sqrt(T)
+    double nu0_gap;      // nu0 of line 0 minus nu0 of this line
     float a_pref;        // A_ul / (4 pi nu0 / c * vth_pref): a = a_pref / sqrt(T)
     double a_over_invdnu; // A_ul / (4 pi): a = a_over_invdnu * (1 / Delta nu_D)
     float sig_pref;      // sqrt(pi) e^2 f / (m_e c) * c / (nu0 vth_pref): sigma0 = sig_pref / sqrt(T)

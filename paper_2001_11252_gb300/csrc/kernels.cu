@@ -31,35 +31,35 @@ struct Tallies {
 template <int NL>
 struct Packet {
     double p0, p1, p2;     // position (box units)
-    double k0, k1, k2;     // direction
     double i0, i1, i2;     // 1/k per axis (valid when inv_ok)
-    double nu;             // gas-frame frequency in the current leaf
-    double tau;            // optical depth left to the next interaction
-    double path;
-    long long idx;
-    long long nscatt, nsteps;
+    double tau;            // optical depth left to the next interaction (formed from tauf when tau_fresh)
+    double path;           // distance travelled (box units)
+    double nu_enter;       // external-frame frequency when the packet entered its leaf
+    long long idx, nscatt, nsteps;
     Where w;
     Rng rng;
+    float kx, ky, kz;      // direction (unit vector, as sampled in FP32)
+    float xh, xl;          // gas-frame Doppler offset of line 0 in this leaf, x = xh + xl
+    float tauf;            // FP32 copy of tau
     float budget;          // path length guaranteed to stay inside the leaf
-    int status;
-    int zero_run;          // consecutive zero-length crossings (guards against a stuck walk)
-    bool inv_ok;
+    int status, zero_run;
+    bool tau_fresh, enter, fresh, inv_ok;
     CellCache<NL> cc;
 };
 
 __device__ __forceinline__ void dir_from(float kx, float ky, float kz, float mu, float st, float r_phi,
-                                         double& o0, double& o1, double& o2) {
+                                         float& ox, float& oy, float& oz) {
     float3 e1, e2;
     onb(kx, ky, kz, e1, e2);
-    float s, c;
-    sincospif(2.0f * r_phi, &s, &c);
-    float ox = mu * kx + st * (c * e1.x + s * e2.x);
-    float oy = mu * ky + st * (c * e1.y + s * e2.y);
-    float oz = mu * kz + st * (c * e1.z + s * e2.z);
-    float nn = rsqrtf(ox * ox + oy * oy + oz * oz);
-    o0 = (double)(ox * nn);
-    o1 = (double)(oy * nn);
-    o2 = (double)(oz * nn);
+    float sn, cs;
+    sincospif(2.0f * r_phi, &sn, &cs);
+    float x = mu * kx + st * (cs * e1.x + sn * e2.x);
+    float y = mu * ky + st * (cs * e1.y + sn * e2.y);
+    float z = mu * kz + st * (cs * e1.z + sn * e2.z);
+    float nn = rsqrtf(x * x + y * y + z * z);
+    ox = x * nn;
+    oy = y * nn;
+    oz = z * nn;
 }
 
 // ---------------------------------------------------------------------------
@@ -161,28 +161,39 @@ __device__ __forceinline__ void scatter_dust(const Params& P, Packet<NL>& s, Tal
     float r_mu = s.rng.u24(), r_phi = s.rng.u24();
     float st;
     float mu = mu_sample(PH_HG, r_mu, P.dust_g, st);
-    float kx = (float)s.k0, ky = (float)s.k1, kz = (float)s.k2;
     if (PEEL) {
+        double nu_gas = nu_of_x(P, s.cc, s.xh, s.xl);   // coherent in the gas frame
 #pragma unroll
         for (int d = 0; d < kMaxDirs; ++d) {
             if (d < P.ndir) {
-                float muo = kx * (float)P.dirs[d][0] + ky * (float)P.dirs[d][1] + kz * (float)P.dirs[d][2];
+                float muo = s.kx * (float)P.dirs[d][0] + s.ky * (float)P.dirs[d][1] + s.kz * (float)P.dirs[d][2];
                 float wt = phase_p(PH_HG, muo, P.dust_g) * (1.0f / kTwoPiF);
-                peel_add<NL>(P.self, s.p0, s.p1, s.p2, s.w, s.cc.vx, s.cc.vy, s.cc.vz, d, wt, s.nu, &tl);
+                peel_add<NL>(P.self, s.p0, s.p1, s.p2, s.w, s.cc.vx, s.cc.vy, s.cc.vz, d, wt, nu_gas, &tl);
             }
         }
     }
     if (!P.keep_dir) {
-        dir_from(kx, ky, kz, mu, st, r_phi, s.k0, s.k1, s.k2);
+        dir_from(s.kx, s.ky, s.kz, mu, st, r_phi, s.kx, s.ky, s.kz);
         s.inv_ok = false;
     }
     ++tl.scatt_dust;
 }
 
+// x = xh + xl advanced by d, kept as a normalised FP32 pair (two-sum)
+__device__ __forceinline__ void pair_add(float& xh, float& xl, float d) {
+    float sum = xh + d;
+    float bb = sum - xh;
+    float err = (xh - (sum - bb)) + (d - bb);
+    float lo = xl + err;
+    float hi = sum + lo;
+    xl = lo - (hi - sum);
+    xh = hi;
+}
+
+// resonant or fluorescent scattering on line IL (Sects. 3.2.1, 3.2.3, 3.3)
 template <int NL, bool PEEL, int IL>
-__device__ __forceinline__ void scatter_line(const Params& P, Packet<NL>& s, Tallies& tl) {
+__device__ __forceinline__ void scatter_line(const Params& P, Packet<NL>& s, float x_in, Tallies& tl) {
     const LineDev& L = P.line[IL];
-    float x_in = (float)((s.nu - L.nu0) * s.cc.invdnu[IL]);
     int ch = 0;
     double chnu = L.nu0;
     if (L.nchan > 1) {
@@ -224,7 +235,7 @@ __device__ __forceinline__ void scatter_line(const Params& P, Packet<NL>& s, Tal
     float sn, cs;
     sincospif(2.0f * r2, &sn, &cs);
     float up1 = rho * cs, up2 = rho * sn;
-    float kx = (float)s.k0, ky = (float)s.k1, kz = (float)s.k2;
+    const float kx = s.kx, ky = s.ky, kz = s.kz;
     float3 e1, e2;
     onb(kx, ky, kz, e1, e2);
     float vx = upar * kx + up1 * e1.x + up2 * e2.x;   // scatterer velocity / v_th
@@ -236,61 +247,58 @@ __device__ __forceinline__ void scatter_line(const Params& P, Packet<NL>& s, Tal
     float r_mu = s.rng.u24(), r_phi = s.rng.u24();
     float st;
     float mu = mu_sample(kind, r_mu, 0.0f, st);
-    double ko0, ko1, ko2;
-    if (P.keep_dir) {
-        ko0 = s.k0; ko1 = s.k1; ko2 = s.k2;
-        mu = 1.0f;
-    } else {
-        dir_from(kx, ky, kz, mu, st, r_phi, ko0, ko1, ko2);
-    }
+    float ox = kx, oy = ky, oz = kz;
+    if (P.keep_dir) mu = 1.0f;
+    else dir_from(kx, ky, kz, mu, st, r_phi, ox, oy, oz);
     const float vthc = s.cc.vth_c[IL];
-    const float recp = P.recoil ? L.recoil_pref * (float)s.nu : 0.0f;
+    // recoil term (1 - mu) h nu / (m c^2) of Eq. (nuout_nuin)
+    const float recp = P.recoil ? L.recoil_pref * ((float)P.line[0].nu0 + s.xh * (float)s.cc.dnu0) : 0.0f;
     if (PEEL) {
+        double nu_in = nu_of_x(P, s.cc, s.xh, s.xl);
 #pragma unroll
         for (int d = 0; d < kMaxDirs; ++d) {
             if (d < P.ndir) {
-                float ox = (float)P.dirs[d][0], oy = (float)P.dirs[d][1], oz = (float)P.dirs[d][2];
-                float muo = kx * ox + ky * oy + kz * oz;
-                float uo = ox * vx + oy * vy + oz * vz;
+                float dx = (float)P.dirs[d][0], dy = (float)P.dirs[d][1], dz = (float)P.dirs[d][2];
+                float muo = kx * dx + ky * dy + kz * dz;
+                float uo = dx * vx + dy * vy + dz * vz;
                 double nu_o;
                 if (ch > 0) {
                     nu_o = __fma_rn(chnu, (double)(uo * vthc), chnu);
                 } else {
                     float rec = (1.0f - muo) * recp;
                     float f = ((uo - upar) * vthc - rec) / (1.0f + rec);
-                    nu_o = __fma_rn(s.nu, (double)f, s.nu);
+                    nu_o = __fma_rn(nu_in, (double)f, nu_in);
                 }
                 float wt = phase_p(kind, muo, 0.0f) * (1.0f / kTwoPiF);
                 peel_add<NL>(P.self, s.p0, s.p1, s.p2, s.w, s.cc.vx, s.cc.vy, s.cc.vz, d, wt, nu_o, &tl);
             }
         }
     }
-    float uout = (float)ko0 * vx + (float)ko1 * vy + (float)ko2 * vz;
+    float uout = ox * vx + oy * vy + oz * vz;
     if (ch > 0) {
-        s.nu = __fma_rn(chnu, (double)(uout * vthc), chnu);
+        double nu = __fma_rn(chnu, (double)(uout * vthc), chnu);
+        x_of_nu(P, s.cc, nu, s.xh, s.xl);
     } else {
+        // nu_out = nu_in (1 + f)  <=>  x_out = x_in + (nu0/Delta nu + x_in) f
         float rec = (1.0f - mu) * recp;
         float f = ((uout - upar) * vthc - rec) / (1.0f + rec);
-        s.nu = __fma_rn(s.nu, (double)f, s.nu);
+        pair_add(s.xh, s.xl, (s.cc.q0 + s.xh) * f);
     }
     if (!P.keep_dir) {
-        s.k0 = ko0; s.k1 = ko1; s.k2 = ko2;
+        s.kx = ox; s.ky = oy; s.kz = oz;
         s.inv_ok = false;
     }
     ++tl.scatt_line;
 }
 
 template <int NL>
-__device__ __forceinline__ void trace_record(const Params& P, const Packet<NL>& s, const TraceOut& tr) {
-    if (tr.nev == nullptr) return;
+__device__ __forceinline__ void trace_record(const Packet<NL>& s, const TraceOut& tr, double nu_ext) {
     int32_t c = tr.nev[s.idx];
     if (c >= tr.max_events) return;
     TraceEvent& e = tr.ev[(long long)s.idx * tr.max_events + c];
-    const double k[3] = {s.k0, s.k1, s.k2};
-    double b = beta_of(s.cc, k);
     e.p[0] = s.p0; e.p[1] = s.p1; e.p[2] = s.p2;
-    e.k[0] = s.k0; e.k[1] = s.k1; e.k[2] = s.k2;
-    e.nu = (s.status == RASCAS_PK_ERROR_ && s.w.leaf < 0) ? s.nu : to_ext(s.nu, b);
+    e.k[0] = s.kx; e.k[1] = s.ky; e.k[2] = s.kz;
+    e.nu = nu_ext;
     e.leaf = s.w.leaf; e.level = s.w.level; e.ijk[0] = s.w.i; e.ijk[1] = s.w.j; e.ijk[2] = s.w.k;
     e.status = s.status;
     e.ndraw = s.rng.n;
@@ -299,130 +307,24 @@ __device__ __forceinline__ void trace_record(const Params& P, const Packet<NL>& 
     tr.nev[s.idx] = c + 1;
 }
 
-template <int NL, bool PEEL>
-__device__ __forceinline__ void interact(const Params& P, Packet<NL>& s, double li, bool exact, float kap,
-                                         const float kl[NL], Tallies& tl, const TraceOut& tr) {
-    s.p0 = __fma_rn(li, s.k0, s.p0);
-    s.p1 = __fma_rn(li, s.k1, s.p1);
-    s.p2 = __fma_rn(li, s.k2, s.p2);
-    s.path += li;
-    if (exact) {
-        const double p[3] = {s.p0, s.p1, s.p2};
-        double D = inner_distance(p, s.w);
-        s.budget = __fsub_rd(__double2float_rd(D * (1.0 - 0x1p-20)), 4e-16f);
-    }
-    // Sect. 3.2: dust with P = tau_d / tau, else line X with P = tau_X / tau
-    float r = s.rng.u24();
-    float rk = r * kap;
-    if (rk < s.cc.kap_d) {
-        scatter_dust<NL, PEEL>(P, s, tl);
-    } else {
-        float acc = s.cc.kap_d;
-        int il = NL - 1;
-#pragma unroll
-        for (int i = NL - 2; i >= 0; --i) {
-            float ai = acc;
-#pragma unroll
-            for (int j = 0; j <= i; ++j) ai += kl[j];
-            if (rk < ai) il = i;
-        }
-        if (il == 0) scatter_line<NL, PEEL, 0>(P, s, tl);
-        if (NL > 1 && il == 1) scatter_line<NL, PEEL, (NL > 1 ? 1 : 0)>(P, s, tl);
-        if (NL > 2 && il == 2) scatter_line<NL, PEEL, (NL > 2 ? 2 : 0)>(P, s, tl);
-        if (NL > 3 && il == 3) scatter_line<NL, PEEL, (NL > 3 ? 3 : 0)>(P, s, tl);
-    }
-    if (s.status == RASCAS_PK_ACTIVE_) {
-        ++s.nscatt;
-        if (P.max_scatt > 0 && s.nscatt >= P.max_scatt) s.status = RASCAS_PK_CAPPED_;
-    }
-    trace_record<NL>(P, s, tr);
-    if (s.status == RASCAS_PK_ACTIVE_) s.tau = tau_event(s.rng.u52());
+// external-frame frequency of the packet now
+template <int NL>
+__device__ __forceinline__ double nu_ext_now(const Params& P, const Packet<NL>& s) {
+    if (s.w.leaf < 0 || s.enter) return s.nu_enter;
+    const double k[3] = {(double)s.kx, (double)s.ky, (double)s.kz};
+    return to_ext(nu_of_x(P, s.cc, s.xh, s.xl), beta_of(s.cc, k));
 }
 
-// one walk step: an interaction inside the current leaf, a face crossing, or
-// the escape through the domain border (Sect. 3, Sect. 4.3)
-template <int NL, bool PEEL>
-__device__ __forceinline__ void step(const Params& P, Packet<NL>& s, Tallies& tl, const TraceOut& tr) {
-    if (P.max_steps > 0 && s.nsteps >= P.max_steps) {
-        s.status = RASCAS_PK_CAPPED_;
-        trace_record<NL>(P, s, tr);
-        return;
-    }
-    ++s.nsteps;
-    float kl[NL];
-    float kap = opacity<NL>(P, s.cc, s.nu, kl);
-    const bool border_leaf = (s.cc.flags & kFlagBorder) != 0;
-    if (!border_leaf) {
-        float li = (float)s.tau / (kap * (float)P.box_cm);
-        float dec = __fmaf_ru(li, 1.0f + 0x1p-20f, 4e-16f);
-        if (dec < s.budget) {
-            s.budget = __fsub_rd(s.budget, dec);
-            interact<NL, PEEL>(P, s, (double)li, false, kap, kl, tl, tr);
-            return;
-        }
-    }
-    if (!s.inv_ok) {
-        s.i0 = s.k0 != 0.0 ? 1.0 / s.k0 : 0.0;
-        s.i1 = s.k1 != 0.0 ? 1.0 / s.k1 : 0.0;
-        s.i2 = s.k2 != 0.0 ? 1.0 / s.k2 : 0.0;
-        s.inv_ok = true;
-    }
-    double p[3] = {s.p0, s.p1, s.p2};
-    const double k[3] = {s.k0, s.k1, s.k2};
-    const double inv[3] = {s.i0, s.i1, s.i2};
-    int axis;
-    double tf = face_distance(p, k, inv, s.w, axis);
-    double tb = border_leaf ? border_distance(P, p, k, inv) : kInf;
-    bool border = tb <= tf;
-    double l = border ? tb : tf;
-    double tau_cell = __dmul_rn(__dmul_rn((double)kap, l), P.box_cm);
-    if (tau_cell >= s.tau) {
-        double li = s.tau / __dmul_rn((double)kap, P.box_cm);
-        interact<NL, PEEL>(P, s, li, true, kap, kl, tl, tr);
-        return;
-    }
-    s.tau = __dsub_rn(s.tau, tau_cell);
-    s.path += l;
-    if (border) {
-        s.p0 = __fma_rn(l, s.k0, s.p0);
-        s.p1 = __fma_rn(l, s.k1, s.p1);
-        s.p2 = __fma_rn(l, s.k2, s.p2);
-        s.status = RASCAS_PK_ESCAPED_;
-        trace_record<NL>(P, s, tr);
-        return;
-    }
-    ++tl.cross;
-    s.zero_run = tf > 0.0 ? 0 : s.zero_run + 1;
-    if (s.zero_run > 64) {
-        s.status = RASCAS_PK_ERROR_;
-        trace_record<NL>(P, s, tr);
-        return;
-    }
-    double nu_ext = to_ext(s.nu, beta_of(s.cc, k));
-    move_to_face(p, k, axis, tf, s.w);
-    wrap_periodic(P, p, k);
-    s.p0 = p[0]; s.p1 = p[1]; s.p2 = p[2];
-    Where nw = s.w;
-    if (!next_leaf(P, p, k, axis, nw, tl.son_loads, tl.nbor_loads)) {
-        s.status = RASCAS_PK_ESCAPED_;   // left the box
-        trace_record<NL>(P, s, tr);
-        return;
-    }
-    s.w = nw;
-    load_cell<NL>(P, s.w.leaf, s.cc);
-    ++tl.leaf_loads;
-    s.nu = to_gas(nu_ext, beta_of(s.cc, k));
-    s.budget = 0.0f;
-}
-
-template <int NL, bool PEEL>
-__device__ __forceinline__ void start_packet(const Params& P, const PacketsIn& in, long long idx, Packet<NL>& s,
+// packet start: read the initial condition, key its random stream, find its
+// leaf, draw its first tau_event (Sect. 2: PPIC lists; Sect. 3)
+template <int NL>
+__device__ __forceinline__ void begin_packet(const Params& P, const PacketsIn& in, long long idx, Packet<NL>& s,
                                              Tallies& tl, const TraceOut& tr) {
     s.idx = idx;
     double p[3] = {in.pos[3 * idx], in.pos[3 * idx + 1], in.pos[3 * idx + 2]};
     const double k[3] = {in.dir[3 * idx], in.dir[3 * idx + 1], in.dir[3 * idx + 2]};
-    s.k0 = k[0]; s.k1 = k[1]; s.k2 = k[2];
-    double nu_ext = in.nu[idx];
+    s.kx = (float)k[0]; s.ky = (float)k[1]; s.kz = (float)k[2];
+    s.nu_enter = in.nu[idx];
     s.rng.init(P, in.id[idx]);
     s.nscatt = 0;
     s.nsteps = 0;
@@ -431,43 +333,34 @@ __device__ __forceinline__ void start_packet(const Params& P, const PacketsIn& i
     s.inv_ok = false;
     s.zero_run = 0;
     s.status = RASCAS_PK_ACTIVE_;
+    s.enter = true;
+    s.fresh = true;
     wrap_periodic(P, p, k);
     s.p0 = p[0]; s.p1 = p[1]; s.p2 = p[2];
     if (!locate_point(P, p, k, s.w, tl.son_loads)) {
         s.status = RASCAS_PK_ERROR_;
-        s.nu = nu_ext;
+        s.enter = false;
         s.w.leaf = -1; s.w.oct = 0; s.w.level = 0; s.w.i = s.w.j = s.w.k = 0;
-        s.cc.vx = s.cc.vy = s.cc.vz = 0.0f;
-        trace_record<NL>(P, s, tr);
-        return;
     }
-    load_cell<NL>(P, s.w.leaf, s.cc);
-    ++tl.leaf_loads;
-    s.nu = to_gas(nu_ext, beta_of(s.cc, k));
-    if (PEEL) {
-#pragma unroll
-        for (int d = 0; d < kMaxDirs; ++d)
-            if (d < P.ndir)
-                peel_add<NL>(P.self, s.p0, s.p1, s.p2, s.w, s.cc.vx, s.cc.vy, s.cc.vz, d,
-                             1.0f / (2.0f * kTwoPiF), s.nu, &tl);
+    if (tr.nev) trace_record<NL>(s, tr, s.nu_enter);
+    if (s.status == RASCAS_PK_ACTIVE_) {
+        s.tauf = s.rng.tau_event();
+        s.tau_fresh = true;
     }
-    trace_record<NL>(P, s, tr);
-    s.tau = tau_event(s.rng.u52());
 }
 
 template <int NL>
 __device__ __forceinline__ void finish_packet(const Params& P, const Packet<NL>& s, const PacketsOut& out,
                                               uint32_t& c_pk, uint32_t& c_esc, uint32_t& c_abs, uint32_t& c_cap,
                                               uint32_t& c_err) {
-    const double k[3] = {s.k0, s.k1, s.k2};
-    double nu_ext = (s.status == RASCAS_PK_ERROR_ && s.w.leaf < 0) ? s.nu : to_ext(s.nu, beta_of(s.cc, k));
+    double nu_ext = nu_ext_now<NL>(P, s);
     long long i = s.idx;
     if (out.status) out.status[i] = s.status;
     if (out.nscatt) out.nscatt[i] = s.nscatt;
     if (out.nu) out.nu[i] = nu_ext;
     if (out.path) out.path[i] = s.path;
     if (out.pos) { out.pos[3 * i] = s.p0; out.pos[3 * i + 1] = s.p1; out.pos[3 * i + 2] = s.p2; }
-    if (out.dir) { out.dir[3 * i] = s.k0; out.dir[3 * i + 1] = s.k1; out.dir[3 * i + 2] = s.k2; }
+    if (out.dir) { out.dir[3 * i] = s.kx; out.dir[3 * i + 1] = s.ky; out.dir[3 * i + 2] = s.kz; }
     ++c_pk;
     c_esc += s.status == RASCAS_PK_ESCAPED_;
     c_abs += s.status == RASCAS_PK_ABSORBED_;
@@ -480,6 +373,156 @@ __device__ __forceinline__ void finish_packet(const Params& P, const Packet<NL>&
     }
 }
 
+// one loop iteration for an active packet: enter a leaf if needed, then one
+// walk step -- an interaction inside the leaf, a face crossing, or the
+// escape through the domain border (Sect. 3, Sect. 4.3).  Each phase appears
+// once, so the loop body stays small for the instruction cache.
+template <int NL, bool PEEL>
+__device__ __forceinline__ void advance(const Params& P, Packet<NL>& s, Tallies& tl, const TraceOut& tr) {
+    bool evt = false;
+    if (s.enter) {
+        load_cell<NL>(P, s.w.leaf, s.cc);
+        ++tl.leaf_loads;
+        const double k[3] = {(double)s.kx, (double)s.ky, (double)s.kz};
+        double nu_gas = to_gas(s.nu_enter, beta_of(s.cc, k));
+        x_of_nu(P, s.cc, nu_gas, s.xh, s.xl);
+        s.budget = 0.0f;
+        s.enter = false;
+        if (PEEL && s.fresh) {
+            // peeling of the isotropic emission (weight 1/4pi per sr)
+#pragma unroll
+            for (int d = 0; d < kMaxDirs; ++d)
+                if (d < P.ndir)
+                    peel_add<NL>(P.self, s.p0, s.p1, s.p2, s.w, s.cc.vx, s.cc.vy, s.cc.vz, d,
+                                 1.0f / (2.0f * kTwoPiF), nu_gas, &tl);
+        }
+        s.fresh = false;
+    }
+    if (P.max_steps > 0 && s.nsteps >= P.max_steps) {
+        s.status = RASCAS_PK_CAPPED_;
+        evt = true;
+    } else {
+        ++s.nsteps;
+        float kl[NL], xin[NL];
+        const float kap = opacity_x<NL>(P, s.cc, s.xh, s.xl, kl, xin);
+        const bool border_leaf = (s.cc.flags & kFlagBorder) != 0;
+        bool inter = false, exact = false;
+        float li_f = 0.0f;
+        double li_d = 0.0;
+        if (!border_leaf) {
+            li_f = s.tauf / (kap * (float)P.box_cm);
+            float dec = __fmaf_ru(li_f, 1.0f + 0x1p-20f, 4e-16f);
+            if (dec < s.budget) {
+                s.budget = __fsub_rd(s.budget, dec);
+                inter = true;
+            }
+        }
+        if (!inter) {
+            // exact FP64 step: distances to the faces and the border
+            if (s.tau_fresh) {
+                s.tau = (double)s.tauf;
+                s.tau_fresh = false;
+            }
+            const double k[3] = {(double)s.kx, (double)s.ky, (double)s.kz};
+            if (!s.inv_ok) {
+                s.i0 = k[0] != 0.0 ? 1.0 / k[0] : 0.0;
+                s.i1 = k[1] != 0.0 ? 1.0 / k[1] : 0.0;
+                s.i2 = k[2] != 0.0 ? 1.0 / k[2] : 0.0;
+                s.inv_ok = true;
+            }
+            double p[3] = {s.p0, s.p1, s.p2};
+            const double inv[3] = {s.i0, s.i1, s.i2};
+            int axis;
+            double tf = face_distance(p, k, inv, s.w, axis);
+            double tb = border_leaf ? border_distance(P, p, k, inv) : kInf;
+            bool border = tb <= tf;
+            double l = border ? tb : tf;
+            double tau_cell = __dmul_rn(__dmul_rn((double)kap, l), P.box_cm);
+            if (tau_cell >= s.tau) {
+                li_d = s.tau / __dmul_rn((double)kap, P.box_cm);
+                inter = true;
+                exact = true;
+            } else {
+                s.tau = __dsub_rn(s.tau, tau_cell);
+                s.tauf = (float)s.tau;
+                s.path += l;
+                if (border) {
+                    s.p0 = __fma_rn(l, k[0], s.p0);
+                    s.p1 = __fma_rn(l, k[1], s.p1);
+                    s.p2 = __fma_rn(l, k[2], s.p2);
+                    s.status = RASCAS_PK_ESCAPED_;
+                    evt = true;
+                } else {
+                    ++tl.cross;
+                    s.zero_run = tf > 0.0 ? 0 : s.zero_run + 1;
+                    double nu_ext = to_ext(nu_of_x(P, s.cc, s.xh, s.xl), beta_of(s.cc, k));
+                    move_to_face(p, k, axis, tf, s.w);
+                    wrap_periodic(P, p, k);
+                    s.p0 = p[0]; s.p1 = p[1]; s.p2 = p[2];
+                    Where nw = s.w;
+                    if (s.zero_run > 64) {
+                        s.status = RASCAS_PK_ERROR_;   // stuck walk
+                        evt = true;
+                    } else if (!next_leaf(P, p, k, axis, nw, tl.son_loads, tl.nbor_loads)) {
+                        s.status = RASCAS_PK_ESCAPED_;   // left the box
+                        evt = true;
+                    } else {
+                        s.w = nw;
+                        s.nu_enter = nu_ext;
+                        s.enter = true;
+                    }
+                }
+            }
+        }
+        if (inter) {
+            if (exact) {
+                s.p0 = __fma_rn(li_d, (double)s.kx, s.p0);
+                s.p1 = __fma_rn(li_d, (double)s.ky, s.p1);
+                s.p2 = __fma_rn(li_d, (double)s.kz, s.p2);
+                s.path += li_d;
+                const double p[3] = {s.p0, s.p1, s.p2};
+                double D = inner_distance(p, s.w);
+                s.budget = __fsub_rd(__double2float_rd(D * (1.0 - 0x1p-20)), 4e-16f);
+            } else {
+                s.p0 += (double)(li_f * s.kx);
+                s.p1 += (double)(li_f * s.ky);
+                s.p2 += (double)(li_f * s.kz);
+                s.path += (double)li_f;
+            }
+            // Sect. 3.2: dust with P = tau_d / tau, else line X with P = tau_X / tau
+            float rk = s.rng.u24() * kap;
+            if (rk < s.cc.kap_d) {
+                scatter_dust<NL, PEEL>(P, s, tl);
+            } else {
+                int il = NL - 1;
+#pragma unroll
+                for (int i = NL - 2; i >= 0; --i) {
+                    float ai = s.cc.kap_d;
+#pragma unroll
+                    for (int j = 0; j <= i; ++j) ai += kl[j];
+                    if (rk < ai) il = i;
+                }
+                if (il == 0) scatter_line<NL, PEEL, 0>(P, s, xin[0], tl);
+                if (NL > 1 && il == 1) scatter_line<NL, PEEL, (NL > 1 ? 1 : 0)>(P, s, xin[NL > 1 ? 1 : 0], tl);
+                if (NL > 2 && il == 2) scatter_line<NL, PEEL, (NL > 2 ? 2 : 0)>(P, s, xin[NL > 2 ? 2 : 0], tl);
+                if (NL > 3 && il == 3) scatter_line<NL, PEEL, (NL > 3 ? 3 : 0)>(P, s, xin[NL > 3 ? 3 : 0], tl);
+            }
+            if (s.status == RASCAS_PK_ACTIVE_) {
+                ++s.nscatt;
+                if (P.max_scatt > 0 && s.nscatt >= P.max_scatt) s.status = RASCAS_PK_CAPPED_;
+            }
+            evt = true;
+            if (s.status == RASCAS_PK_ACTIVE_) {
+                if (tr.nev) trace_record<NL>(s, tr, nu_ext_now<NL>(P, s));
+                evt = false;
+                s.tauf = s.rng.tau_event();
+                s.tau_fresh = true;
+            }
+        }
+    }
+    if (evt && tr.nev) trace_record<NL>(s, tr, nu_ext_now<NL>(P, s));
+}
+
 __device__ __forceinline__ void flush(const Params& P, unsigned long long v, int which) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
@@ -487,7 +530,7 @@ __device__ __forceinline__ void flush(const Params& P, unsigned long long v, int
 }
 
 template <int NL, bool PEEL>
-__global__ void __launch_bounds__(128) k_propagate(Params P, PacketsIn in, PacketsOut out, TraceOut tr) {
+__global__ void __launch_bounds__(128, PEEL ? 2 : 4) k_propagate(Params P, PacketsIn in, PacketsOut out, TraceOut tr) {
     Packet<NL> s;
     Tallies tl = {};
     uint32_t c_pk = 0, c_esc = 0, c_abs = 0, c_cap = 0, c_err = 0;
@@ -504,9 +547,8 @@ __global__ void __launch_bounds__(128) k_propagate(Params P, PacketsIn in, Packe
             if (want) {
                 long long idx = (long long)base + __popc(m & ((1u << lane) - 1u));
                 if (idx < in.n) {
-                    start_packet<NL, PEEL>(P, in, idx, s, tl, tr);
-                    if (s.status == RASCAS_PK_ACTIVE_) have = true;
-                    else finish_packet<NL>(P, s, out, c_pk, c_esc, c_abs, c_cap, c_err);
+                    begin_packet<NL>(P, in, idx, s, tl, tr);
+                    have = true;
                 } else {
                     drained = true;
                 }
@@ -517,7 +559,7 @@ __global__ void __launch_bounds__(128) k_propagate(Params P, PacketsIn in, Packe
             continue;
         }
         if (have) {
-            step<NL, PEEL>(P, s, tl, tr);
+            if (s.status == RASCAS_PK_ACTIVE_) advance<NL, PEEL>(P, s, tl, tr);
             if (s.status != RASCAS_PK_ACTIVE_) {
                 finish_packet<NL>(P, s, out, c_pk, c_esc, c_abs, c_cap, c_err);
                 have = false;
