@@ -17,8 +17,9 @@
  * design notes):
  *  - RNG: Philox4x32-10; key = 64-bit run seed, counter = (draw block lo,
  *    draw block hi, packet id lo, packet id hi); draw word n of a packet is
- *    word (n mod 4) of block n/4.  u24 = ((w>>8)+1/2) 2^-24 for every
- *    single-precision draw, u52 from two words for tau_event.
+ *    word (n mod 4) of block n/4.  u23 = ((w>>9)+1/2) 2^-23 for every
+ *    single-precision draw (exactly representable in FP32 together with
+ *    1 - u23), u52 from two words for tau_event.
  *  - Fixed draw order per event: tau_event (2 words); interaction choice (1);
  *    dust: albedo (1), mu (1), phi (1); line: channel (1, only when the line
  *    has several decay channels), u_par trials (3 words per trial, 2 for the
@@ -139,10 +140,10 @@ ORA_API uint32_t ora_word(uint64_t seed, uint64_t pid, uint64_t n)
     return out[n & 3];
 }
 
-static double u24(const ora_cfg *cf, ora_state *s)
+static double u23(const ora_cfg *cf, ora_state *s)
 {
     uint32_t w = ora_word(cf->seed, s->pid, s->ndraw++);
-    return ((double)(w >> 8) + 0.5) * 0x1p-24;
+    return ((double)(w >> 9) + 0.5) * 0x1p-23;
 }
 
 static double u52(const ora_cfg *cf, ora_state *s)
@@ -242,7 +243,7 @@ static double sample_upar(const ora_cfg *cf, ora_state *s, double x, double a, i
     double sgn = x < 0.0 ? -1.0 : 1.0;
     double xa = fabs(x);
     if (xa >= cf->x_gauss) {
-        double r1 = u24(cf, s), r2 = u24(cf, s);
+        double r1 = u23(cf, s), r2 = u23(cf, s);
         return sgn * (1.0 / xa + sqrt(-log(r1)) * cos(2.0 * OPI * r2));
     }
     double u0 = ora_u0(xa, a);
@@ -250,7 +251,7 @@ static double sample_upar(const ora_cfg *cf, ora_state *s, double x, double a, i
     double e0 = exp(-u0 * u0);
     double p = (th0 + OPI / 2) / ((1.0 - e0) * th0 + (1.0 + e0) * OPI / 2);
     for (long trial = 0; trial < 100000000L; ++trial) {
-        double r1 = u24(cf, s), r2 = u24(cf, s), r3 = u24(cf, s);
+        double r1 = u23(cf, s), r2 = u23(cf, s), r3 = u23(cf, s);
         double u;
         if (r1 <= p) {
             double th = -OPI / 2 + (th0 + OPI / 2) * r2;
@@ -576,12 +577,12 @@ static void peel_emission(const ora_cfg *cf, ora_tally *ty, const ora_state *s, 
 
 static void scatter_dust(const ora_cfg *cf, ora_state *s, ora_tally *ty, double nu_gas)
 {
-    double r_alb = u24(cf, s);
+    double r_alb = u23(cf, s);
     if (r_alb > cf->dust_albedo) {
         s->status = ORA_ABSORBED;
         return;
     }
-    double r_mu = u24(cf, s), r_phi = u24(cf, s);
+    double r_mu = u23(cf, s), r_phi = u23(cf, s);
     double mu = ora_mu_sample(PH_HG, r_mu, cf->dust_g);
     double kin[3] = {s->k[0], s->k[1], s->k[2]};
     double kout[3];
@@ -607,7 +608,7 @@ static int scatter_line(const ora_cfg *cf, ora_state *s, ora_tally *ty, int il, 
     /* decay channel (Sect. 3.2.3): P_i = A_i / sum A */
     int ch = 0;
     if (cf->line_nchan[il] > 1) {
-        double r = u24(cf, s);
+        double r = u23(cf, s);
         double Atot = 0.0;
         for (int c = 0; c < cf->line_nchan[il]; ++c) Atot += cf->chan_A[il][c];
         double acc = 0.0;
@@ -623,7 +624,7 @@ static int scatter_line(const ora_cfg *cf, ora_state *s, ora_tally *ty, int il, 
     int err = 0;
     double upar = sample_upar(cf, s, lp.x, lp.a, &err);
     if (err) return 1;
-    double r1 = u24(cf, s), r2 = u24(cf, s);
+    double r1 = u23(cf, s), r2 = u23(cf, s);
     double rho = sqrt(-log(r1));
     double up1 = rho * cos(2.0 * OPI * r2), up2 = rho * sin(2.0 * OPI * r2);
     double kin[3] = {s->k[0], s->k[1], s->k[2]};
@@ -634,7 +635,7 @@ static int scatter_line(const ora_cfg *cf, ora_state *s, ora_tally *ty, int il, 
     int kind;
     if (ch > 0 || cf->isotropic || cf->line_phase[il] != 0) kind = PH_ISO;
     else kind = fabs(lp.x - upar) < 0.2 ? PH_CORE : PH_WING;
-    double r_mu = u24(cf, s), r_phi = u24(cf, s);
+    double r_mu = u23(cf, s), r_phi = u23(cf, s);
     double mu = ora_mu_sample(kind, r_mu, 0.0);
     double kout[3];
     if (cf->keep_dir) {
@@ -716,7 +717,7 @@ ORA_API int ora_event(const ora_cfg *cf, ora_state *s, ora_tally *ty)
             double li = tau_rem / (kap * cf->box_cm);
             for (int ax = 0; ax < 3; ++ax) s->p[ax] = fma(li, s->k[ax], s->p[ax]);
             s->path += li;
-            double r = u24(cf, s);
+            double r = u23(cf, s);
             double nu_gas = s->nu / (1.0 + beta_of(cf, s->leaf, s->k));
             /* Sect. 3.2: dust with P = tau_d/tau, else line X with P = tau_X/tau */
             double acc = kd;

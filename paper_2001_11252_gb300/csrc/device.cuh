@@ -54,9 +54,10 @@ struct Rng {
         ++n;
         return j == 0u ? w0 : (j == 1u ? w1 : (j == 2u ? w2 : w3));
     }
-    // ((w >> 8) + 1/2) 2^-24: exactly representable, in (0, 1)
-    __device__ __forceinline__ float u24() {
-        return __uint2float_rn(word() >> 8) * 0x1p-24f + 0x1p-25f;
+    // ((w >> 9) + 1/2) 2^-23: in (0, 1), exactly representable in FP32, and
+    // so is 1 - u
+    __device__ __forceinline__ float u23() {
+        return __uint2float_rn(word() >> 9) * 0x1p-23f + 0x1p-24f;
     }
     // ((wa >> 6) 2^26 + (wb >> 6) + 1/2) 2^-52 from two consecutive words
     __device__ __forceinline__ double u52() {
@@ -159,7 +160,7 @@ __device__ __forceinline__ float sample_upar(Rng& rng, float x, float a, const U
     float sg = x < 0.0f ? -1.0f : 1.0f;
     float xa = fabsf(x);
     if (xa >= x_gauss) {
-        float r1 = rng.u24(), r2 = rng.u24();
+        float r1 = rng.u23(), r2 = rng.u23();
         trials += 1;
         return sg * (1.0f / xa + sqrtf(-logf(r1)) * cospif(2.0f * r2));
     }
@@ -179,7 +180,7 @@ __device__ __forceinline__ float sample_upar(Rng& rng, float x, float a, const U
     float p = A / (A + e0 * B);
     float u0sq = u0 * u0;
     for (uint32_t n = 0; n < (1u << 22); ++n) {
-        float r1 = rng.u24(), r2 = rng.u24(), r3 = rng.u24();
+        float r1 = rng.u23(), r2 = rng.u23(), r3 = rng.u23();
         ++trials;
         const bool b1 = r1 <= p;
         float tn = tanf(b1 ? A * r2 : B * (1.0f - r2));
@@ -200,16 +201,29 @@ enum { PH_ISO = 0, PH_CORE = 1, PH_WING = 2, PH_HG = 3 };
 // mu and sin(theta) = sqrt(1 - mu^2), the latter formed from (1 - mu)(1 + mu)
 // so that it stays accurate near forward / backward scattering
 __device__ __forceinline__ float mu_sample(int kind, float r, float g, float& st) {
-    float mu;
-    if (kind == PH_CORE) {
-        float B = 6.0f * (2.0f * r - 1.0f);
-        float A = sqrtf(B * B + 49.296296296296296f);  // 11^3 / 27
-        mu = cbrtf(A + B) - cbrtf(A - B);
-    } else if (kind == PH_WING) {
-        float B = 4.0f * r - 2.0f;
-        float A = sqrtf(B * B + 1.0f);
-        mu = cbrtf(A + B) - cbrtf(A - B);
-    } else if (kind == PH_HG && g != 0.0f) {
+    if (kind == PH_CORE || kind == PH_WING) {
+        // Cardano root of the CDF cubic, then one fixed-point step on 1 + mu
+        // (mu < 0) or 1 - mu (mu >= 0), which the difference of cube roots
+        // loses near mu = -1 / +1: with v = 1 + mu the cubic reads
+        // v (v^2 - 3v + c1) = c2 r, with w = 1 - mu  w (w^2 - 3w + c1) = c2 (1 - r)
+        // (core: c1 = 14, c2 = 24; wing: c1 = 6, c2 = 8)
+        const bool core = kind == PH_CORE;
+        float B = core ? 6.0f * (2.0f * r - 1.0f) : 4.0f * r - 2.0f;
+        float A = sqrtf(B * B + (core ? 49.296296296296296f : 1.0f));   // 11^3/27 or 1
+        float mu = cbrtf(A + B) - cbrtf(A - B);
+        const float c1 = core ? 14.0f : 6.0f, c2 = core ? 24.0f : 8.0f;
+        if (mu < 0.0f) {
+            float v = fmaxf(0.0f, 1.0f + mu);
+            v = c2 * r / (v * v - 3.0f * v + c1);
+            st = sqrtf(fmaxf(0.0f, v * (2.0f - v)));
+            return v - 1.0f;
+        }
+        float w = fmaxf(0.0f, 1.0f - mu);
+        w = c2 * (1.0f - r) / (w * w - 3.0f * w + c1);
+        st = sqrtf(fmaxf(0.0f, w * (2.0f - w)));
+        return 1.0f - w;
+    }
+    if (kind == PH_HG && g != 0.0f) {
         float t = (1.0f - g * g) / (1.0f - g + 2.0f * g * r);
         float inv2g = 0.5f / g;
         float omu = (t - (1.0f - g)) * (t + (1.0f - g)) * inv2g;   // 1 - mu
@@ -218,13 +232,9 @@ __device__ __forceinline__ float mu_sample(int kind, float r, float g, float& st
         opu = fminf(2.0f, fmaxf(0.0f, opu));
         st = sqrtf(omu * opu);
         return fminf(1.0f, fmaxf(-1.0f, 1.0f - omu));
-    } else {
-        st = 2.0f * sqrtf(r * (1.0f - r));
-        return 2.0f * r - 1.0f;
     }
-    mu = fminf(1.0f, fmaxf(-1.0f, mu));
-    st = sqrtf(fmaxf(0.0f, (1.0f - mu) * (1.0f + mu)));
-    return mu;
+    st = 2.0f * sqrtf(r * (1.0f - r));
+    return 2.0f * r - 1.0f;
 }
 
 // phase function per unit mu (integrates to one over [-1, 1])

@@ -153,12 +153,12 @@ __device__ __noinline__ void peel_add(const Params* __restrict__ G, double p0, d
 // ---------------------------------------------------------------------------
 template <int NL, bool PEEL>
 __device__ __forceinline__ void scatter_dust(const Params& P, Packet<NL>& s, Tallies& tl) {
-    float r_alb = s.rng.u24();
+    float r_alb = s.rng.u23();
     if (r_alb > P.dust_albedo) {
         s.status = RASCAS_PK_ABSORBED_;
         return;
     }
-    float r_mu = s.rng.u24(), r_phi = s.rng.u24();
+    float r_mu = s.rng.u23(), r_phi = s.rng.u23();
     float st;
     float mu = mu_sample(PH_HG, r_mu, P.dust_g, st);
     if (PEEL) {
@@ -197,7 +197,7 @@ __device__ __forceinline__ void scatter_line(const Params& P, Packet<NL>& s, flo
     int ch = 0;
     double chnu = L.nu0;
     if (L.nchan > 1) {
-        float r = s.rng.u24();
+        float r = s.rng.u23();
         ch = L.nchan - 1;
 #pragma unroll
         for (int c = kMaxChan - 2; c >= 0; --c)
@@ -230,7 +230,7 @@ __device__ __forceinline__ void scatter_line(const Params& P, Packet<NL>& s, flo
         s.status = RASCAS_PK_ERROR_;
         return;
     }
-    float r1 = s.rng.u24(), r2 = s.rng.u24();
+    float r1 = s.rng.u23(), r2 = s.rng.u23();
     float rho = sqrtf(-logf(r1));
     float sn, cs;
     sincospif(2.0f * r2, &sn, &cs);
@@ -244,7 +244,7 @@ __device__ __forceinline__ void scatter_line(const Params& P, Packet<NL>& s, flo
     int kind;
     if (ch > 0 || P.isotropic || L.phase != 0) kind = PH_ISO;
     else kind = fabsf(x_in - upar) < 0.2f ? PH_CORE : PH_WING;
-    float r_mu = s.rng.u24(), r_phi = s.rng.u24();
+    float r_mu = s.rng.u23(), r_phi = s.rng.u23();
     float st;
     float mu = mu_sample(kind, r_mu, 0.0f, st);
     float ox = kx, oy = ky, oz = kz;
@@ -484,13 +484,14 @@ __device__ __forceinline__ void advance(const Params& P, Packet<NL>& s, Tallies&
                 double D = inner_distance(p, s.w);
                 s.budget = __fsub_rd(__double2float_rd(D * (1.0 - 0x1p-20)), 4e-16f);
             } else {
-                s.p0 += (double)(li_f * s.kx);
-                s.p1 += (double)(li_f * s.ky);
-                s.p2 += (double)(li_f * s.kz);
-                s.path += (double)li_f;
+                const double l = (double)li_f;
+                s.p0 = __fma_rn(l, (double)s.kx, s.p0);
+                s.p1 = __fma_rn(l, (double)s.ky, s.p1);
+                s.p2 = __fma_rn(l, (double)s.kz, s.p2);
+                s.path += l;
             }
             // Sect. 3.2: dust with P = tau_d / tau, else line X with P = tau_X / tau
-            float rk = s.rng.u24() * kap;
+            float rk = s.rng.u23() * kap;
             if (rk < s.cc.kap_d) {
                 scatter_dust<NL, PEEL>(P, s, tl);
             } else {
