@@ -123,30 +123,44 @@ __device__ __forceinline__ float voigt_h2(float a, float xh, float xl) {
 // the fitted separation u0(x, log10 a), clamped at 0; |x| >= x_gauss: Gaussian
 // N(1/|x|, 1/2).  Returns u_par for frequency x (scatterer's Doppler units).
 // ---------------------------------------------------------------------------
-// The x-polynomial of u0 cancels heavily for x ~ 5-8 (terms of a few hundred
-// summing to O(1)) and u_par moves one-for-one with u0, so both the
-// coefficients in zeta = log10 a and the Horner sum in x are FP64.  The six
-// coefficients depend only on a (the line and the cell's T); the propagation
-// kernel computes them once per leaf and line and keeps them in shared memory.
+// u0(x, zeta) of Sect. 3.3.3 is a degree-5 polynomial in x whose monomial
+// form cancels heavily for x ~ 5-8 (terms of a few hundred summing to O(1)),
+// while u_par moves one-for-one with u0.  Once per leaf and line the kernel
+// forms the monomial coefficients in FP64 (zeta = log10 a) and re-expresses
+// the same polynomial in Chebyshev polynomials of t = x/4 - 1 on [0, 8]; the
+// per-draw evaluation is then an FP32 Clenshaw sum, accurate to ~6e-7.
 struct U0Coef {
-    double c[6];
+    float b[6];
 };
 
 __device__ __forceinline__ void u0_coeffs(double a, U0Coef& k) {
     double z = log10(a);
-    k.c[0] = __fma_rn(z, __fma_rn(z, 0.351479, 2.014446), 2.648963);
-    k.c[1] = __fma_rn(z, __fma_rn(z, -0.640003, -3.675859), -4.058673);
-    k.c[2] = __fma_rn(z, __fma_rn(z, 0.370294, 2.117133), 3.017395);
-    k.c[3] = __fma_rn(z, __fma_rn(z, -0.096312, -0.565886), -0.869789);
-    k.c[4] = __fma_rn(z, __fma_rn(z, 0.011557, 0.070103), 0.110987);
-    k.c[5] = __fma_rn(z, __fma_rn(z, -0.000519, -0.003240), -0.005200);
+    double c0 = __fma_rn(z, __fma_rn(z, 0.351479, 2.014446), 2.648963);
+    double c1 = __fma_rn(z, __fma_rn(z, -0.640003, -3.675859), -4.058673);
+    double c2 = __fma_rn(z, __fma_rn(z, 0.370294, 2.117133), 3.017395);
+    double c3 = __fma_rn(z, __fma_rn(z, -0.096312, -0.565886), -0.869789);
+    double c4 = __fma_rn(z, __fma_rn(z, 0.011557, 0.070103), 0.110987);
+    double c5 = __fma_rn(z, __fma_rn(z, -0.000519, -0.003240), -0.005200);
+    // x^k = (4 (t + 1))^k in Chebyshev polynomials T_j(t): exact integer weights
+    k.b[0] = (float)(c0 + 4.0 * c1 + 24.0 * c2 + 160.0 * c3 + 1120.0 * c4 + 8064.0 * c5);
+    k.b[1] = (float)(4.0 * c1 + 32.0 * c2 + 240.0 * c3 + 1792.0 * c4 + 13440.0 * c5);
+    k.b[2] = (float)(8.0 * c2 + 96.0 * c3 + 896.0 * c4 + 7680.0 * c5);
+    k.b[3] = (float)(16.0 * c3 + 256.0 * c4 + 2880.0 * c5);
+    k.b[4] = (float)(32.0 * c4 + 640.0 * c5);
+    k.b[5] = (float)(64.0 * c5);
 }
 
 __device__ __forceinline__ float u0_eval(const U0Coef& k, float x) {
-    double xd = (double)x;
-    double u0 = __fma_rn(xd, __fma_rn(xd, __fma_rn(xd, __fma_rn(xd, __fma_rn(xd, k.c[5], k.c[4]), k.c[3]),
-                                                   k.c[2]), k.c[1]), k.c[0]);
-    return fmaxf((float)u0, 0.0f);
+    float t = fmaf(x, 0.25f, -1.0f);
+    float t2 = 2.0f * t;
+    float b1 = 0.0f, b2 = 0.0f;
+#pragma unroll
+    for (int j = 5; j >= 1; --j) {
+        float b0 = fmaf(t2, b1, k.b[j] - b2);
+        b2 = b1;
+        b1 = b0;
+    }
+    return fmaxf(fmaf(t, b1, k.b[0] - b2), 0.0f);
 }
 
 // The two branches of the comparison function are sampled through their
@@ -467,6 +481,7 @@ struct CellCache {
     int flags;
     double invdnu[NL];           // 1 / Delta nu_D (1/Hz)
     double dnu0;                 // Delta nu_D of line 0 (Hz)
+    float dnu0_f;
     double xa[NL], xb[NL];       // x_i = xa_i + xb_i x_0 (line i's Doppler units from line 0's)
     float a[NL], kap0[NL];       // Voigt a, n_X sigma_0 (cm^-1)
     float vth_c[NL];             // v_th / c
@@ -501,6 +516,7 @@ __device__ __forceinline__ void load_cell(const Params& P, int leaf, CellCache<N
         cc.vth_c[i] = L.vth_over_c_pref * T * rs;
     }
     cc.dnu0 = P.line[0].dnu_pref * (Td * rd);
+    cc.dnu0_f = (float)cc.dnu0;
     cc.q0 = 1.0f / cc.vth_c[0];
 #pragma unroll
     for (int i = 1; i < NL; ++i) {

@@ -325,6 +325,7 @@ int rascas_load_octree(rascas_ctx* ctx, const rascas_octree* t, int mem) {
     P.nleaf = nleaf;
     P.noct = noct;
     P.box_cm = t->box_cm;
+    P.box_cm_f = (float)t->box_cm;
     ctx->has_mesh = true;
     return RASCAS_OK;
 }
@@ -357,6 +358,7 @@ int rascas_set_lines(rascas_ctx* ctx, const rascas_line* lines, int32_t nline, c
             return fail(ctx, RASCAS_E_ARG, "lines: bad line data");
         rg::LineDev& D = P.line[i];
         D.nu0 = L.nu0;
+        D.nu0_f = (float)L.nu0;
         double vp = std::sqrt(2.0 * kKB / L.mass_g);
         D.vth_pref = vp;
         D.invdnu_pref = kC / (L.nu0 * vp);

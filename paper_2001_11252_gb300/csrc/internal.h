@@ -30,6 +30,7 @@ enum Counter {
 
 struct LineDev {
     double nu0;          // rest frequency (Hz)
+    float nu0_f;
     double vth_pref;     // sqrt(2 k_B / m): v_th = vth_pref * sqrt(T)
     double invdnu_pref;  // c / nu0 / vth_pref: 1/Delta nu_D = invdnu_pref / sqrt(T)
     double dnu_pref;     // nu0 vth_pref / c: Delta nu_D = dnu_pref sqrt(T)
@@ -56,6 +57,7 @@ struct Params {
     const int4* top;       // [(2^S)^3]: {code, level, oct, 0}
     int top_level, max_level, nleaf, noct;
     double box_cm;
+    float box_cm_f;
     // domain
     int dom_kind;
     double dom_c[3];

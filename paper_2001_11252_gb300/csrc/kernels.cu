@@ -31,6 +31,7 @@ struct Tallies {
 template <int NL>
 struct Packet {
     double p0, p1, p2;     // position (box units)
+    double kd0, kd1, kd2;  // direction used by the FP64 geometry (the sampled FP32 one, or the exact input)
     double i0, i1, i2;     // 1/k per axis (valid when inv_ok)
     double tau;            // optical depth left to the next interaction (formed from tauf when tau_fresh)
     double path;           // distance travelled (box units)
@@ -75,7 +76,8 @@ __device__ __noinline__ double ray_walk(const Params* __restrict__ G, double p0,
     const Params& P = *G;
     double p[3] = {p0, p1, p2};
     const double k[3] = {k0, k1, k2};
-    const double inv[3] = {k0 != 0.0 ? 1.0 / k0 : 0.0, k1 != 0.0 ? 1.0 / k1 : 0.0, k2 != 0.0 ? 1.0 / k2 : 0.0};
+    const double inv[3] = {k0 != 0.0 ? __drcp_rn(k0) : 0.0, k1 != 0.0 ? __drcp_rn(k1) : 0.0,
+                           k2 != 0.0 ? __drcp_rn(k2) : 0.0};
     double tau = 0.0;
     int n = 0, zero_run = 0;
     uint32_t sl = 0, nl = 0, ll = 0;
@@ -174,6 +176,7 @@ __device__ __forceinline__ void scatter_dust(const Params& P, Packet<NL>& s, Tal
     }
     if (!P.keep_dir) {
         dir_from(s.kx, s.ky, s.kz, mu, st, r_phi, s.kx, s.ky, s.kz);
+        s.kd0 = (double)s.kx; s.kd1 = (double)s.ky; s.kd2 = (double)s.kz;
         s.inv_ok = false;
     }
     ++tl.scatt_dust;
@@ -210,16 +213,16 @@ __device__ __forceinline__ void scatter_line(const Params& P, Packet<NL>& s, flo
     // scattering in the leaf, then read from shared memory
     U0Coef u0c;
     {
-        extern __shared__ double s_u0[];
-        double* col = s_u0 + (size_t)IL * 6 * blockDim.x + threadIdx.x;
+        extern __shared__ float s_u0[];
+        float* col = s_u0 + (size_t)IL * 6 * blockDim.x + threadIdx.x;
         if (!(s.cc.u0mask & (1u << IL))) {
             u0_coeffs(L.a_over_invdnu * s.cc.invdnu[IL], u0c);
 #pragma unroll
-            for (int c = 0; c < 6; ++c) col[c * blockDim.x] = u0c.c[c];
+            for (int c = 0; c < 6; ++c) col[c * blockDim.x] = u0c.b[c];
             s.cc.u0mask |= 1u << IL;
         } else {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) u0c.c[c] = col[c * blockDim.x];
+            for (int c = 0; c < 6; ++c) u0c.b[c] = col[c * blockDim.x];
         }
     }
     bool err = false;
@@ -252,7 +255,7 @@ __device__ __forceinline__ void scatter_line(const Params& P, Packet<NL>& s, flo
     else dir_from(kx, ky, kz, mu, st, r_phi, ox, oy, oz);
     const float vthc = s.cc.vth_c[IL];
     // recoil term (1 - mu) h nu / (m c^2) of Eq. (nuout_nuin)
-    const float recp = P.recoil ? L.recoil_pref * ((float)P.line[0].nu0 + s.xh * (float)s.cc.dnu0) : 0.0f;
+    const float recp = P.recoil ? L.recoil_pref * (P.line[0].nu0_f + s.xh * s.cc.dnu0_f) : 0.0f;
     if (PEEL) {
         double nu_in = nu_of_x(P, s.cc, s.xh, s.xl);
 #pragma unroll
@@ -286,6 +289,7 @@ __device__ __forceinline__ void scatter_line(const Params& P, Packet<NL>& s, flo
     }
     if (!P.keep_dir) {
         s.kx = ox; s.ky = oy; s.kz = oz;
+        s.kd0 = (double)ox; s.kd1 = (double)oy; s.kd2 = (double)oz;
         s.inv_ok = false;
     }
     ++tl.scatt_line;
@@ -297,7 +301,7 @@ __device__ __forceinline__ void trace_record(const Packet<NL>& s, const TraceOut
     if (c >= tr.max_events) return;
     TraceEvent& e = tr.ev[(long long)s.idx * tr.max_events + c];
     e.p[0] = s.p0; e.p[1] = s.p1; e.p[2] = s.p2;
-    e.k[0] = s.kx; e.k[1] = s.ky; e.k[2] = s.kz;
+    e.k[0] = s.kd0; e.k[1] = s.kd1; e.k[2] = s.kd2;
     e.nu = nu_ext;
     e.leaf = s.w.leaf; e.level = s.w.level; e.ijk[0] = s.w.i; e.ijk[1] = s.w.j; e.ijk[2] = s.w.k;
     e.status = s.status;
@@ -311,7 +315,7 @@ __device__ __forceinline__ void trace_record(const Packet<NL>& s, const TraceOut
 template <int NL>
 __device__ __forceinline__ double nu_ext_now(const Params& P, const Packet<NL>& s) {
     if (s.w.leaf < 0 || s.enter) return s.nu_enter;
-    const double k[3] = {(double)s.kx, (double)s.ky, (double)s.kz};
+    const double k[3] = {s.kd0, s.kd1, s.kd2};
     return to_ext(nu_of_x(P, s.cc, s.xh, s.xl), beta_of(s.cc, k));
 }
 
@@ -324,6 +328,7 @@ __device__ __forceinline__ void begin_packet(const Params& P, const PacketsIn& i
     double p[3] = {in.pos[3 * idx], in.pos[3 * idx + 1], in.pos[3 * idx + 2]};
     const double k[3] = {in.dir[3 * idx], in.dir[3 * idx + 1], in.dir[3 * idx + 2]};
     s.kx = (float)k[0]; s.ky = (float)k[1]; s.kz = (float)k[2];
+    s.kd0 = k[0]; s.kd1 = k[1]; s.kd2 = k[2];
     s.nu_enter = in.nu[idx];
     s.rng.init(P, in.id[idx]);
     s.nscatt = 0;
@@ -360,7 +365,7 @@ __device__ __forceinline__ void finish_packet(const Params& P, const Packet<NL>&
     if (out.nu) out.nu[i] = nu_ext;
     if (out.path) out.path[i] = s.path;
     if (out.pos) { out.pos[3 * i] = s.p0; out.pos[3 * i + 1] = s.p1; out.pos[3 * i + 2] = s.p2; }
-    if (out.dir) { out.dir[3 * i] = s.kx; out.dir[3 * i + 1] = s.ky; out.dir[3 * i + 2] = s.kz; }
+    if (out.dir) { out.dir[3 * i] = s.kd0; out.dir[3 * i + 1] = s.kd1; out.dir[3 * i + 2] = s.kd2; }
     ++c_pk;
     c_esc += s.status == RASCAS_PK_ESCAPED_;
     c_abs += s.status == RASCAS_PK_ABSORBED_;
@@ -383,7 +388,7 @@ __device__ __forceinline__ void advance(const Params& P, Packet<NL>& s, Tallies&
     if (s.enter) {
         load_cell<NL>(P, s.w.leaf, s.cc);
         ++tl.leaf_loads;
-        const double k[3] = {(double)s.kx, (double)s.ky, (double)s.kz};
+        const double k[3] = {s.kd0, s.kd1, s.kd2};
         double nu_gas = to_gas(s.nu_enter, beta_of(s.cc, k));
         x_of_nu(P, s.cc, nu_gas, s.xh, s.xl);
         s.budget = 0.0f;
@@ -410,7 +415,7 @@ __device__ __forceinline__ void advance(const Params& P, Packet<NL>& s, Tallies&
         float li_f = 0.0f;
         double li_d = 0.0;
         if (!border_leaf) {
-            li_f = s.tauf / (kap * (float)P.box_cm);
+            li_f = s.tauf / (kap * P.box_cm_f);
             float dec = __fmaf_ru(li_f, 1.0f + 0x1p-20f, 4e-16f);
             if (dec < s.budget) {
                 s.budget = __fsub_rd(s.budget, dec);
@@ -423,11 +428,11 @@ __device__ __forceinline__ void advance(const Params& P, Packet<NL>& s, Tallies&
                 s.tau = (double)s.tauf;
                 s.tau_fresh = false;
             }
-            const double k[3] = {(double)s.kx, (double)s.ky, (double)s.kz};
+            const double k[3] = {s.kd0, s.kd1, s.kd2};
             if (!s.inv_ok) {
-                s.i0 = k[0] != 0.0 ? 1.0 / k[0] : 0.0;
-                s.i1 = k[1] != 0.0 ? 1.0 / k[1] : 0.0;
-                s.i2 = k[2] != 0.0 ? 1.0 / k[2] : 0.0;
+                s.i0 = k[0] != 0.0 ? __drcp_rn(k[0]) : 0.0;
+                s.i1 = k[1] != 0.0 ? __drcp_rn(k[1]) : 0.0;
+                s.i2 = k[2] != 0.0 ? __drcp_rn(k[2]) : 0.0;
                 s.inv_ok = true;
             }
             double p[3] = {s.p0, s.p1, s.p2};
@@ -476,18 +481,18 @@ __device__ __forceinline__ void advance(const Params& P, Packet<NL>& s, Tallies&
         }
         if (inter) {
             if (exact) {
-                s.p0 = __fma_rn(li_d, (double)s.kx, s.p0);
-                s.p1 = __fma_rn(li_d, (double)s.ky, s.p1);
-                s.p2 = __fma_rn(li_d, (double)s.kz, s.p2);
+                s.p0 = __fma_rn(li_d, s.kd0, s.p0);
+                s.p1 = __fma_rn(li_d, s.kd1, s.p1);
+                s.p2 = __fma_rn(li_d, s.kd2, s.p2);
                 s.path += li_d;
                 const double p[3] = {s.p0, s.p1, s.p2};
                 double D = inner_distance(p, s.w);
                 s.budget = __fsub_rd(__double2float_rd(D * (1.0 - 0x1p-20)), 4e-16f);
             } else {
                 const double l = (double)li_f;
-                s.p0 = __fma_rn(l, (double)s.kx, s.p0);
-                s.p1 = __fma_rn(l, (double)s.ky, s.p1);
-                s.p2 = __fma_rn(l, (double)s.kz, s.p2);
+                s.p0 = __fma_rn(l, s.kd0, s.p0);
+                s.p1 = __fma_rn(l, s.kd1, s.p1);
+                s.p2 = __fma_rn(l, s.kd2, s.p2);
                 s.path += l;
             }
             // Sect. 3.2: dust with P = tau_d / tau, else line X with P = tau_X / tau
@@ -631,7 +636,7 @@ __global__ void k_sample_upar(Params P, long long n, const double* x, const floa
 // ---------------------------------------------------------------------------
 int propagate_block_size() { return 128; }
 
-size_t propagate_smem(int nline, int block) { return (size_t)nline * 6 * block * sizeof(double); }
+size_t propagate_smem(int nline, int block) { return (size_t)nline * 6 * block * sizeof(float); }
 
 template <int NL, bool PEEL>
 static int occ(int block) {

@@ -140,8 +140,9 @@ def _replay(wl, n_packets, max_events):
 def test_trace_replay_per_step(which):
     """Each GPU event, replayed by the oracle from the GPU's state, lands on
     the same leaf with the same draw count and status; positions agree to
-    1e-6 of the step, directions to 1e-5 (FP32 sampling), frequencies to 1e-5
-    Doppler widths."""
+    1e-6 of the step; directions to 1e-6 and outgoing frequencies to 3e-5
+    Doppler widths (both produced by FP32 velocity and angle sampling: a few
+    FP32 ulps of |x| + |u_par| <= ~20)."""
     if which == "slab":
         wl = synth.slab(tau0=1e4, n_packets=64)
     elif which == "sphere_dust":
@@ -153,8 +154,8 @@ def test_trace_replay_per_step(which):
     assert st["steps"] > 1000
     assert st["mismatch"] <= 0.002 * st["steps"] + 2
     assert st["pos"] < 1e-6
-    assert st["dir"] < 1e-5
-    assert st["x"] < 1e-5
+    assert st["dir"] < 1e-6
+    assert st["x"] < 3e-5
 
 
 # ---------------------------------------------------------------- whole runs
