@@ -34,9 +34,10 @@ sys.path.insert(0, ROOT)
 METRIC = "scatterings/sec & packets/sec on 1 GB300 vs oracle; batched vs plain speedup; HBM roofline %"
 WORKLOAD = ("static H I + dust sphere: 8^3 root refined to 64^3-equivalent octree (172992 leaves), "
             "tau0=1e6 centre-to-edge, T=1e4 K, tau_dust=1, albedo 0.32, packets from the centre at x=0")
-# warp instructions executed per scattering by k_propagate on this workload,
-# from one ncu capture (smsp__inst_executed.sum / scatterings); see profiles/
-INST_PER_SCATT = None
+# warp instructions executed per scattering by k_propagate on this workload:
+# smsp__inst_executed.sum / scatterings of one ncu capture (65536 packets capped
+# at 1e4 scatterings each, profiles/k_propagate_sphere_tau1e6.md)
+INST_PER_SCATT = 58313234500 / (65536 * 9767.794143676758)
 ISSUE_PEAK_NOTE = "152 SMs x 4 schedulers x 1 warp-instruction/clock x SM clock"
 
 

@@ -55,9 +55,10 @@ def build(force=False, verbose=False, ptxas_v=False):
     if ptxas_v:
         kcmd.insert(1, "-Xptxas=-v")
     hcmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-c", os.path.join(CSRC, "host.cpp"), "-o", h_obj, *inc]
-    procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT) for c in (kcmd, hcmd)]
+    cmds = (kcmd, hcmd)
+    procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT) for c in cmds]
     outs = [p.communicate()[0].decode() for p in procs]
-    for p, o, c in zip(procs, outs, (kcmd, hcmd)):
+    for p, o, c in zip(procs, outs, cmds):
         if p.returncode != 0:
             raise RuntimeError("build failed: %s\n%s" % (" ".join(c), o))
         if verbose and o.strip():

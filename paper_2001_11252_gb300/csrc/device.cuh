@@ -287,8 +287,8 @@ __device__ __forceinline__ int dir_coord(double p, double k, double scale) {
 }
 
 // slab domains are periodic in x and y (Sect. 4): bring p + eps k into the box
-__device__ __forceinline__ void wrap_periodic(const Params& P, double p[3], const double k[3]) {
-    if (P.dom_kind != 1) return;
+__device__ __forceinline__ void wrap_periodic(const Geo& G, double p[3], const double k[3]) {
+    if (G.dom_kind != 1) return;
 #pragma unroll
     for (int ax = 0; ax < 2; ++ax) {
         int c = dir_coord(p[ax], k[ax], 2.0);
@@ -298,15 +298,15 @@ __device__ __forceinline__ void wrap_periodic(const Params& P, double p[3], cons
 }
 
 // descend from the son value `code` of a cell at level m in oct `oct`
-__device__ __forceinline__ void descend(const Params& P, int code, int m, int oct,
+__device__ __forceinline__ void descend(const Geo& G, int code, int m, int oct,
                                         int tx, int ty, int tz, Where& w, uint32_t& loads) {
-    const int L = P.max_level;
+    const int L = G.max_level;
     while (code > 0) {
         oct = code;
         ++m;
         int s = L - m;
         int child = ((tx >> s) & 1) | (((ty >> s) & 1) << 1) | (((tz >> s) & 1) << 2);
-        code = __ldg(P.son + 8 * oct + child);
+        code = __ldg(G.son + 8 * oct + child);
         ++loads;
     }
     int s = L - m;
@@ -320,36 +320,36 @@ __device__ __forceinline__ void descend(const Params& P, int code, int m, int oc
 
 // where-is-point: the dense top grid at level S gives the deepest cell at level
 // <= S holding the target; descend from there.  False if outside the box.
-__device__ __forceinline__ bool locate(const Params& P, int tx, int ty, int tz, Where& w,
+__device__ __forceinline__ bool locate(const Geo& G, int tx, int ty, int tz, Where& w,
                                        uint32_t& loads) {
-    const int L = P.max_level;
+    const int L = G.max_level;
     const int n = 1 << L;
     if ((unsigned)tx >= (unsigned)n || (unsigned)ty >= (unsigned)n || (unsigned)tz >= (unsigned)n)
         return false;
-    const int S = P.top_level;
+    const int S = G.top_level;
     const int s = L - S;
     long long idx = (((long long)(tz >> s) << S) + (ty >> s)) << S;
     idx += (tx >> s);
-    int4 e = __ldg(P.top + idx);
+    int4 e = __ldg(G.top + idx);
     ++loads;
-    descend(P, e.x, e.y, e.z, tx, ty, tz, w, loads);
+    descend(G, e.x, e.y, e.z, tx, ty, tz, w, loads);
     return true;
 }
 
-__device__ __forceinline__ bool locate_point(const Params& P, const double p[3], const double k[3],
+__device__ __forceinline__ bool locate_point(const Geo& G, const double p[3], const double k[3],
                                              Where& w, uint32_t& loads) {
-    double sc = (double)(1 << P.max_level);
-    return locate(P, dir_coord(p[0], k[0], sc), dir_coord(p[1], k[1], sc), dir_coord(p[2], k[2], sc),
+    double sc = (double)(1 << G.max_level);
+    return locate(G, dir_coord(p[0], k[0], sc), dir_coord(p[1], k[1], sc), dir_coord(p[2], k[2], sc),
                   w, loads);
 }
 
 // Neighbour search after crossing a face (Sect. 4.3): the target is first
 // looked for inside the father cell of the current leaf (its own oct), then in
 // the father's neighbour across the face, then from the top grid.
-__device__ __forceinline__ bool next_leaf(const Params& P, const double p[3], const double k[3],
+__device__ __forceinline__ bool next_leaf(const Geo& G, const double p[3], const double k[3],
                                           int axis, Where& w, uint32_t& son_loads,
                                           uint32_t& nbor_loads) {
-    const int L = P.max_level;
+    const int L = G.max_level;
     double sc = (double)(1 << L);
     int t[3];
 #pragma unroll
@@ -362,16 +362,16 @@ __device__ __forceinline__ bool next_leaf(const Params& P, const double p[3], co
     int fi = w.i >> 1, fj = w.j >> 1, fk = w.k >> 1;
     if ((t[0] >> (sh + 1)) == fi && (t[1] >> (sh + 1)) == fj && (t[2] >> (sh + 1)) == fk) {
         int child = ((t[0] >> sh) & 1) | (((t[1] >> sh) & 1) << 1) | (((t[2] >> sh) & 1) << 2);
-        int code = __ldg(P.son + 8 * w.oct + child);
+        int code = __ldg(G.son + 8 * w.oct + child);
         ++son_loads;
-        descend(P, code, l, w.oct, t[0], t[1], t[2], w, son_loads);
+        descend(G, code, l, w.oct, t[0], t[1], t[2], w, son_loads);
         return true;
     }
     if (l >= 2) {
         const bool up = axis == 0 ? k[0] > 0.0 : (axis == 1 ? k[1] > 0.0 : k[2] > 0.0);
         int face = 2 * axis + (up ? 1 : 0);
-        int4 a = __ldg(P.nbr + 2 * w.oct);
-        int4 b = __ldg(P.nbr + 2 * w.oct + 1);
+        int4 a = __ldg(G.nbr + 2 * w.oct);
+        int4 b = __ldg(G.nbr + 2 * w.oct + 1);
         ++nbor_loads;
         int nc = face == 0 ? a.x : face == 1 ? a.y : face == 2 ? a.z : face == 3 ? a.w : face == 4 ? b.x : b.y;
         int nl = (b.w >> (5 * face)) & 31;
@@ -385,14 +385,14 @@ __device__ __forceinline__ bool next_leaf(const Params& P, const double p[3], co
             int d = (l - 1) - nl;
             int s2 = L - nl;
             if ((t[0] >> s2) == (f[0] >> d) && (t[1] >> s2) == (f[1] >> d) && (t[2] >> s2) == (f[2] >> d)) {
-                int code = __ldg(P.son + nc);
+                int code = __ldg(G.son + nc);
                 ++son_loads;
-                descend(P, code, nl, nc >> 3, t[0], t[1], t[2], w, son_loads);
+                descend(G, code, nl, nc >> 3, t[0], t[1], t[2], w, son_loads);
                 return true;
             }
         }
     }
-    return locate(P, t[0], t[1], t[2], w, son_loads);
+    return locate(G, t[0], t[1], t[2], w, son_loads);
 }
 
 // distance along k from p to the exit face of leaf w (FP64, exactly the
@@ -416,15 +416,15 @@ __device__ __forceinline__ double face_distance(const double p[3], const double 
 
 // distance along k from p to the domain border (FP64, same operation order as
 // the oracle)
-__device__ __forceinline__ double border_distance(const Params& P, const double p[3],
+__device__ __forceinline__ double border_distance(const Geo& G, const double p[3],
                                                   const double k[3], const double inv[3]) {
-    if (P.dom_kind == 0) {
-        double d0 = __dsub_rn(p[0], P.dom_c[0]);
-        double d1 = __dsub_rn(p[1], P.dom_c[1]);
-        double d2 = __dsub_rn(p[2], P.dom_c[2]);
+    if (G.dom_kind == 0) {
+        double d0 = __dsub_rn(p[0], G.dom_c[0]);
+        double d1 = __dsub_rn(p[1], G.dom_c[1]);
+        double d2 = __dsub_rn(p[2], G.dom_c[2]);
         double b = __dadd_rn(__dadd_rn(__dmul_rn(d0, k[0]), __dmul_rn(d1, k[1])), __dmul_rn(d2, k[2]));
         double cc = __dsub_rn(__dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2)),
-                              __dmul_rn(P.dom_R, P.dom_R));
+                              __dmul_rn(G.dom_R, G.dom_R));
         double disc = __dsub_rn(__dmul_rn(b, b), cc);
         if (disc < 0.0) disc = 0.0;
         double sq = __dsqrt_rn(disc);
@@ -434,9 +434,9 @@ __device__ __forceinline__ double border_distance(const Params& P, const double 
     double best = __longlong_as_double(0x7ff0000000000000ULL);
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-        if (P.dom_kind == 1 && ax != 2) continue;
+        if (G.dom_kind == 1 && ax != 2) continue;
         if (k[ax] == 0.0) continue;
-        double edge = k[ax] > 0.0 ? __dadd_rn(P.dom_c[ax], P.dom_R) : __dsub_rn(P.dom_c[ax], P.dom_R);
+        double edge = k[ax] > 0.0 ? __dadd_rn(G.dom_c[ax], G.dom_R) : __dsub_rn(G.dom_c[ax], G.dom_R);
         double t = __dmul_rn(__dsub_rn(edge, p[ax]), inv[ax]);
         if (t < best) best = t;
     }
@@ -491,9 +491,9 @@ struct CellCache {
 };
 
 template <int NL>
-__device__ __forceinline__ void load_cell(const Params& P, int leaf, CellCache<NL>& cc) {
-    float4 r0 = __ldg(P.rec + 2 * leaf);
-    float4 r1 = __ldg(P.rec + 2 * leaf + 1);
+__device__ __forceinline__ void load_cell(const Params& P, const Geo& G, int leaf, CellCache<NL>& cc) {
+    float4 r0 = __ldg(G.rec + 2 * leaf);
+    float4 r1 = __ldg(G.rec + 2 * leaf + 1);
     cc.vx = r0.y; cc.vy = r0.z; cc.vz = r0.w;
     cc.T = r1.x;
     cc.kap_d = r1.y * P.dust_sigma;

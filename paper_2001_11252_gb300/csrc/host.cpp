@@ -316,16 +316,16 @@ int rascas_load_octree(rascas_ctx* ctx, const rascas_octree* t, int mem) {
     CK(cudaMemcpy(ctx->d_nbr.p, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->d_top.p, top.data(), top.size() * 4, cudaMemcpyHostToDevice));
     Params& P = ctx->P;
-    P.rec = (const float4*)ctx->d_rec.p;
-    P.son = (const int*)ctx->d_son.p;
-    P.nbr = (const int4*)ctx->d_nbr.p;
-    P.top = (const int4*)ctx->d_top.p;
-    P.top_level = S;
-    P.max_level = max_level;
-    P.nleaf = nleaf;
-    P.noct = noct;
-    P.box_cm = t->box_cm;
-    P.box_cm_f = (float)t->box_cm;
+    P.g.rec = (const float4*)ctx->d_rec.p;
+    P.g.son = (const int*)ctx->d_son.p;
+    P.g.nbr = (const int4*)ctx->d_nbr.p;
+    P.g.top = (const int4*)ctx->d_top.p;
+    P.g.top_level = S;
+    P.g.max_level = max_level;
+    P.g.nleaf = nleaf;
+    P.g.noct = noct;
+    P.g.box_cm = t->box_cm;
+    P.g.box_cm_f = (float)t->box_cm;
     ctx->has_mesh = true;
     return RASCAS_OK;
 }
@@ -336,9 +336,9 @@ int rascas_set_domain(rascas_ctx* ctx, const rascas_domain* d) {
     ctx->dom = *d;
     ctx->has_domain = true;
     Params& P = ctx->P;
-    P.dom_kind = d->kind;
-    for (int ax = 0; ax < 3; ++ax) P.dom_c[ax] = d->centre[ax];
-    P.dom_R = d->size;
+    P.g.dom_kind = d->kind;
+    for (int ax = 0; ax < 3; ++ax) P.g.dom_c[ax] = d->centre[ax];
+    P.g.dom_R = d->size;
     if (ctx->has_mesh) {
         CK(cudaSetDevice(ctx->device));
         leaf_flags(ctx);
@@ -422,9 +422,9 @@ int rascas_set_detector(rascas_ctx* ctx, const rascas_detector* d) {
     CK(cudaSetDevice(ctx->device));
     ctx->det = *d;
     Params& P = ctx->P;
-    P.nu_lo = d->nu_lo;
-    P.nu_inv_range = 1.0 / (d->nu_hi - d->nu_lo);
-    P.nbin = d->nbin;
+    P.g.nu_lo = d->nu_lo;
+    P.g.nu_inv_range = 1.0 / (d->nu_hi - d->nu_lo);
+    P.g.nbin = d->nbin;
     P.ndir = d->ndir;
     P.npix = d->npix;
     P.cube = d->cube && d->npix > 0 && d->ndir > 0;
@@ -452,7 +452,7 @@ int rascas_set_detector(rascas_ctx* ctx, const rascas_detector* d) {
     CK(ctx->d_pspec.ensure((size_t)(d->ndir > 0 ? d->ndir : 1) * d->nbin * 4));
     CK(ctx->d_pimg.ensure((size_t)(d->ndir > 0 ? d->ndir : 1) * (npix2 > 0 ? npix2 : 1) * 4));
     if (P.cube) CK(ctx->d_pcube.ensure((size_t)d->ndir * npix2 * d->nbin * 4));
-    P.spec = (float*)ctx->d_spec.p;
+    P.g.spec = (float*)ctx->d_spec.p;
     P.pspec = (float*)ctx->d_pspec.p;
     P.pimg = (float*)ctx->d_pimg.p;
     P.pcube = P.cube ? (float*)ctx->d_pcube.p : nullptr;
@@ -515,12 +515,12 @@ int run_propagate(rascas_ctx* ctx, const rascas_packets_in* in, int64_t n, const
     CK(cudaSetDevice(ctx->device));
     Params P = ctx->P;
     if (!tallies || !ctx->has_det) {
-        P.spec = nullptr;
+        P.g.spec = nullptr;
         P.ndir = 0;
         if (!ctx->has_det) {
-            P.nbin = 1;
-            P.nu_lo = 0.0;
-            P.nu_inv_range = 0.0;
+            P.g.nbin = 1;
+            P.g.nu_lo = 0.0;
+            P.g.nu_inv_range = 0.0;
         }
     }
     rg::PacketsIn din{in->pos, in->dir, in->nu, in->id, (long long)n};

@@ -48,9 +48,10 @@ struct LineDev {
     double chan_nu[kMaxChan];
 };
 
-struct Params {
-    const Params* self;    // device-side copy of these parameters (read by the peeling walk)
-    // mesh (device)
+// One medium: its octree, leaf records, domain and escape-spectrum axis.  A
+// single-model run keeps it inside Params; a batch keeps one per model in a
+// device table.
+struct Geo {
     const float4* rec;     // [2*nleaf]: {n_HI, vx, vy, vz}, {T, n_dust, n_metal, flags}
     const int* son;        // [8*noct]
     const int4* nbr;       // [2*noct]: {nb0, nb1, nb2, nb3}, {nb4, nb5, father, packed levels}
@@ -58,10 +59,22 @@ struct Params {
     int top_level, max_level, nleaf, noct;
     double box_cm;
     float box_cm_f;
-    // domain
-    int dom_kind;
+    int dom_kind;          // 0 sphere, 1 slab (periodic x, y), 2 cube
     double dom_c[3];
     double dom_R;
+    // escape spectrum: bin = floor((nu - nu_lo) * nu_inv_range * nbin)
+    double nu_lo, nu_inv_range;
+    int nbin;
+    float* spec;
+};
+
+struct Params {
+    const Params* self;    // device-side copy of these parameters (read by the peeling walk)
+    Geo g;                 // the medium of a single-model run
+    // batch of independent models (Geo per model, packet index ranges)
+    const Geo* models;
+    const long long* model_first;   // [nmodels + 1] prefix sums of packet counts
+    int nmodels;
     // opacity sources
     int nline;
     LineDev line[kMaxLines];
@@ -72,14 +85,12 @@ struct Params {
     long long max_scatt, max_steps;
     double tau_stop;
     uint32_t key0, key1;
-    // detector
-    double nu_lo, nu_inv_range;
-    int nbin, ndir, npix, cube;
+    // peeling detector (single-model runs)
+    int ndir, npix, cube;
     double dirs[kMaxDirs][3];
     double eu[kMaxDirs][3], ev[kMaxDirs][3];
     double img_c[3];
     double inv_fov;
-    float* spec;
     float* pspec;
     float* pimg;
     float* pcube;

@@ -39,6 +39,7 @@ struct Packet {
     long long idx, nscatt, nsteps;
     Where w;
     Rng rng;
+    int mi;                // model of a batch run (0 otherwise)
     float kx, ky, kz;      // direction (unit vector, as sampled in FP32)
     float xh, xl;          // gas-frame Doppler offset of line 0 in this leaf, x = xh + xl
     float tauf;            // FP32 copy of tau
@@ -83,17 +84,17 @@ __device__ __noinline__ double ray_walk(const Params* __restrict__ G, double p0,
     uint32_t sl = 0, nl = 0, ll = 0;
     for (int guard = 0; guard < (1 << 26); ++guard) {
         CellCache<NL> cc;
-        load_cell<NL>(P, w.leaf, cc);
+        load_cell<NL>(P, P.g, w.leaf, cc);
         ++ll;
         double nu = to_gas(nu_ext, beta_of(cc, k));
         float kl[NL];
         float kap = opacity<NL>(P, cc, nu, kl);
         int axis;
         double tf = face_distance(p, k, inv, w, axis);
-        double tb = (cc.flags & kFlagBorder) ? border_distance(P, p, k, inv) : kInf;
+        double tb = (cc.flags & kFlagBorder) ? border_distance(P.g, p, k, inv) : kInf;
         bool border = tb <= tf;
         double l = border ? tb : tf;
-        tau = __dadd_rn(tau, __dmul_rn(__dmul_rn((double)kap, l), P.box_cm));
+        tau = __dadd_rn(tau, __dmul_rn(__dmul_rn((double)kap, l), P.g.box_cm));
         if (cells != nullptr && n < cap) {
             cells[n] = w.leaf;
             lens[n] = l;
@@ -103,8 +104,8 @@ __device__ __noinline__ double ray_walk(const Params* __restrict__ G, double p0,
         zero_run = tf > 0.0 ? 0 : zero_run + 1;
         if (zero_run > 64) break;
         move_to_face(p, k, axis, tf, w);
-        wrap_periodic(P, p, k);
-        if (!next_leaf(P, p, k, axis, w, sl, nl)) break;
+        wrap_periodic(P.g, p, k);
+        if (!next_leaf(P.g, p, k, axis, w, sl, nl)) break;
     }
     if (tl) {
         tl->peel_cells += n;
@@ -130,11 +131,12 @@ __device__ __noinline__ void peel_add(const Params* __restrict__ G, double p0, d
     double tau = ray_walk<NL>(G, p0, p1, p2, w, k0, k1, k2, nu_ext, P.tau_stop, tl, nullptr, nullptr, 0, nullptr);
     if (tau > P.tau_stop) return;
     float f = wt * expf(-(float)tau);
-    double t = __dmul_rn(__dsub_rn(nu_ext, P.nu_lo), P.nu_inv_range);
-    double fb = floor(t * (double)P.nbin);
-    bool chok = fb >= 0.0 && fb < (double)P.nbin;
+    const int nbin = P.g.nbin;
+    double t = __dmul_rn(__dsub_rn(nu_ext, P.g.nu_lo), P.g.nu_inv_range);
+    double fb = floor(t * (double)nbin);
+    bool chok = fb >= 0.0 && fb < (double)nbin;
     int ch = chok ? (int)fb : 0;
-    if (chok) atomicAdd(P.pspec + d * P.nbin + ch, f);
+    if (chok) atomicAdd(P.pspec + d * nbin + ch, f);
     if (P.npix > 0) {
         double r0 = p0 - P.img_c[0], r1 = p1 - P.img_c[1], r2 = p2 - P.img_c[2];
         double u = r0 * P.eu[d][0] + r1 * P.eu[d][1] + r2 * P.eu[d][2];
@@ -145,7 +147,7 @@ __device__ __noinline__ void peel_add(const Params* __restrict__ G, double p0, d
             long long px = (long long)fv * P.npix + (long long)fu;
             long long npix2 = (long long)P.npix * P.npix;
             atomicAdd(P.pimg + d * npix2 + px, f);
-            if (chok && P.cube) atomicAdd(P.pcube + (d * npix2 + px) * P.nbin + ch, f);
+            if (chok && P.cube) atomicAdd(P.pcube + (d * npix2 + px) * nbin + ch, f);
         }
     }
 }
@@ -322,8 +324,8 @@ __device__ __forceinline__ double nu_ext_now(const Params& P, const Packet<NL>& 
 // packet start: read the initial condition, key its random stream, find its
 // leaf, draw its first tau_event (Sect. 2: PPIC lists; Sect. 3)
 template <int NL>
-__device__ __forceinline__ void begin_packet(const Params& P, const PacketsIn& in, long long idx, Packet<NL>& s,
-                                             Tallies& tl, const TraceOut& tr) {
+__device__ __forceinline__ void begin_packet(const Params& P, const Geo& G, const PacketsIn& in, long long idx,
+                                             Packet<NL>& s, Tallies& tl, const TraceOut& tr) {
     s.idx = idx;
     double p[3] = {in.pos[3 * idx], in.pos[3 * idx + 1], in.pos[3 * idx + 2]};
     const double k[3] = {in.dir[3 * idx], in.dir[3 * idx + 1], in.dir[3 * idx + 2]};
@@ -340,9 +342,9 @@ __device__ __forceinline__ void begin_packet(const Params& P, const PacketsIn& i
     s.status = RASCAS_PK_ACTIVE_;
     s.enter = true;
     s.fresh = true;
-    wrap_periodic(P, p, k);
+    wrap_periodic(G, p, k);
     s.p0 = p[0]; s.p1 = p[1]; s.p2 = p[2];
-    if (!locate_point(P, p, k, s.w, tl.son_loads)) {
+    if (!locate_point(G, p, k, s.w, tl.son_loads)) {
         s.status = RASCAS_PK_ERROR_;
         s.enter = false;
         s.w.leaf = -1; s.w.oct = 0; s.w.level = 0; s.w.i = s.w.j = s.w.k = 0;
@@ -355,7 +357,7 @@ __device__ __forceinline__ void begin_packet(const Params& P, const PacketsIn& i
 }
 
 template <int NL>
-__device__ __forceinline__ void finish_packet(const Params& P, const Packet<NL>& s, const PacketsOut& out,
+__device__ __forceinline__ void finish_packet(const Params& P, const Geo& G, const Packet<NL>& s, const PacketsOut& out,
                                               uint32_t& c_pk, uint32_t& c_esc, uint32_t& c_abs, uint32_t& c_cap,
                                               uint32_t& c_err) {
     double nu_ext = nu_ext_now<NL>(P, s);
@@ -371,10 +373,10 @@ __device__ __forceinline__ void finish_packet(const Params& P, const Packet<NL>&
     c_abs += s.status == RASCAS_PK_ABSORBED_;
     c_cap += s.status == RASCAS_PK_CAPPED_;
     c_err += s.status == RASCAS_PK_ERROR_;
-    if (s.status == RASCAS_PK_ESCAPED_ && P.spec != nullptr) {
-        double t = __dmul_rn(__dsub_rn(nu_ext, P.nu_lo), P.nu_inv_range);
-        double fb = floor(t * (double)P.nbin);
-        if (fb >= 0.0 && fb < (double)P.nbin) atomicAdd(P.spec + (int)fb, 1.0f);
+    if (s.status == RASCAS_PK_ESCAPED_ && G.spec != nullptr) {
+        double t = __dmul_rn(__dsub_rn(nu_ext, G.nu_lo), G.nu_inv_range);
+        double fb = floor(t * (double)G.nbin);
+        if (fb >= 0.0 && fb < (double)G.nbin) atomicAdd(G.spec + (int)fb, 1.0f);
     }
 }
 
@@ -383,10 +385,11 @@ __device__ __forceinline__ void finish_packet(const Params& P, const Packet<NL>&
 // escape through the domain border (Sect. 3, Sect. 4.3).  Each phase appears
 // once, so the loop body stays small for the instruction cache.
 template <int NL, bool PEEL>
-__device__ __forceinline__ void advance(const Params& P, Packet<NL>& s, Tallies& tl, const TraceOut& tr) {
+__device__ __forceinline__ void advance(const Params& P, const Geo& G, Packet<NL>& s, Tallies& tl,
+                                        const TraceOut& tr) {
     bool evt = false;
     if (s.enter) {
-        load_cell<NL>(P, s.w.leaf, s.cc);
+        load_cell<NL>(P, G, s.w.leaf, s.cc);
         ++tl.leaf_loads;
         const double k[3] = {s.kd0, s.kd1, s.kd2};
         double nu_gas = to_gas(s.nu_enter, beta_of(s.cc, k));
@@ -415,7 +418,7 @@ __device__ __forceinline__ void advance(const Params& P, Packet<NL>& s, Tallies&
         float li_f = 0.0f;
         double li_d = 0.0;
         if (!border_leaf) {
-            li_f = s.tauf / (kap * P.box_cm_f);
+            li_f = s.tauf / (kap * G.box_cm_f);
             float dec = __fmaf_ru(li_f, 1.0f + 0x1p-20f, 4e-16f);
             if (dec < s.budget) {
                 s.budget = __fsub_rd(s.budget, dec);
@@ -439,12 +442,12 @@ __device__ __forceinline__ void advance(const Params& P, Packet<NL>& s, Tallies&
             const double inv[3] = {s.i0, s.i1, s.i2};
             int axis;
             double tf = face_distance(p, k, inv, s.w, axis);
-            double tb = border_leaf ? border_distance(P, p, k, inv) : kInf;
+            double tb = border_leaf ? border_distance(G, p, k, inv) : kInf;
             bool border = tb <= tf;
             double l = border ? tb : tf;
-            double tau_cell = __dmul_rn(__dmul_rn((double)kap, l), P.box_cm);
+            double tau_cell = __dmul_rn(__dmul_rn((double)kap, l), G.box_cm);
             if (tau_cell >= s.tau) {
-                li_d = s.tau / __dmul_rn((double)kap, P.box_cm);
+                li_d = s.tau / __dmul_rn((double)kap, G.box_cm);
                 inter = true;
                 exact = true;
             } else {
@@ -462,13 +465,13 @@ __device__ __forceinline__ void advance(const Params& P, Packet<NL>& s, Tallies&
                     s.zero_run = tf > 0.0 ? 0 : s.zero_run + 1;
                     double nu_ext = to_ext(nu_of_x(P, s.cc, s.xh, s.xl), beta_of(s.cc, k));
                     move_to_face(p, k, axis, tf, s.w);
-                    wrap_periodic(P, p, k);
+                    wrap_periodic(G, p, k);
                     s.p0 = p[0]; s.p1 = p[1]; s.p2 = p[2];
                     Where nw = s.w;
                     if (s.zero_run > 64) {
                         s.status = RASCAS_PK_ERROR_;   // stuck walk
                         evt = true;
-                    } else if (!next_leaf(P, p, k, axis, nw, tl.son_loads, tl.nbor_loads)) {
+                    } else if (!next_leaf(G, p, k, axis, nw, tl.son_loads, tl.nbor_loads)) {
                         s.status = RASCAS_PK_ESCAPED_;   // left the box
                         evt = true;
                     } else {
@@ -535,13 +538,26 @@ __device__ __forceinline__ void flush(const Params& P, unsigned long long v, int
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(P.counters + which, v);
 }
 
-template <int NL, bool PEEL>
-__global__ void __launch_bounds__(128, PEEL ? 2 : 4) k_propagate(Params P, PacketsIn in, PacketsOut out, TraceOut tr) {
+// model of packet idx in a batch: the last m with model_first[m] <= idx
+__device__ __forceinline__ int model_of(const Params& P, long long idx) {
+    int lo = 0, hi = P.nmodels;   // model_first[lo] <= idx < model_first[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (__ldg(P.model_first + mid) <= idx) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int NL, bool PEEL, bool BATCH>
+__global__ void __launch_bounds__(128, PEEL ? 2 : 4)
+k_propagate(const __grid_constant__ Params P, PacketsIn in, PacketsOut out, TraceOut tr) {
     Packet<NL> s;
     Tallies tl = {};
     uint32_t c_pk = 0, c_esc = 0, c_abs = 0, c_cap = 0, c_err = 0;
     const unsigned lane = threadIdx.x & 31u;
     bool have = false, drained = false;
+    s.mi = 0;
     for (;;) {
         bool want = !have && !drained;
         unsigned m = __ballot_sync(kFull, want);
@@ -553,7 +569,12 @@ __global__ void __launch_bounds__(128, PEEL ? 2 : 4) k_propagate(Params P, Packe
             if (want) {
                 long long idx = (long long)base + __popc(m & ((1u << lane) - 1u));
                 if (idx < in.n) {
-                    begin_packet<NL>(P, in, idx, s, tl, tr);
+                    if constexpr (BATCH) {
+                        s.mi = model_of(P, idx);
+                        begin_packet<NL>(P, P.models[s.mi], in, idx, s, tl, tr);
+                    } else {
+                        begin_packet<NL>(P, P.g, in, idx, s, tl, tr);
+                    }
                     have = true;
                 } else {
                     drained = true;
@@ -565,9 +586,10 @@ __global__ void __launch_bounds__(128, PEEL ? 2 : 4) k_propagate(Params P, Packe
             continue;
         }
         if (have) {
-            if (s.status == RASCAS_PK_ACTIVE_) advance<NL, PEEL>(P, s, tl, tr);
+            const Geo& G = BATCH ? P.models[s.mi] : P.g;
+            if (s.status == RASCAS_PK_ACTIVE_) advance<NL, PEEL>(P, G, s, tl, tr);
             if (s.status != RASCAS_PK_ACTIVE_) {
-                finish_packet<NL>(P, s, out, c_pk, c_esc, c_abs, c_cap, c_err);
+                finish_packet<NL>(P, G, s, out, c_pk, c_esc, c_abs, c_cap, c_err);
                 have = false;
             }
         }
@@ -600,9 +622,9 @@ __global__ void k_ray_tau(const Params* __restrict__ G, long long n, const doubl
     double p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
     const double k[3] = {dir[3 * i], dir[3 * i + 1], dir[3 * i + 2]};
     uint32_t loads = 0;
-    wrap_periodic(P, p, k);
+    wrap_periodic(P.g, p, k);
     Where w;
-    if (!locate_point(P, p, k, w, loads)) {
+    if (!locate_point(P.g, p, k, w, loads)) {
         tau[i] = 0.0;
         if (ncell) ncell[i] = 0;
         return;
@@ -638,23 +660,24 @@ int propagate_block_size() { return 128; }
 
 size_t propagate_smem(int nline, int block) { return (size_t)nline * 6 * block * sizeof(float); }
 
-template <int NL, bool PEEL>
+template <int NL, bool PEEL, bool BATCH>
 static int occ(int block) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate<NL, PEEL>, block, propagate_smem(NL, block));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate<NL, PEEL, BATCH>, block, propagate_smem(NL, block));
     return nb;
 }
 
 int propagate_blocks_per_sm(int block, bool peel) {
-    return peel ? occ<1, true>(block) : occ<1, false>(block);
+    return peel ? occ<1, true, false>(block) : occ<1, false, false>(block);
 }
 
 template <int NL>
 static cudaError_t launch_nl(const Params& P, const PacketsIn& in, const PacketsOut& out, const TraceOut& tr,
                              int grid, int block, cudaStream_t st) {
     size_t smem = propagate_smem(NL, block);
-    if (P.ndir > 0) k_propagate<NL, true><<<grid, block, smem, st>>>(P, in, out, tr);
-    else k_propagate<NL, false><<<grid, block, smem, st>>>(P, in, out, tr);
+    if (P.nmodels > 0) k_propagate<NL, false, true><<<grid, block, smem, st>>>(P, in, out, tr);
+    else if (P.ndir > 0) k_propagate<NL, true, false><<<grid, block, smem, st>>>(P, in, out, tr);
+    else k_propagate<NL, false, false><<<grid, block, smem, st>>>(P, in, out, tr);
     return cudaGetLastError();
 }
 
