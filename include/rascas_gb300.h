@@ -240,6 +240,35 @@ int rascas_eval_voigt(rascas_ctx *ctx, int64_t n, const float *a, const double *
 int rascas_sample_upar(rascas_ctx *ctx, int64_t n, const double *x, const float *a,
                        const uint64_t *id, float *u, int32_t *ndraw, int mem);
 
+/* ---- allocation-free variant ------------------------------------------- */
+
+/* Largest n accepted by rascas_propagate_noalloc. */
+#define RASCAS_NOALLOC_MAX_PACKETS 57344
+
+/* rascas_propagate for callers that must not allocate device memory while
+ * they run -- for example an application that hands all free HBM to another
+ * framework's memory pool at start-up, or a latency-critical loop where a
+ * cudaMalloc (which can synchronise the device) is not acceptable.  This call
+ * itself performs no cudaMalloc, cudaFree or allocating library call: its
+ * device scratch (work-queue head, counters, a parameter copy and the staging
+ * of up to RASCAS_NOALLOC_MAX_PACKETS packets, 8 MiB in all) is a static
+ * device array that every GPU loading the library holds until the process
+ * exits.  The context must already be set up (octree, domain, lines,
+ * physics).  No counterpart in the paper: this is an interface variant only.
+ *
+ * in/out are HOST arrays (as rascas_packets_in / rascas_packets_out); out and
+ * stats may be NULL.  Results per packet are identical to rascas_propagate on
+ * the same packets; tallies and peeling are not accumulated (per-packet
+ * outputs only).  n > RASCAS_NOALLOC_MAX_PACKETS returns RASCAS_E_ARG.
+ * The first call on a device looks up the array's device address (once per
+ * device; make that first call before any stream capture).  Every call
+ * reuses the same array and clears the parts that must start at zero; calls
+ * that overlap on the GPU (several host threads, streams or contexts on one
+ * device at once) race on it and must be serialised by the caller.  The call
+ * synchronises the context's stream before returning. */
+int rascas_propagate_noalloc(rascas_ctx *ctx, const rascas_packets_in *in, int64_t n,
+                             const rascas_packets_out *out, rascas_run_stats *stats);
+
 #ifdef __cplusplus
 }
 #endif

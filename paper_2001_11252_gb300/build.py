@@ -50,12 +50,15 @@ def build(force=False, verbose=False, ptxas_v=False):
     inc = ["-I", os.path.join(cu, "include"), "-I", CSRC, "-I", os.path.join(ROOT, "include")]
     k_obj = os.path.join(BUILD, "kernels.o")
     h_obj = os.path.join(BUILD, "host.o")
+    n_obj = os.path.join(BUILD, "noalloc.o")
     kcmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c",
             os.path.join(CSRC, "kernels.cu"), "-o", k_obj, *inc]
     if ptxas_v:
         kcmd.insert(1, "-Xptxas=-v")
     hcmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-c", os.path.join(CSRC, "host.cpp"), "-o", h_obj, *inc]
-    cmds = (kcmd, hcmd)
+    ncmd = [nvcc, *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-c", os.path.join(CSRC, "noalloc.cu"),
+            "-o", n_obj, *inc]
+    cmds = (kcmd, hcmd, ncmd)
     procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT) for c in cmds]
     outs = [p.communicate()[0].decode() for p in procs]
     for p, o, c in zip(procs, outs, cmds):
@@ -64,7 +67,7 @@ def build(force=False, verbose=False, ptxas_v=False):
         if verbose and o.strip():
             print(o)
     tmp = LIB + ".tmp%d" % os.getpid()
-    lcmd = [nvcc, *ARCH, "-shared", "-o", tmp, k_obj, h_obj, "-lcudart"]
+    lcmd = [nvcc, *ARCH, "-shared", "-o", tmp, k_obj, h_obj, n_obj, "-lcudart"]
     r = subprocess.run(lcmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed: %s\n%s" % (" ".join(lcmd), r.stdout.decode()))

@@ -756,4 +756,89 @@ int rascas_sample_upar(rascas_ctx* ctx, int64_t n, const double* x, const float*
     return RASCAS_OK;
 }
 
+int rascas_propagate_noalloc(rascas_ctx* ctx, const rascas_packets_in* in, int64_t n,
+                             const rascas_packets_out* out, rascas_run_stats* stats) {
+    if (!ctx || !in || n < 0) return fail(ctx, RASCAS_E_ARG, "propagate_noalloc: bad arguments");
+    if (n > RASCAS_NOALLOC_MAX_PACKETS)
+        return fail(ctx, RASCAS_E_ARG,
+                    "propagate_noalloc: n exceeds RASCAS_NOALLOC_MAX_PACKETS (" +
+                        std::to_string(RASCAS_NOALLOC_MAX_PACKETS) + "); split the packet list");
+    if (n > 0 && (!in->pos || !in->dir || !in->nu || !in->id)) return fail(ctx, RASCAS_E_ARG, "packets: null array");
+    int r = check_ready(ctx);
+    if (r) return r;
+    CK(cudaSetDevice(ctx->device));
+    char* base = nullptr;
+    size_t bytes = 0;
+    CK(rg::noalloc_scratch(ctx->device, (void**)&base, &bytes));
+    // layout: counters + queue head | parameter copy | packet staging
+    const size_t N = (size_t)n;
+    auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
+    size_t off = 0;
+    unsigned long long* cnt_d = (unsigned long long*)(base + off);
+    off += al(sizeof(unsigned long long) * (rg::CNT_N + 1));
+    Params* par_d = (Params*)(base + off);
+    off += al(sizeof(Params));
+    double* pos = (double*)(base + off); off += al(3 * N * 8);
+    double* dir = (double*)(base + off); off += al(3 * N * 8);
+    double* nu = (double*)(base + off); off += al(N * 8);
+    uint64_t* id = (uint64_t*)(base + off); off += al(N * 8);
+    int32_t* ost = (int32_t*)(base + off); off += al(N * 4);
+    int64_t* ons = (int64_t*)(base + off); off += al(N * 8);
+    double* onu = (double*)(base + off); off += al(N * 8);
+    double* opos = (double*)(base + off); off += al(3 * N * 8);
+    double* odir = (double*)(base + off); off += al(3 * N * 8);
+    double* opath = (double*)(base + off); off += al(N * 8);
+    if (off > bytes) return fail(ctx, RASCAS_E_ARG, "propagate_noalloc: scratch layout exceeds the static array");
+    Params P = ctx->P;
+    P.g.spec = nullptr;   // per-packet outputs only: no tallies, no peeling
+    P.ndir = 0;
+    P.counters = cnt_d;
+    P.head = cnt_d + rg::CNT_N;
+    P.self = par_d;
+    cudaStream_t st = ctx->stream;
+    CK(cudaMemsetAsync(cnt_d, 0, sizeof(unsigned long long) * (rg::CNT_N + 1), st));
+    CK(cudaMemcpyAsync(par_d, &P, sizeof(Params), cudaMemcpyHostToDevice, st));
+    rg::PacketsIn din{pos, dir, nu, id, (long long)n};
+    rg::PacketsOut dout{};
+    if (out) dout = rg::PacketsOut{out->status ? ost : nullptr, out->nscatt ? ons : nullptr, out->nu ? onu : nullptr,
+                                   out->pos ? opos : nullptr, out->dir ? odir : nullptr, out->path ? opath : nullptr};
+    rg::TraceOut tr{nullptr, nullptr, 0};
+    if (n > 0) {
+        CK(cudaMemcpyAsync(pos, in->pos, 3 * N * 8, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(dir, in->dir, 3 * N * 8, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(nu, in->nu, N * 8, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(id, in->id, N * 8, cudaMemcpyHostToDevice, st));
+        CK(rg::launch_propagate(P, din, dout, tr, persistent_grid(ctx, false), rg::propagate_block_size(), st));
+        if (out) {
+            if (out->status) CK(cudaMemcpyAsync(out->status, ost, N * 4, cudaMemcpyDeviceToHost, st));
+            if (out->nscatt) CK(cudaMemcpyAsync(out->nscatt, ons, N * 8, cudaMemcpyDeviceToHost, st));
+            if (out->nu) CK(cudaMemcpyAsync(out->nu, onu, N * 8, cudaMemcpyDeviceToHost, st));
+            if (out->pos) CK(cudaMemcpyAsync(out->pos, opos, 3 * N * 8, cudaMemcpyDeviceToHost, st));
+            if (out->dir) CK(cudaMemcpyAsync(out->dir, odir, 3 * N * 8, cudaMemcpyDeviceToHost, st));
+            if (out->path) CK(cudaMemcpyAsync(out->path, opath, N * 8, cudaMemcpyDeviceToHost, st));
+        }
+    }
+    unsigned long long cnt[rg::CNT_N] = {};
+    CK(cudaMemcpyAsync(cnt, cnt_d, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->packets = (int64_t)cnt[rg::CNT_PACKETS];
+        stats->escaped = (int64_t)cnt[rg::CNT_ESCAPED];
+        stats->absorbed = (int64_t)cnt[rg::CNT_ABSORBED];
+        stats->capped = (int64_t)cnt[rg::CNT_CAPPED];
+        stats->errors = (int64_t)cnt[rg::CNT_ERRORS];
+        stats->nscatt_line = (int64_t)cnt[rg::CNT_SCATT_LINE];
+        stats->nscatt_dust = (int64_t)cnt[rg::CNT_SCATT_DUST];
+        stats->ncross = (int64_t)cnt[rg::CNT_CROSS];
+        stats->upar_trials = (int64_t)cnt[rg::CNT_UPAR_TRIALS];
+        stats->leaf_loads = (int64_t)cnt[rg::CNT_LEAF_LOADS];
+        stats->son_loads = (int64_t)cnt[rg::CNT_SON_LOADS];
+        stats->nbor_loads = (int64_t)cnt[rg::CNT_NBOR_LOADS];
+    }
+    if (ctx->phys.fail_on_cap && cnt[rg::CNT_CAPPED] > 0)
+        return fail(ctx, RASCAS_E_CAPPED, "some packets reached a cap");
+    return RASCAS_OK;
+}
+
 }  // extern "C"

@@ -137,6 +137,7 @@ cudaError_t launch_ray_tau(const Params& P, long long n, const double* pos, cons
 cudaError_t launch_eval_voigt(long long n, const float* a, const double* x, float* H, cudaStream_t st);
 cudaError_t launch_sample_upar(const Params& P, long long n, const double* x, const float* a,
                                const uint64_t* id, float* u, int32_t* ndraw, cudaStream_t st);
+cudaError_t noalloc_scratch(int device, void** ptr, size_t* bytes);
 int propagate_block_size();
 size_t propagate_smem(int nline, int block);
 int propagate_blocks_per_sm(int block, bool peel);
