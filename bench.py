@@ -50,6 +50,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--batch-models", type=int, default=512,
+                    help="models in the batched-vs-plain comparison (0 = skip it)")
+    ap.add_argument("--batch-scale", type=float, default=0.01,
+                    help="packets per batch model: log-uniform [1e3, 1e5] times this")
+    ap.add_argument("--batch-cap", type=int, default=20000,
+                    help="scatterings per packet cap in the batch comparison")
     ap.add_argument("--max-scatt", type=int, default=0,
                     help="cap scatterings per packet (profiling runs only; 0 = the full workload)")
     return ap.parse_args()
@@ -152,6 +158,37 @@ def run_reference(args):
                              "sample": "%d packets of the workload per step, %d threads" % (int(np.mean([r[2] for r in rates])), threads)},
             "e2e": {"value": sc, "unit": "scatterings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ batch comparison
+def run_batch(args):
+    """Many uneven independent models: one persistent launch (CUDA graph,
+    autotuned shape) against one launch per model on the same stream."""
+    import paper_2001_11252_gb300 as rg
+    import synth
+    models = synth.batch_models(args.batch_models, packet_scale=args.batch_scale)
+    ctx = rg.Context(0)
+    w0 = models[0]
+    ctx.set_lines(w0.lines, w0.dust)
+    ph = w0.physics
+    ctx.set_physics(ph.recoil, ph.isotropic, 0, ph.x_gauss, args.batch_cap, 0, ph.tau_stop, ph.seed)
+    ctx.load_batch(models, nbin=200)
+    tune = ctx.autotune_batch(max_scatt=max(1, args.batch_cap // 20))
+    ctx.propagate_batch(rg.BATCH_PERSISTENT)           # warm-up (graph capture)
+    t0 = time.perf_counter()
+    stb = ctx.propagate_batch(rg.BATCH_PERSISTENT)
+    tb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    stp = ctx.propagate_batch(rg.BATCH_PER_MODEL)
+    tp = time.perf_counter() - t0
+    sc = stb["nscatt_line"] + stb["nscatt_dust"]
+    ctx.close()
+    return {"models": len(models), "packets": stb["packets"], "scatterings": sc, "capped": stb["capped"],
+            "cap_per_packet": args.batch_cap, "persistent_s": tb, "per_model_s": tp,
+            "persistent_scatt_per_s": sc / tb, "per_model_scatt_per_s": sc / tp, "speedup": tp / tb,
+            "autotuned": {"block": tune["best"][0], "blocks_per_sm": tune["best"][1]},
+            "workload": "512 homogeneous slab/sphere models: tau0 log-U[1e2,1e7], T log-U[1e2,1e5] K, "
+                        "v_max U[0,300] km/s, (2^d)^3 grids d in 2..5, packets log-U[1e3,1e5] x %g" % args.batch_scale}
 
 
 # ------------------------------------------------------------------ our arm
@@ -297,6 +334,8 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps,
             "clocks": clk}
+    if args.batch_models > 0 and world == 1:
+        line["batch"] = run_batch(args)
     if not args.no_cpu_baseline and world == 1:
         threads = os.cpu_count() or 1
         sc, pr, npk, secs = cpu_oracle_rate(workload, args.cpu_seconds, threads)

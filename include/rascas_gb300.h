@@ -240,6 +240,48 @@ int rascas_eval_voigt(rascas_ctx *ctx, int64_t n, const float *a, const double *
 int rascas_sample_upar(rascas_ctx *ctx, int64_t n, const double *x, const float *a,
                        const uint64_t *id, float *u, int32_t *ndraw, int mem);
 
+/* ---- batches of independent models --------------------------------------- */
+
+/* One independent model of a batch: its own octree and leaf fields, domain,
+ * escape-spectrum axis [nu_lo, nu_hi) and packet list (npackets entries).
+ * Lines, dust and physics switches are the context's.  The paper's master
+ * distributes bundles of packets of many domains to workers (Sect. 4.4); here
+ * every model's packets feed one device work queue. */
+typedef struct {
+    rascas_octree tree;
+    rascas_domain domain;
+    double nu_lo, nu_hi;
+    rascas_packets_in packets;
+    int64_t npackets;
+} rascas_model;
+
+enum { RASCAS_BATCH_PERSISTENT = 0,   /* one persistent launch over all models (CUDA graph) */
+       RASCAS_BATCH_PER_MODEL = 1 };  /* one launch per model, in sequence (the plain way) */
+
+/* Launch shape tried by the autotuner and its time for the capped batch. */
+typedef struct {
+    int32_t block, blocks_per_sm;
+    double ms;
+} rascas_tune;
+
+/* Copy nmodels models to the device (arrays per `mem`), validating each octree
+ * like rascas_load_octree.  Needs the lines set (the queue is ordered by each
+ * model's estimated line-centre optical depth, costliest first).  Escape
+ * spectra: nbin bins per model. */
+int rascas_load_batch(rascas_ctx *ctx, const rascas_model *models, int32_t nmodels, int32_t nbin, int mem);
+/* Propagate every packet of the loaded batch (spectra are zeroed first);
+ * mode = RASCAS_BATCH_*.  Synchronises; stats (may be NULL) cover the batch,
+ * kernel_ms the device time of the whole call. */
+int rascas_propagate_batch(rascas_ctx *ctx, int32_t mode, rascas_run_stats *stats);
+/* Escape spectra [nmodels][nbin] in the order the models were given. */
+int rascas_get_batch_spectra(rascas_ctx *ctx, float *dst, size_t count, int mem);
+/* Time the persistent batch launch for block sizes {64, 128} and every
+ * resident-block count per SM, with each packet capped at max_scatt
+ * scatterings, and keep the fastest shape for later rascas_propagate_batch
+ * calls.  tried (may be NULL) receives up to max_tried timings. */
+int rascas_autotune_batch(rascas_ctx *ctx, int64_t max_scatt, rascas_tune *best, rascas_tune *tried,
+                          int32_t max_tried, int32_t *ntried);
+
 /* ---- allocation-free variant ------------------------------------------- */
 
 /* Largest n accepted by rascas_propagate_noalloc. */

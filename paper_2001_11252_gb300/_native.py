@@ -81,6 +81,17 @@ class Event(C.Structure):
                 ("ndraw", C.c_int64), ("nscatt", C.c_int64), ("nsteps", C.c_int64)]
 
 
+class Model(C.Structure):
+    _fields_ = [("tree", Octree), ("domain", Domain), ("nu_lo", C.c_double), ("nu_hi", C.c_double),
+                ("packets", PacketsIn), ("npackets", C.c_int64)]
+
+
+class Tune(C.Structure):
+    _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("ms", C.c_double)]
+
+
+BATCH_PERSISTENT, BATCH_PER_MODEL = 0, 1
+
 EVENT_DTYPE = np.dtype([("p", "<f8", 3), ("k", "<f8", 3), ("nu", "<f8"), ("leaf", "<i4"), ("level", "<i4"),
                         ("ijk", "<i4", 3), ("status", "<i4"), ("ndraw", "<i8"), ("nscatt", "<i8"),
                         ("nsteps", "<i8")])
@@ -116,6 +127,10 @@ def lib():
             "rascas_trace": [vp, C.POINTER(PacketsIn), i64, i32, vp, vp, C.c_int],
             "rascas_eval_voigt": [vp, i64, vp, vp, vp, C.c_int],
             "rascas_sample_upar": [vp, i64, vp, vp, vp, vp, vp, C.c_int],
+            "rascas_load_batch": [vp, C.POINTER(Model), i32, i32, C.c_int],
+            "rascas_propagate_batch": [vp, i32, C.POINTER(Stats)],
+            "rascas_get_batch_spectra": [vp, vp, C.c_size_t, C.c_int],
+            "rascas_autotune_batch": [vp, i64, C.POINTER(Tune), C.POINTER(Tune), i32, C.POINTER(i32)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -371,6 +386,55 @@ class Context:
         self._ck(self._L.rascas_sample_upar(self._h, n, _ptr(x), _ptr(a), _ptr(ids), _ptr(u), _ptr(nd), mem),
                  "sample_upar")
         return u, nd
+
+    # ------------------------------------------------------------ batches
+    def load_batch(self, workloads, nbin):
+        """Load independent models (objects with medium, domain, detector
+        (nu_lo, nu_hi) and packets, like synth.Workload) as one batch.  Lines,
+        dust and physics must already be set on the context."""
+        arr = (Model * len(workloads))()
+        keep = []
+        for i, wl in enumerate(workloads):
+            m = wl.medium
+            a = [np.ascontiguousarray(m.tree.son, dtype=np.int32)] + [
+                np.ascontiguousarray(x, dtype=np.float32) for x in (m.n_HI, m.vx, m.vy, m.vz, m.T, m.n_dust)]
+            pk = wl.packets
+            b = [np.ascontiguousarray(pk.pos, dtype=np.float64), np.ascontiguousarray(pk.dir, dtype=np.float64),
+                 np.ascontiguousarray(pk.nu, dtype=np.float64), np.ascontiguousarray(pk.ids, dtype=np.uint64)]
+            keep += a + b
+            M = arr[i]
+            M.tree.noct, M.tree.nleaf = a[0].size // 8, a[1].size
+            M.tree.son, M.tree.n_HI, M.tree.vx, M.tree.vy, M.tree.vz, M.tree.T, M.tree.n_dust = [x.ctypes.data for x in a]
+            M.tree.n_metal = None
+            M.tree.box_cm = float(m.box_cm)
+            M.domain.kind = wl.domain.kind
+            M.domain.centre[:] = [float(v) for v in wl.domain.centre]
+            M.domain.size = float(wl.domain.size)
+            M.nu_lo, M.nu_hi = float(wl.detector.nu_lo), float(wl.detector.nu_hi)
+            M.packets = PacketsIn(*[x.ctypes.data for x in b])
+            M.npackets = int(pk.n)
+        self.batch_shape = (len(workloads), int(nbin))
+        self._ck(self._L.rascas_load_batch(self._h, arr, len(workloads), int(nbin), HOST), "load_batch")
+
+    def propagate_batch(self, mode=BATCH_PERSISTENT):
+        st = Stats()
+        self._ck(self._L.rascas_propagate_batch(self._h, int(mode), C.byref(st)), "propagate_batch")
+        return st.as_dict()
+
+    def get_batch_spectra(self):
+        dst = np.zeros(self.batch_shape, dtype=np.float32)
+        self._ck(self._L.rascas_get_batch_spectra(self._h, C.c_void_p(dst.ctypes.data), dst.size, HOST),
+                 "get_batch_spectra")
+        return dst
+
+    def autotune_batch(self, max_scatt=1000):
+        best = Tune()
+        tried = (Tune * 64)()
+        nt = C.c_int32()
+        self._ck(self._L.rascas_autotune_batch(self._h, int(max_scatt), C.byref(best), tried, 64, C.byref(nt)),
+                 "autotune_batch")
+        return {"best": (best.block, best.blocks_per_sm, best.ms),
+                "tried": [(tried[i].block, tried[i].blocks_per_sm, tried[i].ms) for i in range(nt.value)]}
 
     def _stream_sync_torch(self, mem):
         """Device calls run on torch's current stream."""

@@ -3,6 +3,7 @@
 // packed leaf records), problem set-up and kernel launches.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -42,6 +43,16 @@ struct DevBuf {
     }
 };
 
+// an octree and its leaf records as prepared on the host (Sect. 4.3 indices)
+struct HostMesh {
+    int noct = 0, nleaf = 0, max_level = 0, top_level = 0;
+    double box_cm = 0.0;
+    bool has_metal = false;
+    std::vector<int> son, nbr, top;   // 8 per oct, 8 per oct, 4 per top-grid region
+    std::vector<float> rec;           // 8 per leaf
+    std::vector<int> leaf_level, leaf_ijk;
+};
+
 }  // namespace
 
 struct rascas_ctx {
@@ -51,12 +62,7 @@ struct rascas_ctx {
     int sms = 0;
     // mesh
     bool has_mesh = false;
-    int noct = 0, nleaf = 0, max_level = 0, top_level = 0;
-    double box_cm = 0.0;
-    std::vector<int> leaf_level;
-    std::vector<int> leaf_ijk;     // 3 per leaf
-    std::vector<float> rec;        // 8 per leaf
-    bool has_metal = false;
+    HostMesh mesh;
     DevBuf d_rec, d_son, d_nbr, d_top;
     // problem
     bool has_domain = false, has_lines = false, has_phys = false, has_det = false;
@@ -66,6 +72,20 @@ struct rascas_ctx {
     Params P{};
     DevBuf d_spec, d_pspec, d_pimg, d_pcube, d_counters, d_params;
     DevBuf stage_in, stage_out, stage_aux;
+    // batch of independent models
+    struct Batch {
+        int nmodels = 0, nbin = 0, nline_at_load = 0;
+        long long npackets = 0;
+        std::vector<int> order;          // scheduled position -> model index
+        std::vector<long long> first;    // packet prefix sums in scheduled order
+        DevBuf d_rec, d_son, d_nbr, d_top, d_geo, d_first, d_pos, d_dir, d_nu, d_id, d_spec;
+        int block = 128, blocks_per_sm = 0;   // launch shape (autotuned)
+        cudaGraphExec_t graph = nullptr;
+        cudaStream_t graph_stream = nullptr;
+        unsigned long long graph_key = 0;
+    } batch;
+    cudaStream_t own_stream = nullptr;    // for graph capture when the context's stream is the legacy one
+    unsigned long long version = 1;       // bumped by every set-up call
 };
 
 namespace {
@@ -92,24 +112,24 @@ cudaError_t to_host(void* dst, const void* src, size_t bytes, int mem) {
     return cudaSuccess;
 }
 
-void leaf_flags(rascas_ctx* ctx) {
-    // a leaf is interior when it lies strictly inside the domain with a
-    // relative margin: then no ray from inside it reaches the border before
-    // one of its faces, and the walk skips the border distance there
-    for (int i = 0; i < ctx->nleaf; ++i) {
-        int l = ctx->leaf_level[i];
+// leaf flags for a domain: a leaf is interior when it lies strictly inside the
+// domain with a relative margin; then no ray from inside it reaches the border
+// before one of its faces, and the walk skips the border distance there
+void mesh_flags(HostMesh& M, const rascas_domain* dom) {
+    for (int i = 0; i < M.nleaf; ++i) {
+        int l = M.leaf_level[i];
         double h = std::ldexp(1.0, -l);
         double lo[3], hi[3];
         for (int ax = 0; ax < 3; ++ax) {
-            lo[ax] = ctx->leaf_ijk[3 * i + ax] * h;
+            lo[ax] = M.leaf_ijk[3 * (size_t)i + ax] * h;
             hi[ax] = lo[ax] + h;
         }
         bool interior = false;
-        if (ctx->has_domain) {
-            const double* c = ctx->dom.centre;
-            double R = ctx->dom.size;
+        if (dom) {
+            const double* c = dom->centre;
+            double R = dom->size;
             const double m = 1e-9 * (R > 0 ? R : 1.0);
-            if (ctx->dom.kind == RASCAS_DOMAIN_SPHERE) {
+            if (dom->kind == RASCAS_DOMAIN_SPHERE) {
                 double d2 = 0.0;
                 for (int ax = 0; ax < 3; ++ax) {
                     double far = std::fmax(std::fabs(lo[ax] - c[ax]), std::fabs(hi[ax] - c[ax]));
@@ -119,84 +139,34 @@ void leaf_flags(rascas_ctx* ctx) {
             } else {
                 interior = true;
                 for (int ax = 0; ax < 3; ++ax) {
-                    if (ctx->dom.kind == RASCAS_DOMAIN_SLAB && ax != 2) continue;
+                    if (dom->kind == RASCAS_DOMAIN_SLAB && ax != 2) continue;
                     if (!(lo[ax] > c[ax] - R + m && hi[ax] < c[ax] + R - m)) interior = false;
                 }
             }
         }
         int flags = interior ? 0 : rg::kFlagBorder;
-        std::memcpy(&ctx->rec[8 * i + 7], &flags, 4);
+        std::memcpy(&M.rec[8 * (size_t)i + 7], &flags, 4);
     }
 }
 
-}  // namespace
-
-extern "C" {
-
-int rascas_create(rascas_ctx** out, int device) {
-    if (!out) return RASCAS_E_ARG;
-    *out = nullptr;
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return RASCAS_E_CUDA;
-    rascas_ctx* ctx = new (std::nothrow) rascas_ctx();
-    if (!ctx) return RASCAS_E_OOM;
-    ctx->device = device;
-    if (cudaSetDevice(device) != cudaSuccess) {
-        delete ctx;
-        return RASCAS_E_CUDA;
-    }
-    cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
-    if (ctx->d_counters.ensure(sizeof(unsigned long long) * (rg::CNT_N + 1)) != cudaSuccess ||
-        ctx->d_params.ensure(sizeof(Params)) != cudaSuccess) {
-        ctx->d_counters.release();
-        delete ctx;
-        return RASCAS_E_OOM;
-    }
-    ctx->P.self = (const Params*)ctx->d_params.p;
-    ctx->P.counters = (unsigned long long*)ctx->d_counters.p;
-    ctx->P.head = ctx->P.counters + rg::CNT_N;
-    ctx->P.tau_stop = 50.0;
-    ctx->P.x_gauss = 8.0f;
-    ctx->P.recoil = 1;
-    *out = ctx;
-    return RASCAS_OK;
-}
-
-int rascas_destroy(rascas_ctx* ctx) {
-    if (!ctx) return RASCAS_E_ARG;
-    cudaSetDevice(ctx->device);
-    for (DevBuf* b : {&ctx->d_rec, &ctx->d_son, &ctx->d_nbr, &ctx->d_top, &ctx->d_spec, &ctx->d_pspec,
-                      &ctx->d_pimg, &ctx->d_pcube, &ctx->d_counters, &ctx->d_params, &ctx->stage_in,
-                      &ctx->stage_out, &ctx->stage_aux})
-        b->release();
-    delete ctx;
-    return RASCAS_OK;
-}
-
-const char* rascas_last_error(const rascas_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
-
-int rascas_set_stream(rascas_ctx* ctx, void* stream) {
-    if (!ctx) return RASCAS_E_ARG;
-    ctx->stream = (cudaStream_t)stream;
-    return RASCAS_OK;
-}
-
-int rascas_load_octree(rascas_ctx* ctx, const rascas_octree* t, int mem) {
-    if (!ctx || !t) return RASCAS_E_ARG;
+// validate an octree and build its host-side indices: BFS levels and
+// coordinates, father and neighbour cells per oct (Sect. 4.3), the dense top
+// grid, packed leaf records.  Returns 0 or an error message.
+const char* build_mesh(const rascas_octree* t, int mem, HostMesh& M, cudaError_t& cerr) {
+    cerr = cudaSuccess;
     if (t->noct < 1 || t->nleaf < 1 || !t->son || !t->n_HI || !t->vx || !t->vy || !t->vz || !t->T || !t->n_dust)
-        return fail(ctx, RASCAS_E_ARG, "octree: missing array or empty tree");
-    if (!(t->box_cm > 0.0)) return fail(ctx, RASCAS_E_ARG, "octree: box_cm must be > 0");
-    CK(cudaSetDevice(ctx->device));
+        return "octree: missing array or empty tree";
+    if (!(t->box_cm > 0.0)) return "octree: box_cm must be > 0";
     const int noct = t->noct, nleaf = t->nleaf;
     std::vector<int> son((size_t)8 * noct);
-    CK(to_host(son.data(), t->son, son.size() * 4, mem));
+    if ((cerr = to_host(son.data(), t->son, son.size() * 4, mem)) != cudaSuccess) return "octree: copy failed";
     std::vector<float> f[7];
     const float* src[7] = {t->n_HI, t->vx, t->vy, t->vz, t->T, t->n_dust, t->n_metal};
     for (int i = 0; i < 7; ++i) {
         f[i].assign(nleaf, 0.0f);
-        if (src[i]) CK(to_host(f[i].data(), src[i], (size_t)nleaf * 4, mem));
+        if (src[i] && (cerr = to_host(f[i].data(), src[i], (size_t)nleaf * 4, mem)) != cudaSuccess)
+            return "octree: copy failed";
     }
-    // breadth-first traversal: validates links, gives levels and coordinates
     std::vector<int> oct_level(noct, 0), oct_org((size_t)3 * noct, 0), oct_father(noct, -1);
     std::vector<int> lvl(nleaf, 0), ijk((size_t)3 * nleaf, 0);
     std::vector<int> queue;
@@ -208,31 +178,30 @@ int rascas_load_octree(rascas_ctx* ctx, const rascas_octree* t, int mem) {
     for (size_t qi = 0; qi < queue.size(); ++qi) {
         int o = queue[qi];
         int l = oct_level[o];
-        if (l > 21) return fail(ctx, RASCAS_E_ARG, "octree: deeper than 21 levels");
+        if (l > 21) return "octree: deeper than 21 levels";
         max_level = l > max_level ? l : max_level;
         for (int c = 0; c < 8; ++c) {
-            int ci[3] = {oct_org[3 * o] + (c & 1), oct_org[3 * o + 1] + ((c >> 1) & 1),
-                         oct_org[3 * o + 2] + ((c >> 2) & 1)};
+            int ci[3] = {oct_org[3 * (size_t)o] + (c & 1), oct_org[3 * (size_t)o + 1] + ((c >> 1) & 1),
+                         oct_org[3 * (size_t)o + 2] + ((c >> 2) & 1)};
             int v = son[(size_t)8 * o + c];
             if (v > 0) {
-                if (v >= noct || oct_level[v] != 0) return fail(ctx, RASCAS_E_ARG, "octree: bad or repeated oct link");
+                if (v >= noct || oct_level[v] != 0) return "octree: bad or repeated oct link";
                 oct_level[v] = l + 1;
                 oct_father[v] = 8 * o + c;
                 for (int ax = 0; ax < 3; ++ax) oct_org[3 * (size_t)v + ax] = 2 * ci[ax];
                 queue.push_back(v);
             } else if (v < 0) {
                 long long leaf = -(long long)v - 1;
-                if (leaf >= nleaf || lvl[leaf] != 0) return fail(ctx, RASCAS_E_ARG, "octree: bad or repeated leaf link");
+                if (leaf >= nleaf || lvl[leaf] != 0) return "octree: bad or repeated leaf link";
                 lvl[leaf] = l;
                 for (int ax = 0; ax < 3; ++ax) ijk[3 * leaf + ax] = ci[ax];
                 ++seen_leaf;
             } else {
-                return fail(ctx, RASCAS_E_ARG, "octree: son value 0");
+                return "octree: son value 0";
             }
         }
     }
-    if ((int)queue.size() != noct || (int)seen_leaf != nleaf)
-        return fail(ctx, RASCAS_E_ARG, "octree: unreachable octs or leaves");
+    if ((int)queue.size() != noct || (int)seen_leaf != nleaf) return "octree: unreachable octs or leaves";
     // neighbour links: per oct the 6 cells (level l-1, or the deepest coarser
     // cell when the tree is not graded) across the faces of its father cell,
     // wrapped periodically; -1 for the root oct
@@ -291,41 +260,112 @@ int rascas_load_octree(rascas_ctx* ctx, const rascas_octree* t, int mem) {
             o = v;
         }
     }
-    // packed leaf records {n_HI, vx, vy, vz}, {T, n_dust, n_metal, flags}
-    ctx->rec.assign((size_t)8 * nleaf, 0.0f);
+    M.rec.assign((size_t)8 * nleaf, 0.0f);
     for (int i = 0; i < nleaf; ++i) {
-        float* r = &ctx->rec[8 * (size_t)i];
-        r[0] = f[0][i]; r[1] = f[1][i]; r[2] = f[2][i]; r[3] = f[3][i];
-        r[4] = f[4][i]; r[5] = f[5][i]; r[6] = f[6][i];
+        float* r = &M.rec[8 * (size_t)i];
+        for (int j = 0; j < 7; ++j) r[j] = f[j][i];
     }
-    ctx->noct = noct;
-    ctx->nleaf = nleaf;
-    ctx->max_level = max_level;
-    ctx->top_level = S;
-    ctx->box_cm = t->box_cm;
-    ctx->leaf_level.swap(lvl);
-    ctx->leaf_ijk.swap(ijk);
-    ctx->has_metal = t->n_metal != nullptr;
-    leaf_flags(ctx);
-    CK(ctx->d_rec.ensure(ctx->rec.size() * 4));
-    CK(ctx->d_son.ensure(son.size() * 4));
-    CK(ctx->d_nbr.ensure(nbr.size() * 4));
-    CK(ctx->d_top.ensure(top.size() * 4));
-    CK(cudaMemcpy(ctx->d_rec.p, ctx->rec.data(), ctx->rec.size() * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(ctx->d_son.p, son.data(), son.size() * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(ctx->d_nbr.p, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(ctx->d_top.p, top.data(), top.size() * 4, cudaMemcpyHostToDevice));
+    M.noct = noct;
+    M.nleaf = nleaf;
+    M.max_level = max_level;
+    M.top_level = S;
+    M.box_cm = t->box_cm;
+    M.has_metal = t->n_metal != nullptr;
+    M.son.swap(son);
+    M.nbr.swap(nbr);
+    M.top.swap(top);
+    M.leaf_level.swap(lvl);
+    M.leaf_ijk.swap(ijk);
+    return nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rascas_create(rascas_ctx** out, int device) {
+    if (!out) return RASCAS_E_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return RASCAS_E_CUDA;
+    rascas_ctx* ctx = new (std::nothrow) rascas_ctx();
+    if (!ctx) return RASCAS_E_OOM;
+    ctx->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete ctx;
+        return RASCAS_E_CUDA;
+    }
+    cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
+    if (ctx->d_counters.ensure(sizeof(unsigned long long) * (rg::CNT_N + 1)) != cudaSuccess ||
+        ctx->d_params.ensure(sizeof(Params)) != cudaSuccess) {
+        ctx->d_counters.release();
+        delete ctx;
+        return RASCAS_E_OOM;
+    }
+    ctx->P.self = (const Params*)ctx->d_params.p;
+    ctx->P.counters = (unsigned long long*)ctx->d_counters.p;
+    ctx->P.head = ctx->P.counters + rg::CNT_N;
+    ctx->P.tau_stop = 50.0;
+    ctx->P.x_gauss = 8.0f;
+    ctx->P.recoil = 1;
+    *out = ctx;
+    return RASCAS_OK;
+}
+
+int rascas_destroy(rascas_ctx* ctx) {
+    if (!ctx) return RASCAS_E_ARG;
+    cudaSetDevice(ctx->device);
+    for (DevBuf* b : {&ctx->d_rec, &ctx->d_son, &ctx->d_nbr, &ctx->d_top, &ctx->d_spec, &ctx->d_pspec,
+                      &ctx->d_pimg, &ctx->d_pcube, &ctx->d_counters, &ctx->d_params, &ctx->stage_in,
+                      &ctx->stage_out, &ctx->stage_aux})
+        b->release();
+    auto& B = ctx->batch;
+    for (DevBuf* b : {&B.d_rec, &B.d_son, &B.d_nbr, &B.d_top, &B.d_geo, &B.d_first, &B.d_pos, &B.d_dir, &B.d_nu,
+                      &B.d_id, &B.d_spec})
+        b->release();
+    if (B.graph) cudaGraphExecDestroy(B.graph);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    delete ctx;
+    return RASCAS_OK;
+}
+
+const char* rascas_last_error(const rascas_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int rascas_set_stream(rascas_ctx* ctx, void* stream) {
+    if (!ctx) return RASCAS_E_ARG;
+    ctx->stream = (cudaStream_t)stream;
+    return RASCAS_OK;
+}
+
+int rascas_load_octree(rascas_ctx* ctx, const rascas_octree* t, int mem) {
+    if (!ctx || !t) return RASCAS_E_ARG;
+    CK(cudaSetDevice(ctx->device));
+    HostMesh M;
+    cudaError_t ce;
+    const char* err = build_mesh(t, mem, M, ce);
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "load_octree");
+    if (err) return fail(ctx, RASCAS_E_ARG, err);
+    mesh_flags(M, ctx->has_domain ? &ctx->dom : nullptr);
+    CK(ctx->d_rec.ensure(M.rec.size() * 4));
+    CK(ctx->d_son.ensure(M.son.size() * 4));
+    CK(ctx->d_nbr.ensure(M.nbr.size() * 4));
+    CK(ctx->d_top.ensure(M.top.size() * 4));
+    CK(cudaMemcpy(ctx->d_rec.p, M.rec.data(), M.rec.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_son.p, M.son.data(), M.son.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_nbr.p, M.nbr.data(), M.nbr.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_top.p, M.top.data(), M.top.size() * 4, cudaMemcpyHostToDevice));
     Params& P = ctx->P;
     P.g.rec = (const float4*)ctx->d_rec.p;
     P.g.son = (const int*)ctx->d_son.p;
     P.g.nbr = (const int4*)ctx->d_nbr.p;
     P.g.top = (const int4*)ctx->d_top.p;
-    P.g.top_level = S;
-    P.g.max_level = max_level;
-    P.g.nleaf = nleaf;
-    P.g.noct = noct;
-    P.g.box_cm = t->box_cm;
-    P.g.box_cm_f = (float)t->box_cm;
+    P.g.top_level = M.top_level;
+    P.g.max_level = M.max_level;
+    P.g.nleaf = M.nleaf;
+    P.g.noct = M.noct;
+    P.g.box_cm = M.box_cm;
+    P.g.box_cm_f = (float)M.box_cm;
+    ctx->mesh = std::move(M);
     ctx->has_mesh = true;
     return RASCAS_OK;
 }
@@ -341,8 +381,8 @@ int rascas_set_domain(rascas_ctx* ctx, const rascas_domain* d) {
     P.g.dom_R = d->size;
     if (ctx->has_mesh) {
         CK(cudaSetDevice(ctx->device));
-        leaf_flags(ctx);
-        CK(cudaMemcpy(ctx->d_rec.p, ctx->rec.data(), ctx->rec.size() * 4, cudaMemcpyHostToDevice));
+        mesh_flags(ctx->mesh, &ctx->dom);
+        CK(cudaMemcpy(ctx->d_rec.p, ctx->mesh.rec.data(), ctx->mesh.rec.size() * 4, cudaMemcpyHostToDevice));
     }
     return RASCAS_OK;
 }
@@ -388,6 +428,7 @@ int rascas_set_lines(rascas_ctx* ctx, const rascas_line* lines, int32_t nline, c
         }
     }
     P.nline = nline;
+    ++ctx->version;
     P.dust_sigma = dust ? (float)dust->sigma : 0.0f;
     P.dust_albedo = dust ? (float)dust->albedo : 0.0f;
     P.dust_g = dust ? (float)dust->g : 0.0f;
@@ -410,6 +451,7 @@ int rascas_set_physics(rascas_ctx* ctx, const rascas_physics* ph) {
     P.tau_stop = ph->tau_stop;
     P.key0 = (uint32_t)ph->seed;
     P.key1 = (uint32_t)(ph->seed >> 32);
+    ++ctx->version;
     ctx->has_phys = true;
     return RASCAS_OK;
 }
@@ -486,7 +528,7 @@ int check_ready(rascas_ctx* ctx) {
     if (!ctx->has_phys) return fail(ctx, RASCAS_E_STATE, "no physics set");
     if (ctx->P.nline > 0) {
         for (int i = 0; i < ctx->P.nline; ++i)
-            if (ctx->P.line[i].dens == 1 && !ctx->has_metal)
+            if (ctx->P.line[i].dens == 1 && !ctx->mesh.has_metal)
                 return fail(ctx, RASCAS_E_STATE, "a line needs n_metal but the octree has none");
     }
     return RASCAS_OK;
@@ -523,7 +565,7 @@ int run_propagate(rascas_ctx* ctx, const rascas_packets_in* in, int64_t n, const
             P.g.nu_inv_range = 0.0;
         }
     }
-    rg::PacketsIn din{in->pos, in->dir, in->nu, in->id, (long long)n};
+    rg::PacketsIn din{in->pos, in->dir, in->nu, in->id, (long long)n, 0};
     rg::PacketsOut dout{};
     if (out) dout = rg::PacketsOut{out->status, out->nscatt, out->nu, out->pos, out->dir, out->path};
     rg::TraceOut tr{nullptr, nullptr, max_events};
@@ -541,7 +583,7 @@ int run_propagate(rascas_ctx* ctx, const rascas_packets_in* in, int64_t n, const
         CK(cudaMemcpyAsync(dir, in->dir, 3 * N * 8, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(nu, in->nu, N * 8, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(id, in->id, N * 8, cudaMemcpyHostToDevice, st));
-        din = rg::PacketsIn{pos, dir, nu, id, (long long)n};
+        din = rg::PacketsIn{pos, dir, nu, id, (long long)n, 0};
         if (out) {
             size_t bout = N * (4 + 8 + 8 + 24 + 24 + 8) + 64;
             CK(ctx->stage_out.ensure(bout));
@@ -798,7 +840,7 @@ int rascas_propagate_noalloc(rascas_ctx* ctx, const rascas_packets_in* in, int64
     cudaStream_t st = ctx->stream;
     CK(cudaMemsetAsync(cnt_d, 0, sizeof(unsigned long long) * (rg::CNT_N + 1), st));
     CK(cudaMemcpyAsync(par_d, &P, sizeof(Params), cudaMemcpyHostToDevice, st));
-    rg::PacketsIn din{pos, dir, nu, id, (long long)n};
+    rg::PacketsIn din{pos, dir, nu, id, (long long)n, 0};
     rg::PacketsOut dout{};
     if (out) dout = rg::PacketsOut{out->status ? ost : nullptr, out->nscatt ? ons : nullptr, out->nu ? onu : nullptr,
                                    out->pos ? opos : nullptr, out->dir ? odir : nullptr, out->path ? opath : nullptr};
@@ -838,6 +880,256 @@ int rascas_propagate_noalloc(rascas_ctx* ctx, const rascas_packets_in* in, int64
     }
     if (ctx->phys.fail_on_cap && cnt[rg::CNT_CAPPED] > 0)
         return fail(ctx, RASCAS_E_CAPPED, "some packets reached a cap");
+    return RASCAS_OK;
+}
+
+int rascas_load_batch(rascas_ctx* ctx, const rascas_model* models, int32_t nmodels, int32_t nbin, int mem) {
+    if (!ctx || !models || nmodels < 1 || nbin < 1 || (mem != RASCAS_HOST && mem != RASCAS_DEVICE))
+        return fail(ctx, RASCAS_E_ARG, "load_batch: bad arguments");
+    if (!ctx->has_lines) return fail(ctx, RASCAS_E_STATE, "load_batch: set the lines first");
+    CK(cudaSetDevice(ctx->device));
+    auto& B = ctx->batch;
+    const Params& P = ctx->P;
+    std::vector<HostMesh> meshes(nmodels);
+    std::vector<double> cost(nmodels, 0.0);
+    for (int m = 0; m < nmodels; ++m) {
+        const rascas_model& md = models[m];
+        if (md.domain.kind < 0 || md.domain.kind > 2 || !(md.domain.size > 0.0) || !(md.nu_hi > md.nu_lo) ||
+            md.npackets < 0 || (md.npackets > 0 && (!md.packets.pos || !md.packets.dir || !md.packets.nu ||
+                                                   !md.packets.id)))
+            return fail(ctx, RASCAS_E_ARG, "load_batch: model " + std::to_string(m) + ": bad domain, axis or packets");
+        cudaError_t ce;
+        const char* err = build_mesh(&md.tree, mem, meshes[m], ce);
+        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "load_batch");
+        if (err) return fail(ctx, RASCAS_E_ARG, "load_batch: model " + std::to_string(m) + ": " + err);
+        for (int i = 0; i < P.nline; ++i)
+            if (P.line[i].dens == 1 && !meshes[m].has_metal)
+                return fail(ctx, RASCAS_E_STATE, "load_batch: a line needs n_metal but a model has none");
+        mesh_flags(meshes[m], &md.domain);
+        // expected scatterings per packet grow with the line-centre optical
+        // depth across the domain: schedule the costliest models first
+        double t = 0.0;
+        const HostMesh& M = meshes[m];
+        for (int i = 0; i < M.nleaf; ++i) {
+            double n = M.rec[8 * (size_t)i], T = std::fmax((double)M.rec[8 * (size_t)i + 4], 1e-30);
+            t = std::fmax(t, n * P.line[0].abund * P.line[0].sig_pref / std::sqrt(T));
+        }
+        cost[m] = t * md.domain.size * M.box_cm;
+    }
+    B.order.resize(nmodels);
+    for (int m = 0; m < nmodels; ++m) B.order[m] = m;
+    std::stable_sort(B.order.begin(), B.order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    // concatenate meshes and packets in scheduled order
+    size_t nrec = 0, nson = 0, nnbr = 0, ntop = 0;
+    long long npk = 0;
+    B.first.assign(nmodels + 1, 0);
+    for (int k = 0; k < nmodels; ++k) {
+        const HostMesh& M = meshes[B.order[k]];
+        nrec += M.rec.size(); nson += M.son.size(); nnbr += M.nbr.size(); ntop += M.top.size();
+        npk += models[B.order[k]].npackets;
+        B.first[k + 1] = npk;
+    }
+    CK(B.d_rec.ensure(nrec * 4)); CK(B.d_son.ensure(nson * 4)); CK(B.d_nbr.ensure(nnbr * 4));
+    CK(B.d_top.ensure(ntop * 4)); CK(B.d_geo.ensure(sizeof(rg::Geo) * nmodels));
+    CK(B.d_first.ensure(sizeof(long long) * (nmodels + 1)));
+    CK(B.d_spec.ensure(sizeof(float) * (size_t)nmodels * nbin));
+    size_t pk_bytes = (size_t)(npk > 0 ? npk : 1) * 8;
+    CK(B.d_pos.ensure(3 * pk_bytes)); CK(B.d_dir.ensure(3 * pk_bytes));
+    CK(B.d_nu.ensure(pk_bytes)); CK(B.d_id.ensure(pk_bytes));
+    std::vector<rg::Geo> geo(nmodels);
+    size_t orec = 0, oson = 0, onbr = 0, otop = 0;
+    for (int k = 0; k < nmodels; ++k) {
+        int m = B.order[k];
+        const HostMesh& M = meshes[m];
+        const rascas_model& md = models[m];
+        char* drec = (char*)B.d_rec.p + orec * 4;
+        char* dson = (char*)B.d_son.p + oson * 4;
+        char* dnbr = (char*)B.d_nbr.p + onbr * 4;
+        char* dtop = (char*)B.d_top.p + otop * 4;
+        CK(cudaMemcpy(drec, M.rec.data(), M.rec.size() * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(dson, M.son.data(), M.son.size() * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(dnbr, M.nbr.data(), M.nbr.size() * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(dtop, M.top.data(), M.top.size() * 4, cudaMemcpyHostToDevice));
+        rg::Geo& G = geo[k];
+        G.rec = (const float4*)drec; G.son = (const int*)dson; G.nbr = (const int4*)dnbr; G.top = (const int4*)dtop;
+        G.top_level = M.top_level; G.max_level = M.max_level; G.nleaf = M.nleaf; G.noct = M.noct;
+        G.box_cm = M.box_cm; G.box_cm_f = (float)M.box_cm;
+        G.dom_kind = md.domain.kind;
+        for (int ax = 0; ax < 3; ++ax) G.dom_c[ax] = md.domain.centre[ax];
+        G.dom_R = md.domain.size;
+        G.nu_lo = md.nu_lo; G.nu_inv_range = 1.0 / (md.nu_hi - md.nu_lo); G.nbin = nbin;
+        G.spec = (float*)B.d_spec.p + (size_t)m * nbin;
+        orec += M.rec.size(); oson += M.son.size(); onbr += M.nbr.size(); otop += M.top.size();
+        const size_t n = (size_t)md.npackets, o = (size_t)B.first[k];
+        if (n > 0) {
+            cudaMemcpyKind kind = mem == RASCAS_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+            CK(cudaMemcpy((double*)B.d_pos.p + 3 * o, md.packets.pos, 3 * n * 8, kind));
+            CK(cudaMemcpy((double*)B.d_dir.p + 3 * o, md.packets.dir, 3 * n * 8, kind));
+            CK(cudaMemcpy((double*)B.d_nu.p + o, md.packets.nu, n * 8, kind));
+            CK(cudaMemcpy((uint64_t*)B.d_id.p + o, md.packets.id, n * 8, kind));
+        }
+    }
+    CK(cudaMemcpy(B.d_geo.p, geo.data(), sizeof(rg::Geo) * nmodels, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(B.d_first.p, B.first.data(), sizeof(long long) * (nmodels + 1), cudaMemcpyHostToDevice));
+    B.nmodels = nmodels;
+    B.nbin = nbin;
+    B.npackets = npk;
+    B.nline_at_load = P.nline;
+    ++ctx->version;
+    return RASCAS_OK;
+}
+
+int rascas_propagate_batch(rascas_ctx* ctx, int32_t mode, rascas_run_stats* stats) {
+    if (!ctx || (mode != RASCAS_BATCH_PERSISTENT && mode != RASCAS_BATCH_PER_MODEL))
+        return fail(ctx, RASCAS_E_ARG, "propagate_batch: bad arguments");
+    auto& B = ctx->batch;
+    if (B.nmodels < 1) return fail(ctx, RASCAS_E_STATE, "propagate_batch: no batch loaded");
+    if (!ctx->has_lines || !ctx->has_phys) return fail(ctx, RASCAS_E_STATE, "propagate_batch: lines or physics unset");
+    if (B.nline_at_load != ctx->P.nline) return fail(ctx, RASCAS_E_STATE, "propagate_batch: lines changed since load_batch");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    if (!st) {
+        if (!ctx->own_stream) CK(cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking));
+        st = ctx->own_stream;
+    }
+    Params P = ctx->P;
+    P.ndir = 0;
+    P.g.spec = nullptr;
+    P.models = (const rg::Geo*)B.d_geo.p;
+    P.model_first = (const long long*)B.d_first.p;
+    P.nmodels = B.nmodels;
+    rg::PacketsIn in{(const double*)B.d_pos.p, (const double*)B.d_dir.p, (const double*)B.d_nu.p,
+                     (const uint64_t*)B.d_id.p, B.npackets, 0};
+    rg::PacketsOut out{};
+    rg::TraceOut tr{nullptr, nullptr, 0};
+    const int block = B.block;
+    int per_sm = B.blocks_per_sm > 0 ? B.blocks_per_sm : rg::propagate_batch_blocks_per_sm(P.nline, block);
+    if (per_sm < 1) per_sm = 1;
+    const int grid = ctx->sms * per_sm;
+    const size_t cnt_bytes = sizeof(unsigned long long) * (rg::CNT_N + 1);
+    const size_t spec_bytes = sizeof(float) * (size_t)B.nmodels * B.nbin;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, st));
+    if (mode == RASCAS_BATCH_PERSISTENT) {
+        // one persistent launch over every model's packets, replayed from a
+        // captured CUDA graph (re-captured when the set-up or shape changed)
+        unsigned long long key = ctx->version * 1000003ULL + (unsigned long long)(block * 64 + per_sm);
+        if (!B.graph || B.graph_key != key || B.graph_stream != st) {
+            if (B.graph) {
+                cudaGraphExecDestroy(B.graph);
+                B.graph = nullptr;
+            }
+            cudaGraph_t g;
+            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e1c = cudaMemsetAsync(ctx->d_counters.p, 0, cnt_bytes, st);
+            cudaError_t e2c = cudaMemsetAsync(B.d_spec.p, 0, spec_bytes, st);
+            cudaError_t e3c = rg::launch_propagate(P, in, out, tr, grid, block, st);
+            cudaError_t ec = cudaStreamEndCapture(st, &g);
+            if (e1c != cudaSuccess || e2c != cudaSuccess || e3c != cudaSuccess || ec != cudaSuccess)
+                return cuda_fail(ctx, ec != cudaSuccess ? ec : (e3c != cudaSuccess ? e3c : e1c), "batch graph capture");
+            cudaError_t ei = cudaGraphInstantiate(&B.graph, g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) return cuda_fail(ctx, ei, "cudaGraphInstantiate");
+            B.graph_key = key;
+            B.graph_stream = st;
+        }
+        CK(cudaGraphLaunch(B.graph, st));
+    } else {
+        // the plain alternative: one launch per model, in sequence
+        CK(cudaMemsetAsync(ctx->d_counters.p, 0, cnt_bytes, st));
+        CK(cudaMemsetAsync(B.d_spec.p, 0, spec_bytes, st));
+        for (int k = 0; k < B.nmodels; ++k) {
+            long long n = B.first[k + 1] - B.first[k];
+            if (n <= 0) continue;
+            Params Pk = P;
+            Pk.models = (const rg::Geo*)B.d_geo.p + k;
+            Pk.model_first = (const long long*)B.d_first.p + k;
+            Pk.nmodels = 1;
+            rg::PacketsIn ink = in;
+            ink.first = B.first[k];
+            ink.n = B.first[k + 1];
+            long long blocks = (n + block - 1) / block;
+            int gk = (int)(blocks < grid ? blocks : grid);
+            CK(cudaMemsetAsync(P.head, 0, sizeof(unsigned long long), st));
+            CK(rg::launch_propagate(Pk, ink, out, tr, gk, block, st));
+        }
+    }
+    CK(cudaEventRecord(e1, st));
+    unsigned long long cnt[rg::CNT_N] = {};
+    CK(cudaMemcpyAsync(cnt, ctx->d_counters.p, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->packets = (int64_t)cnt[rg::CNT_PACKETS];
+        stats->escaped = (int64_t)cnt[rg::CNT_ESCAPED];
+        stats->absorbed = (int64_t)cnt[rg::CNT_ABSORBED];
+        stats->capped = (int64_t)cnt[rg::CNT_CAPPED];
+        stats->errors = (int64_t)cnt[rg::CNT_ERRORS];
+        stats->nscatt_line = (int64_t)cnt[rg::CNT_SCATT_LINE];
+        stats->nscatt_dust = (int64_t)cnt[rg::CNT_SCATT_DUST];
+        stats->ncross = (int64_t)cnt[rg::CNT_CROSS];
+        stats->upar_trials = (int64_t)cnt[rg::CNT_UPAR_TRIALS];
+        stats->leaf_loads = (int64_t)cnt[rg::CNT_LEAF_LOADS];
+        stats->son_loads = (int64_t)cnt[rg::CNT_SON_LOADS];
+        stats->nbor_loads = (int64_t)cnt[rg::CNT_NBOR_LOADS];
+        stats->kernel_ms = ms;
+    }
+    return RASCAS_OK;
+}
+
+int rascas_get_batch_spectra(rascas_ctx* ctx, float* dst, size_t count, int mem) {
+    if (!ctx || !dst) return RASCAS_E_ARG;
+    auto& B = ctx->batch;
+    if (B.nmodels < 1) return fail(ctx, RASCAS_E_STATE, "get_batch_spectra: no batch loaded");
+    if (count != (size_t)B.nmodels * B.nbin) return fail(ctx, RASCAS_E_ARG, "get_batch_spectra: count != nmodels*nbin");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemcpy(dst, B.d_spec.p, count * 4, mem == RASCAS_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+    return RASCAS_OK;
+}
+
+int rascas_autotune_batch(rascas_ctx* ctx, int64_t max_scatt, rascas_tune* best, rascas_tune* tried, int32_t max_tried,
+                          int32_t* ntried) {
+    if (!ctx || max_scatt < 1) return fail(ctx, RASCAS_E_ARG, "autotune_batch: bad arguments");
+    auto& B = ctx->batch;
+    if (B.nmodels < 1) return fail(ctx, RASCAS_E_STATE, "autotune_batch: no batch loaded");
+    const long long saved_scatt = ctx->P.max_scatt;
+    const int saved_block = B.block, saved_per_sm = B.blocks_per_sm;
+    ctx->P.max_scatt = max_scatt;   // short runs of the same batch, each packet capped
+    ++ctx->version;
+    rascas_tune bt{0, 0, 0.0};
+    int nt = 0;
+    int rc = RASCAS_OK;
+    for (int block : {64, 128}) {
+        int occ = rg::propagate_batch_blocks_per_sm(ctx->P.nline, block);
+        for (int per_sm = 1; per_sm <= occ && rc == RASCAS_OK; ++per_sm) {
+            B.block = block;
+            B.blocks_per_sm = per_sm;
+            rascas_run_stats st;
+            rc = rascas_propagate_batch(ctx, RASCAS_BATCH_PERSISTENT, &st);
+            if (rc != RASCAS_OK) break;
+            rascas_tune t{block, per_sm, st.kernel_ms};
+            if (tried && nt < max_tried) tried[nt] = t;
+            ++nt;
+            if (bt.ms == 0.0 || t.ms < bt.ms) bt = t;
+        }
+    }
+    ctx->P.max_scatt = saved_scatt;
+    ++ctx->version;
+    if (rc != RASCAS_OK) {
+        B.block = saved_block;
+        B.blocks_per_sm = saved_per_sm;
+        return rc;
+    }
+    B.block = bt.block;
+    B.blocks_per_sm = bt.blocks_per_sm;
+    if (best) *best = bt;
+    if (ntried) *ntried = nt;
     return RASCAS_OK;
 }
 

@@ -104,7 +104,8 @@ struct PacketsIn {
     const double* dir;
     const double* nu;
     const uint64_t* id;
-    long long n;
+    long long n;       // packets [first, n) of the arrays are propagated
+    long long first;
 };
 
 struct PacketsOut {
@@ -141,5 +142,6 @@ cudaError_t noalloc_scratch(int device, void** ptr, size_t* bytes);
 int propagate_block_size();
 size_t propagate_smem(int nline, int block);
 int propagate_blocks_per_sm(int block, bool peel);
+int propagate_batch_blocks_per_sm(int nline, int block);
 
 }  // namespace rg

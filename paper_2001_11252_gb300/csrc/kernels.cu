@@ -567,7 +567,7 @@ k_propagate(const __grid_constant__ Params P, PacketsIn in, PacketsOut out, Trac
             if ((int)lane == leader) base = atomicAdd(P.head, (unsigned long long)__popc(m));
             base = __shfl_sync(kFull, base, leader);
             if (want) {
-                long long idx = (long long)base + __popc(m & ((1u << lane) - 1u));
+                long long idx = in.first + (long long)base + __popc(m & ((1u << lane) - 1u));
                 if (idx < in.n) {
                     if constexpr (BATCH) {
                         s.mi = model_of(P, idx);
@@ -669,6 +669,15 @@ static int occ(int block) {
 
 int propagate_blocks_per_sm(int block, bool peel) {
     return peel ? occ<1, true, false>(block) : occ<1, false, false>(block);
+}
+
+int propagate_batch_blocks_per_sm(int nline, int block) {
+    switch (nline) {
+        case 1: return occ<1, false, true>(block);
+        case 2: return occ<2, false, true>(block);
+        case 3: return occ<3, false, true>(block);
+        default: return occ<4, false, true>(block);
+    }
 }
 
 template <int NL>

@@ -442,3 +442,52 @@ def expanding_sphere(N_HI=1e20, T=1e4, v_max_kms=200.0, tau_dust=0.5, n_packets=
                    dirs=PEEL_DIRS_3.copy(), npix=npix, fov=2 * R, centre=(0.5, 0.5, 0.5), cube=1)
     return Workload("expanding", med, Domain(0, (0.5, 0.5, 0.5), R), [line], dust,
                     Physics(recoil=1, isotropic=0, seed=seed), det, pk)
+
+
+def batch_models(n_models=512, packet_scale=1.0, seed_offset=0, max_scatt=0):
+    """Many independent homogeneous models (the batching workload): geometry
+    slab or sphere with equal probability; line-centre optical depth tau0
+    log-uniform in [1e2, 1e7] (centre-to-edge / half-thickness); T log-uniform
+    in [1e2, 1e5] K; v_max uniform in [0, 300] km/s (sphere: radial v_max r/R;
+    slab: v_z = v_max (z - 1/2)/(1/2)); uniform grid of depth d in {2..5}
+    ((2^d)^3 leaves); packets log-uniform in [1e3, 1e5] times packet_scale
+    (at least 1); Lya only, no dust; escape spectrum over
+    x in +-(4 (a tau0)^(1/3) + 10) of each model.  Returns Workloads that share
+    one line list and physics."""
+    seed = RUN_SEED + 3 + seed_offset
+    rng = np.random.default_rng(seed ^ 0xA5A5)
+    line = lya()
+    L = 1.0 * KPC_CM
+    out = []
+    first_id = 0
+    for m in range(n_models):
+        slab_geom = rng.random() < 0.5
+        tau0 = 10 ** rng.uniform(2, 7)
+        T = 10 ** rng.uniform(2, 5)
+        vmax = rng.uniform(0, 300) * 1e5
+        depth = int(rng.integers(2, 6))
+        npk = max(1, int(round(10 ** rng.uniform(3, 5) * packet_scale)))
+        tree = uniform_octree(depth)
+        ctr = tree.leaf_centres()
+        if slab_geom:
+            dom = Domain(1, (0.5, 0.5, 0.5), 0.5)
+            n = density_for_tau0(line, T, tau0, 0.5 * L)
+            med = uniform_medium(tree, L, n, T)
+            med.vz = (vmax * (ctr[:, 2] - 0.5) / 0.5).astype(np.float32)
+        else:
+            R = 0.45
+            dom = Domain(0, (0.5, 0.5, 0.5), R)
+            n = density_for_tau0(line, T, tau0, R * L)
+            med = uniform_medium(tree, L, n, T)
+            v = (vmax / R) * (ctr - 0.5)
+            med.vx, med.vy, med.vz = (v[:, i].astype(np.float32) for i in range(3))
+        dnu = doppler_width(line, T)
+        a = line.A_ul / (4 * math.pi * dnu)
+        xr = 4.0 * (a * tau0) ** (1.0 / 3.0) + 10.0 + vmax / (math.sqrt(2 * KB_CGS * T / line.mass_g))
+        lo, hi, nb = x_axis(line, T, -xr, xr, 200)
+        pk = point_source(npk, (0.5, 0.5, 0.5), nu_of(line.lambda_A), int(rng.integers(0, 2**31)),
+                          first_id=first_id)
+        first_id += npk
+        out.append(Workload("batch%03d" % m, med, dom, [line], Dust(),
+                            Physics(recoil=1, isotropic=0, seed=seed, max_scatt=max_scatt), Detector(lo, hi, nb), pk))
+    return out

@@ -1,0 +1,67 @@
+"""Batches of independent models (the persistent work-queue pattern) on the
+GPU: one persistent launch over every model equals one launch per model and
+equals each model run on its own, packet for packet (the same Philox streams),
+so their escape spectra agree exactly; the autotuner keeps a valid launch
+shape."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch_ctx(models, cap):
+    import paper_2001_11252_gb300 as rg
+    ctx = rg.Context(0)
+    w0 = models[0]
+    ctx.set_lines(w0.lines, w0.dust)
+    ph = w0.physics
+    ctx.set_physics(ph.recoil, ph.isotropic, ph.keep_direction, ph.x_gauss, cap, 0, ph.tau_stop, ph.seed)
+    ctx.load_batch(models, nbin=200)
+    return ctx
+
+
+def test_batch_equals_per_model_and_single_runs():
+    import paper_2001_11252_gb300 as rg
+    models = synth.batch_models(40, packet_scale=0.004)
+    cap = 20000
+    ctx = _batch_ctx(models, cap)
+    st_b = ctx.propagate_batch(rg.BATCH_PERSISTENT)
+    sp_b = ctx.get_batch_spectra()
+    st_p = ctx.propagate_batch(rg.BATCH_PER_MODEL)
+    sp_p = ctx.get_batch_spectra()
+    npk = sum(w.packets.n for w in models)
+    assert st_b["packets"] == npk == st_p["packets"]
+    for k in ("escaped", "absorbed", "capped", "nscatt_line", "ncross"):
+        assert st_b[k] == st_p[k], k
+    assert np.array_equal(sp_b, sp_p)
+    # the persistent launch is replayed from its captured graph: same again
+    st_b2 = ctx.propagate_batch(rg.BATCH_PERSISTENT)
+    assert np.array_equal(ctx.get_batch_spectra(), sp_b) and st_b2["nscatt_line"] == st_b["nscatt_line"]
+    # each model alone, through the single-model entry point
+    for m in (0, 7, 23, 39):
+        w = models[m]
+        one = rg.Context(0)
+        one.setup(w)
+        one.set_physics(w.physics.recoil, w.physics.isotropic, 0, w.physics.x_gauss, cap, 0, w.physics.tau_stop,
+                        w.physics.seed)
+        one.propagate(w.packets.pos, w.packets.dir, w.packets.nu, w.packets.ids, out={})
+        assert np.array_equal(one.get_tally(0), sp_b[m]), m
+        one.close()
+    assert sp_b.sum() == st_b["escaped"]
+
+
+def test_batch_autotune_keeps_results():
+    import paper_2001_11252_gb300 as rg
+    models = synth.batch_models(16, packet_scale=0.003, seed_offset=5)
+    ctx = _batch_ctx(models, 5000)
+    ref = ctx.propagate_batch(rg.BATCH_PERSISTENT)
+    sp = ctx.get_batch_spectra()
+    tune = ctx.autotune_batch(max_scatt=500)
+    block, per_sm, ms = tune["best"]
+    assert block in (64, 128) and per_sm >= 1 and ms > 0
+    assert len(tune["tried"]) >= 2
+    st = ctx.propagate_batch(rg.BATCH_PERSISTENT)
+    assert st["nscatt_line"] == ref["nscatt_line"]
+    assert np.array_equal(ctx.get_batch_spectra(), sp)
