@@ -96,8 +96,12 @@ class Tally(C.Structure):
     _fields_ = [
         ("spec", C.c_void_p), ("pspec", C.c_void_p), ("pimg", C.c_void_p), ("pcube", C.c_void_p),
         ("ncross", C.c_int64), ("nscatt_line", C.c_int64), ("nscatt_dust", C.c_int64),
-        ("npeel", C.c_int64),
+        ("npeel", C.c_int64), ("events", C.c_void_p), ("nev", C.c_int64), ("cap", C.c_int64),
     ]
+
+
+EVENT_DTYPE = np.dtype([("p", "<f8", 3), ("leaf", "<i8"), ("level", "<i8"), ("ijk", "<i8", 3), ("dir", "<i8"),
+                        ("w", "<f8"), ("nu", "<f8")])
 
 
 def lib():
@@ -133,11 +137,16 @@ def lib():
             L.ora_run.restype = C.c_int
             L.ora_run.argtypes = [C.POINTER(Cfg), i64, dp, dp, dp, C.POINTER(u64),
                                   C.POINTER(C.c_int32), C.POINTER(i64), dp, dp, dp, dp, C.POINTER(Tally)]
-            for f in ("ora_sizeof_cfg", "ora_sizeof_state", "ora_sizeof_tally"):
+            L.ora_peel_from_events.argtypes = [C.POINTER(Cfg), C.c_void_p, i64, C.POINTER(Tally)]
+            L.ora_adjoint_events.argtypes = [C.POINTER(Cfg), C.c_void_p, i64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.c_void_p]
+            L.ora_voigt_derivs.argtypes = [C.c_double, C.c_double, dp, dp, dp]
+            for f in ("ora_sizeof_cfg", "ora_sizeof_state", "ora_sizeof_tally", "ora_sizeof_event"):
                 getattr(L, f).restype = i64
             assert L.ora_sizeof_cfg() == C.sizeof(Cfg)
             assert L.ora_sizeof_state() == C.sizeof(State)
             assert L.ora_sizeof_tally() == C.sizeof(Tally)
+            assert L.ora_sizeof_event() == EVENT_DTYPE.itemsize
             _lib = L
     return _lib
 
@@ -212,7 +221,7 @@ class Oracle:
         ty.pcube = t["pcube"].ctypes.data if t["pcube"] is not None else None
         return ty, t
 
-    def _run_range(self, pk, lo, hi):
+    def _run_range(self, pk, lo, hi, record=0):
         n = hi - lo
         pos = np.ascontiguousarray(pk.pos[lo:hi], dtype=np.float64)
         dr = np.ascontiguousarray(pk.dir[lo:hi], dtype=np.float64)
@@ -221,6 +230,9 @@ class Oracle:
         out = {"status": np.zeros(n, np.int32), "nscatt": np.zeros(n, np.int64),
                "nu": np.zeros(n), "pos": np.zeros((n, 3)), "dir": np.zeros((n, 3)), "path": np.zeros(n)}
         ty, t = self._alloc_tally()
+        if record:
+            ev = np.zeros(record, dtype=EVENT_DTYPE)
+            ty.events, ty.cap = ev.ctypes.data, record
         lib().ora_run(C.byref(self.cfg), n, _dp(pos), _dp(dr), _dp(nu),
                       ids.ctypes.data_as(C.POINTER(C.c_uint64)),
                       out["status"].ctypes.data_as(C.POINTER(C.c_int32)),
@@ -228,26 +240,31 @@ class Oracle:
                       _dp(out["nu"]), _dp(out["pos"]), _dp(out["dir"]), _dp(out["path"]), C.byref(ty))
         t["ncross"], t["nscatt_line"], t["nscatt_dust"], t["npeel"] = (
             ty.ncross, ty.nscatt_line, ty.nscatt_dust, ty.npeel)
+        if record:
+            if ty.nev > record:
+                raise RuntimeError("event record overflow: %d > %d" % (ty.nev, record))
+            t["events"] = ev[: ty.nev]
         return out, t
 
-    def run(self, packets=None, lo=0, hi=None, threads=1, chunk=None):
-        """Propagate packets [lo, hi) of the workload (or of ``packets``)."""
+    def run(self, packets=None, lo=0, hi=None, threads=1, chunk=None, record_events=0):
+        """Propagate packets [lo, hi) of the workload (or of ``packets``);
+        record_events > 0 keeps up to that many peeling events per chunk."""
         pk = packets if packets is not None else self.wl.packets
         hi = pk.n if hi is None else hi
         if threads <= 1:
-            parts = [self._run_range(pk, lo, hi)]
+            parts = [self._run_range(pk, lo, hi, record_events)]
         else:
             chunk = chunk or max(1, (hi - lo + threads * 4 - 1) // (threads * 4))
             bounds = [(a, min(hi, a + chunk)) for a in range(lo, hi, chunk)]
             with ThreadPoolExecutor(threads) as ex:
-                parts = list(ex.map(lambda b: self._run_range(pk, *b), bounds))
+                parts = list(ex.map(lambda b: self._run_range(pk, *b, record_events), bounds))
         out = {k: np.concatenate([p[0][k] for p in parts]) for k in parts[0][0]}
         tal = {}
         for k in parts[0][1]:
             if parts[0][1][k] is None:
                 tal[k] = None
-            elif isinstance(parts[0][1][k], np.ndarray):
-                tal[k] = sum(p[1][k] for p in parts)
+            elif k == "events":
+                tal[k] = np.concatenate([p[1][k] for p in parts])
             else:
                 tal[k] = sum(p[1][k] for p in parts)
         c = self.cfg
@@ -257,6 +274,40 @@ class Oracle:
             if tal["pcube"] is not None:
                 tal["pcube"] = tal["pcube"].reshape(c.ndir, c.npix, c.npix, c.nbin)
         return out, tal
+
+    def _shape(self, tal):
+        c = self.cfg
+        if c.ndir:
+            tal["pspec"] = tal["pspec"].reshape(c.ndir, c.nbin)
+            tal["pimg"] = tal["pimg"].reshape(c.ndir, c.npix, c.npix) if c.npix else None
+            if tal["pcube"] is not None:
+                tal["pcube"] = tal["pcube"].reshape(c.ndir, c.npix, c.npix, c.nbin)
+        return tal
+
+    def peel_from_events(self, events):
+        """Peeled spectra / images / cubes of a fixed event record with the
+        current leaf fields (the forward map the adjoint differentiates)."""
+        ev = np.ascontiguousarray(events, dtype=EVENT_DTYPE)
+        ty, t = self._alloc_tally()
+        lib().ora_peel_from_events(C.byref(self.cfg), ev.ctypes.data, ev.size, C.byref(ty))
+        return self._shape(t)
+
+    def adjoint(self, events, g_cube=None, g_img=None, g_spec=None):
+        """dL/d(n_HI, vx, vy, vz, T, n_dust) per leaf, [6, nleaf], for
+        L = sum(g_cube*cube) + sum(g_img*img) + sum(g_spec*spec) over a fixed
+        event record (optical depths of the peeling rays differentiated)."""
+        ev = np.ascontiguousarray(events, dtype=EVENT_DTYPE)
+        arr = [None if g is None else np.ascontiguousarray(g, dtype=np.float64) for g in (g_cube, g_img, g_spec)]
+        grad = np.zeros((6, self.cfg.nleaf))
+        lib().ora_adjoint_events(C.byref(self.cfg), ev.ctypes.data, ev.size,
+                                 *[None if a is None else a.ctypes.data for a in arr], grad.ctypes.data)
+        return grad
+
+    def set_field(self, name, values):
+        """Replace one leaf field (float32 copy kept alive by the wrapper)."""
+        v = np.ascontiguousarray(values, dtype=np.float32)
+        self._keep[name] = v
+        setattr(self.cfg, name, v.ctypes.data)
 
     # -------------------------------------------------------------- pieces
     def locate(self, p, k=(1.0, 1.0, 1.0)):

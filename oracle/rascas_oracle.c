@@ -95,12 +95,23 @@ typedef struct {
     double path;                /* total path length (box units) */
 } ora_state;
 
+/* one peeling event: the fixed scattering record used by the adjoint */
+typedef struct {
+    double p[3];
+    int64_t leaf, level, ijk[3];
+    int64_t dir;      /* peeling direction index */
+    double w;         /* weight per steradian */
+    double nu;        /* external-frame frequency along the direction */
+} ora_peel_event;
+
 typedef struct {
     double *spec;   /* [nbin] escape spectrum, weight 1 per escaped packet */
     double *pspec;  /* [ndir*nbin] peeled spectra */
     double *pimg;   /* [ndir*npix*npix] peeled images */
     double *pcube;  /* [ndir*npix*npix*nbin] peeled cubes (optional) */
     int64_t ncross, nscatt_line, nscatt_dust, npeel;
+    ora_peel_event *events;   /* optional record of every peeling event */
+    int64_t nev, cap;
 } ora_tally;
 
 /* ------------------------------------------------------------------ */
@@ -532,32 +543,159 @@ ORA_API double ora_ray_tau(const ora_cfg *cf, const double p[3], const double k[
     return ray_tau(cf, p, k, nu_ext, leaf, level, ijk, tau_stop, cells, lens, cap, ncell);
 }
 
-static void peel_add(const ora_cfg *cf, ora_tally *ty, const ora_state *s, int d,
-                     double w, double nu_o_ext)
+/* detector bins of a peeling event: channel (or -1) and pixel (or -1) */
+static void peel_bins(const ora_cfg *cf, const double p[3], int d, double nu_o_ext, int64_t *ch, int64_t *px)
 {
     const double *ko = cf->dirs[d];
-    double tau = ray_tau(cf, s->p, ko, nu_o_ext, s->leaf, s->level, s->ijk, cf->tau_stop, 0, 0, 0, 0);
-    ty->npeel++;
-    if (tau > cf->tau_stop) return;
-    double f = w * exp(-tau);
     double t = (nu_o_ext - cf->nu_lo) / (cf->nu_hi - cf->nu_lo);
-    int64_t ch = (int64_t)floor(t * (double)cf->nbin);
-    int chok = ch >= 0 && ch < cf->nbin;
-    if (chok && ty->pspec) ty->pspec[d * cf->nbin + ch] += f;
+    int64_t c = (int64_t)floor(t * (double)cf->nbin);
+    *ch = (c >= 0 && c < cf->nbin) ? c : -1;
+    *px = -1;
     if (cf->npix > 0) {
         double eu[3], ev[3];
         onb(ko, eu, ev);
-        double r[3] = {s->p[0] - cf->img_c[0], s->p[1] - cf->img_c[1], s->p[2] - cf->img_c[2]};
+        double r[3] = {p[0] - cf->img_c[0], p[1] - cf->img_c[1], p[2] - cf->img_c[2]};
         double u = r[0] * eu[0] + r[1] * eu[1] + r[2] * eu[2];
         double v = r[0] * ev[0] + r[1] * ev[1] + r[2] * ev[2];
         int64_t iu = (int64_t)floor((u / cf->fov + 0.5) * (double)cf->npix);
         int64_t iv = (int64_t)floor((v / cf->fov + 0.5) * (double)cf->npix);
-        if (iu >= 0 && iu < cf->npix && iv >= 0 && iv < cf->npix) {
-            int64_t px = iv * cf->npix + iu;
-            if (ty->pimg) ty->pimg[d * cf->npix * cf->npix + px] += f;
-            if (chok && cf->cube && ty->pcube)
-                ty->pcube[(d * cf->npix * cf->npix + px) * cf->nbin + ch] += f;
-        }
+        if (iu >= 0 && iu < cf->npix && iv >= 0 && iv < cf->npix) *px = iv * cf->npix + iu;
+    }
+}
+
+/* add the contribution w exp(-tau) of one event to spectra, images, cubes */
+static void peel_deposit(const ora_cfg *cf, ora_tally *ty, const ora_peel_event *e)
+{
+    int d = (int)e->dir;
+    double tau = ray_tau(cf, e->p, cf->dirs[d], e->nu, e->leaf, e->level, e->ijk, cf->tau_stop, 0, 0, 0, 0);
+    if (tau > cf->tau_stop) return;
+    double f = e->w * exp(-tau);
+    int64_t ch, px;
+    peel_bins(cf, e->p, d, e->nu, &ch, &px);
+    if (ch >= 0 && ty->pspec) ty->pspec[d * cf->nbin + ch] += f;
+    if (px >= 0) {
+        if (ty->pimg) ty->pimg[d * cf->npix * cf->npix + px] += f;
+        if (ch >= 0 && cf->cube && ty->pcube) ty->pcube[(d * cf->npix * cf->npix + px) * cf->nbin + ch] += f;
+    }
+}
+
+static void peel_add(const ora_cfg *cf, ora_tally *ty, const ora_state *s, int d,
+                     double w, double nu_o_ext)
+{
+    ora_peel_event e;
+    memcpy(e.p, s->p, sizeof e.p);
+    e.leaf = s->leaf;
+    e.level = s->level;
+    memcpy(e.ijk, s->ijk, sizeof e.ijk);
+    e.dir = d;
+    e.w = w;
+    e.nu = nu_o_ext;
+    if (ty->events && ty->nev < ty->cap) ty->events[ty->nev] = e;
+    if (ty->events) ty->nev++;
+    ty->npeel++;
+    peel_deposit(cf, ty, &e);
+}
+
+ORA_API void ora_peel_from_events(const ora_cfg *cf, const ora_peel_event *ev, int64_t n, ora_tally *ty)
+{
+    for (int64_t i = 0; i < n; ++i) peel_deposit(cf, ty, ev + i);
+}
+
+/* ------------------------------------------------------------------ */
+/* adjoint of the peeled optical depths with the event record fixed     */
+/* ------------------------------------------------------------------ */
+
+/* Tasitsiomi H(a,x) with its partial derivatives in a and x */
+ORA_API void ora_voigt_derivs(double a, double x, double *H, double *dHda, double *dHdx)
+{
+    double s = x * x;
+    double e = exp(-s);
+    double Q = 0.0, dQds = 0.0;
+    double z = (s - 0.855) / (s + 3.42);
+    if (z > 0.0) {
+        double zp = 4.275 / ((s + 3.42) * (s + 3.42));
+        double P = 0.1117 + z * (4.421 + z * (-9.207 + 5.674 * z));
+        double Pp = 4.421 + z * (-18.414 + 17.022 * z);
+        double A1 = 1.0 + 21.0 / s;
+        double den = OPI * (s + 1.0);
+        Q = z * A1 * P / den;
+        dQds = (zp * A1 * P - z * (21.0 / (s * s)) * P + z * A1 * Pp * zp) / den - Q / (s + 1.0);
+    }
+    *H = sqrt(OPI) * a * Q + e;
+    *dHda = sqrt(OPI) * Q;
+    *dHdx = sqrt(OPI) * a * dQds * 2.0 * x - 2.0 * x * e;
+}
+
+/* d kappa / d theta of one leaf at external frequency nu along k, for theta =
+ * (n_HI, vx, vy, vz, T, n_dust) */
+static void opacity_grad(const ora_cfg *cf, int64_t leaf, double nu_ext, const double k[3], double dk[6])
+{
+    double b = beta_of(cf, leaf, k);
+    double nu_gas = nu_ext / (1.0 + b);
+    double T = (double)cf->T[leaf];
+    for (int j = 0; j < 6; ++j) dk[j] = 0.0;
+    for (int il = 0; il < cf->nline; ++il) {
+        ora_lineprop lp;
+        line_props(cf, il, leaf, nu_gas, &lp);
+        double H, dHa, dHx;
+        ora_voigt_derivs(lp.a, lp.x, &H, &dHa, &dHx);
+        double s0 = sqrt(OPI) * OE * OE * cf->line_f[il] / (OME * OC * lp.dnu);
+        double nX = line_density(cf, il, leaf);
+        if (cf->line_dens[il] != 1) dk[0] += cf->line_abund[il] * s0 * H;
+        /* x = (nu_ext/(1+beta) - nu0)/dnu:  dx/dv_j = -nu_gas k_j / (c (1+beta) dnu) */
+        double dxdv = -nu_gas / (OC * (1.0 + b) * lp.dnu);
+        for (int j = 0; j < 3; ++j) dk[1 + j] += nX * s0 * dHx * dxdv * k[j];
+        /* sigma0, a and x all scale as T^-1/2 */
+        dk[4] += nX * s0 * (-0.5 / T) * (H + lp.a * dHa + lp.x * dHx);
+    }
+    dk[5] = cf->dust_sigma;
+}
+
+/* second walk of a ray: grad[j][leaf] += scale * L * l * dkappa_j/dtheta */
+static void ray_grad(const ora_cfg *cf, const ora_peel_event *e, double scale, double *grad)
+{
+    const double *k = cf->dirs[e->dir];
+    double p[3] = {e->p[0], e->p[1], e->p[2]};
+    int64_t leaf = e->leaf, level = e->level, ijk[3] = {e->ijk[0], e->ijk[1], e->ijk[2]};
+    double inv[3];
+    inverse_dir(k, inv);
+    int64_t n = cf->nleaf;
+    for (long guard = 0; guard < 100000000L; ++guard) {
+        ora_state tmp;
+        memcpy(tmp.p, p, sizeof p);
+        memcpy(tmp.k, k, sizeof tmp.k);
+        tmp.level = level;
+        memcpy(tmp.ijk, ijk, sizeof ijk);
+        int axis;
+        double tf = face_distance(&tmp, inv, &axis);
+        double tb = border_distance(cf, p, k, inv);
+        double l = tb <= tf ? tb : tf;
+        double dk[6];
+        opacity_grad(cf, leaf, e->nu, k, dk);
+        for (int j = 0; j < 6; ++j) grad[j * n + leaf] += scale * cf->box_cm * l * dk[j];
+        if (tb <= tf) break;
+        if (cross_face(cf, p, k, axis, tf, &leaf, &level, ijk)) break;
+    }
+}
+
+/* gradient of L = sum g_cube*cube + g_img*img + g_spec*spec over the events:
+ * dL/dtheta_c = -sum_e G_e w_e exp(-tau_e) d tau_e / d theta_c */
+ORA_API void ora_adjoint_events(const ora_cfg *cf, const ora_peel_event *ev, int64_t n, const double *g_cube,
+                                const double *g_img, const double *g_spec, double *grad)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        const ora_peel_event *e = ev + i;
+        int d = (int)e->dir;
+        double tau = ray_tau(cf, e->p, cf->dirs[d], e->nu, e->leaf, e->level, e->ijk, cf->tau_stop, 0, 0, 0, 0);
+        if (tau > cf->tau_stop) continue;
+        int64_t ch, px;
+        peel_bins(cf, e->p, d, e->nu, &ch, &px);
+        double G = 0.0;
+        if (ch >= 0 && g_spec) G += g_spec[d * cf->nbin + ch];
+        if (px >= 0 && g_img) G += g_img[d * cf->npix * cf->npix + px];
+        if (px >= 0 && ch >= 0 && g_cube && cf->cube) G += g_cube[(d * cf->npix * cf->npix + px) * cf->nbin + ch];
+        if (G == 0.0) continue;
+        ray_grad(cf, e, -G * e->w * exp(-tau), grad);
     }
 }
 
@@ -794,3 +932,4 @@ ORA_API int ora_run(const ora_cfg *cf, int64_t n, const double *pos, const doubl
 ORA_API int64_t ora_sizeof_cfg(void) { return (int64_t)sizeof(ora_cfg); }
 ORA_API int64_t ora_sizeof_state(void) { return (int64_t)sizeof(ora_state); }
 ORA_API int64_t ora_sizeof_tally(void) { return (int64_t)sizeof(ora_tally); }
+ORA_API int64_t ora_sizeof_event(void) { return (int64_t)sizeof(ora_peel_event); }
