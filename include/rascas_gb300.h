@@ -240,6 +240,30 @@ int rascas_eval_voigt(rascas_ctx *ctx, int64_t n, const float *a, const double *
 int rascas_sample_upar(rascas_ctx *ctx, int64_t n, const double *x, const float *a,
                        const uint64_t *id, float *u, int32_t *ndraw, int mem);
 
+/* ---- adjoint (gradients of the peeled tallies) --------------------------- */
+
+/* Replace the leaf fields of the loaded octree (same tree, same leaf order;
+ * arrays of nleaf floats per `mem`, n_metal may be NULL).  The domain flags
+ * are kept. */
+int rascas_update_fields(rascas_ctx *ctx, const float *n_HI, const float *vx, const float *vy, const float *vz,
+                         const float *T, const float *n_dust, const float *n_metal, int mem);
+
+/* Gradient of L = sum(g_cube * cube) + sum(g_img * image) + sum(g_spec *
+ * spectrum) with respect to each leaf's n_HI, vx, vy, vz, T and n_dust, with
+ * the scattering record held fixed: the positions, directions, external
+ * frequencies and weights of every peeling event of the given packets are
+ * those of rascas_propagate on the same packets (the run is replayed: same
+ * streams, same fields), and only the optical depths of the peeling rays
+ * (Sect. 3.1 opacities along each ray, Sect. 5.1 peeling) are differentiated:
+ *     dL/dtheta_c = - sum_events G_e w_e exp(-tau_e) L l_(e,c) dkappa_c/dtheta_c.
+ * Each ray is walked twice (tau first, then the gradients), so nothing per ray
+ * is stored.  g_* follow the detector shapes of rascas_get_tally (any may be
+ * NULL, not all); grad receives [6][nleaf] floats (n_HI, vx, vy, vz, T,
+ * n_dust), zeroed first.  Not in the paper: the adjoint is an addition.
+ * All pointers follow `mem`; tallies are left untouched. */
+int rascas_peel_adjoint(rascas_ctx *ctx, const rascas_packets_in *in, int64_t n, const float *g_cube,
+                        const float *g_img, const float *g_spec, float *grad, int mem);
+
 /* ---- batches of independent models --------------------------------------- */
 
 /* One independent model of a batch: its own octree and leaf fields, domain,

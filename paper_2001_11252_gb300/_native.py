@@ -127,6 +127,8 @@ def lib():
             "rascas_trace": [vp, C.POINTER(PacketsIn), i64, i32, vp, vp, C.c_int],
             "rascas_eval_voigt": [vp, i64, vp, vp, vp, C.c_int],
             "rascas_sample_upar": [vp, i64, vp, vp, vp, vp, vp, C.c_int],
+            "rascas_update_fields": [vp, vp, vp, vp, vp, vp, vp, vp, C.c_int],
+            "rascas_peel_adjoint": [vp, C.POINTER(PacketsIn), i64, vp, vp, vp, vp, C.c_int],
             "rascas_load_batch": [vp, C.POINTER(Model), i32, i32, C.c_int],
             "rascas_propagate_batch": [vp, i32, C.POINTER(Stats)],
             "rascas_get_batch_spectra": [vp, vp, C.c_size_t, C.c_int],
@@ -218,6 +220,7 @@ class Context:
         t = Octree()
         t.noct = int(arrs[0].shape[0]) // 8
         t.nleaf = int(arrs[1].shape[0])
+        self.nleaf = t.nleaf
         t.son, t.n_HI, t.vx, t.vy, t.vz, t.T, t.n_dust, t.n_metal = [_ptr(a) for a in arrs]
         t.box_cm = float(box_cm)
         self._ck(self._L.rascas_load_octree(self._h, C.byref(t), mem), "load_octree")
@@ -386,6 +389,35 @@ class Context:
         self._ck(self._L.rascas_sample_upar(self._h, n, _ptr(x), _ptr(a), _ptr(ids), _ptr(u), _ptr(nd), mem),
                  "sample_upar")
         return u, nd
+
+    # ------------------------------------------------------------ adjoint
+    def update_fields(self, n_HI, vx, vy, vz, T, n_dust, n_metal=None):
+        arrs = [_c(a, np.float32) for a in (n_HI, vx, vy, vz, T, n_dust, n_metal)]
+        mem = _mem(*arrs)
+        self._stream_sync_torch(mem)
+        self._ck(self._L.rascas_update_fields(self._h, *[_ptr(a) for a in arrs], mem), "update_fields")
+
+    def peel_adjoint(self, pos, dir, nu, ids, g_cube=None, g_img=None, g_spec=None, nleaf=None):
+        """[6, nleaf] gradient (n_HI, vx, vy, vz, T, n_dust) of
+        sum(g_cube*cube) + sum(g_img*img) + sum(g_spec*spec) with the
+        scattering record of these packets held fixed."""
+        pos, dir, nu = _c(pos, np.float64), _c(dir, np.float64), _c(nu, np.float64)
+        ids = _c(ids, np.uint64)
+        gs = [_c(g, np.float32) for g in (g_cube, g_img, g_spec)]
+        mem = _mem(pos, dir, nu, ids, *gs)
+        n = int(nu.shape[0])
+        if nleaf is None:
+            nleaf = self.nleaf
+        if mem == DEVICE:
+            import torch
+            grad = torch.zeros((6, nleaf), dtype=torch.float32, device=nu.device)
+        else:
+            grad = np.zeros((6, nleaf), np.float32)
+        pin = PacketsIn(_ptr(pos), _ptr(dir), _ptr(nu), _ptr(ids))
+        self._stream_sync_torch(mem)
+        self._ck(self._L.rascas_peel_adjoint(self._h, C.byref(pin), n, *[_ptr(g) for g in gs], _ptr(grad), mem),
+                 "peel_adjoint")
+        return grad
 
     # ------------------------------------------------------------ batches
     def load_batch(self, workloads, nbin):

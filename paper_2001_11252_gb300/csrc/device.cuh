@@ -118,6 +118,28 @@ __device__ __forceinline__ float voigt_h2(float a, float xh, float xl) {
     return kSqrtPiF * q + e;
 }
 
+// H with its partial derivatives in a and x (the derivative of this
+// approximation, which is what the adjoint differentiates)
+__device__ __forceinline__ void voigt_derivs(float a, float x, float& H, float& Ha, float& Hx) {
+    float s = x * x;
+    float e = expf(-s);
+    float Q = 0.0f, dQ = 0.0f;
+    float z = (s - 0.855f) / (s + 3.42f);
+    if (z > 0.0f) {
+        float w = s + 3.42f;
+        float zp = 4.275f / (w * w);
+        float Pz = 0.1117f + z * (4.421f + z * (-9.207f + 5.674f * z));
+        float Pp = 4.421f + z * (-18.414f + 17.022f * z);
+        float A1 = 1.0f + 21.0f / s;
+        float inv = 1.0f / (kPiF * (s + 1.0f));
+        Q = z * A1 * Pz * inv;
+        dQ = (zp * A1 * Pz - z * (21.0f / (s * s)) * Pz + z * A1 * Pp * zp) * inv - Q / (s + 1.0f);
+    }
+    H = kSqrtPiF * a * Q + e;
+    Ha = kSqrtPiF * Q;
+    Hx = 2.0f * x * (kSqrtPiF * a * dQ - e);
+}
+
 // ---------------------------------------------------------------------------
 // u_par (Sect. 3.3.3): rejection method of Zheng & Miralda-Escude (2002) with
 // the fitted separation u0(x, log10 a), clamped at 0; |x| >= x_gauss: Gaussian

@@ -71,7 +71,7 @@ struct rascas_ctx {
     rascas_detector det{};
     Params P{};
     DevBuf d_spec, d_pspec, d_pimg, d_pcube, d_counters, d_params;
-    DevBuf stage_in, stage_out, stage_aux;
+    DevBuf stage_in, stage_out, stage_aux, stage_adj;
     // batch of independent models
     struct Batch {
         int nmodels = 0, nbin = 0, nline_at_load = 0;
@@ -317,7 +317,7 @@ int rascas_destroy(rascas_ctx* ctx) {
     cudaSetDevice(ctx->device);
     for (DevBuf* b : {&ctx->d_rec, &ctx->d_son, &ctx->d_nbr, &ctx->d_top, &ctx->d_spec, &ctx->d_pspec,
                       &ctx->d_pimg, &ctx->d_pcube, &ctx->d_counters, &ctx->d_params, &ctx->stage_in,
-                      &ctx->stage_out, &ctx->stage_aux})
+                      &ctx->stage_out, &ctx->stage_aux, &ctx->stage_adj})
         b->release();
     auto& B = ctx->batch;
     for (DevBuf* b : {&B.d_rec, &B.d_son, &B.d_nbr, &B.d_top, &B.d_geo, &B.d_first, &B.d_pos, &B.d_dir, &B.d_nu,
@@ -549,13 +549,13 @@ int persistent_grid(rascas_ctx* ctx, bool peel) {
 
 int run_propagate(rascas_ctx* ctx, const rascas_packets_in* in, int64_t n, const rascas_packets_out* out,
                   int mem, rascas_run_stats* stats, rascas_event* events, int32_t* nevents, int32_t max_events,
-                  bool tallies) {
+                  bool tallies, const Params* adj = nullptr) {
     if (!ctx || !in || n < 0 || (mem != RASCAS_HOST && mem != RASCAS_DEVICE)) return fail(ctx, RASCAS_E_ARG, "bad arguments");
     if (n > 0 && (!in->pos || !in->dir || !in->nu || !in->id)) return fail(ctx, RASCAS_E_ARG, "packets: null array");
     int r = check_ready(ctx);
     if (r) return r;
     CK(cudaSetDevice(ctx->device));
-    Params P = ctx->P;
+    Params P = adj ? *adj : ctx->P;
     if (!tallies || !ctx->has_det) {
         P.g.spec = nullptr;
         P.ndir = 0;
@@ -1130,6 +1130,74 @@ int rascas_autotune_batch(rascas_ctx* ctx, int64_t max_scatt, rascas_tune* best,
     B.blocks_per_sm = bt.blocks_per_sm;
     if (best) *best = bt;
     if (ntried) *ntried = nt;
+    return RASCAS_OK;
+}
+
+int rascas_update_fields(rascas_ctx* ctx, const float* n_HI, const float* vx, const float* vy, const float* vz,
+                         const float* T, const float* n_dust, const float* n_metal, int mem) {
+    if (!ctx || !n_HI || !vx || !vy || !vz || !T || !n_dust) return fail(ctx, RASCAS_E_ARG, "update_fields: null array");
+    if (!ctx->has_mesh) return fail(ctx, RASCAS_E_STATE, "update_fields: no octree loaded");
+    CK(cudaSetDevice(ctx->device));
+    const size_t N = (size_t)ctx->mesh.nleaf;
+    if (mem == RASCAS_DEVICE) {
+        CK(rg::launch_pack_fields((long long)N, n_HI, vx, vy, vz, T, n_dust, n_metal, (float4*)ctx->d_rec.p,
+                                  ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        // keep the host copy of the records in step (used when the domain changes)
+        CK(cudaMemcpy(ctx->mesh.rec.data(), ctx->d_rec.p, N * 32, cudaMemcpyDeviceToHost));
+    } else {
+        const float* src[7] = {n_HI, vx, vy, vz, T, n_dust, n_metal};
+        for (size_t i = 0; i < N; ++i)
+            for (int j = 0; j < 7; ++j) ctx->mesh.rec[8 * i + j] = src[j] ? src[j][i] : 0.0f;
+        CK(cudaMemcpy(ctx->d_rec.p, ctx->mesh.rec.data(), N * 32, cudaMemcpyHostToDevice));
+    }
+    if (n_metal) ctx->mesh.has_metal = true;
+    return RASCAS_OK;
+}
+
+int rascas_peel_adjoint(rascas_ctx* ctx, const rascas_packets_in* in, int64_t n, const float* g_cube,
+                        const float* g_img, const float* g_spec, float* grad, int mem) {
+    if (!ctx || !in || n < 0 || !grad || (!g_cube && !g_img && !g_spec))
+        return fail(ctx, RASCAS_E_ARG, "peel_adjoint: bad arguments");
+    if (!ctx->has_det || ctx->det.ndir < 1) return fail(ctx, RASCAS_E_STATE, "peel_adjoint: no peeling directions");
+    if (g_cube && !ctx->P.cube) return fail(ctx, RASCAS_E_STATE, "peel_adjoint: the detector accumulates no cubes");
+    int r = check_ready(ctx);
+    if (r) return r;
+    CK(cudaSetDevice(ctx->device));
+    const rascas_detector& d = ctx->det;
+    const size_t npix2 = (size_t)d.npix * d.npix;
+    const size_t n_cube = g_cube ? (size_t)d.ndir * npix2 * d.nbin : 0;
+    const size_t n_img = g_img ? (size_t)d.ndir * npix2 : 0;
+    const size_t n_spec = g_spec ? (size_t)d.ndir * d.nbin : 0;
+    const size_t n_grad = 6 * (size_t)ctx->mesh.nleaf;
+    cudaStream_t st = ctx->stream;
+    Params P = ctx->P;
+    float* dgrad = grad;
+    if (mem == RASCAS_HOST) {
+        CK(ctx->stage_adj.ensure((n_cube + n_img + n_spec + n_grad) * 4 + 256));
+        float* b = (float*)ctx->stage_adj.p;
+        float* dc = g_cube ? b : nullptr; b += n_cube;
+        float* di = g_img ? b : nullptr; b += n_img;
+        float* ds = g_spec ? b : nullptr; b += n_spec;
+        dgrad = b;
+        if (dc) CK(cudaMemcpyAsync(dc, g_cube, n_cube * 4, cudaMemcpyHostToDevice, st));
+        if (di) CK(cudaMemcpyAsync(di, g_img, n_img * 4, cudaMemcpyHostToDevice, st));
+        if (ds) CK(cudaMemcpyAsync(ds, g_spec, n_spec * 4, cudaMemcpyHostToDevice, st));
+        P.adj_g_cube = dc; P.adj_g_img = di; P.adj_g_spec = ds;
+    } else {
+        P.adj_g_cube = g_cube; P.adj_g_img = g_img; P.adj_g_spec = g_spec;
+    }
+    P.adj_grad = dgrad;
+    P.g.spec = nullptr;   // the replay leaves the escape spectrum alone
+    CK(cudaMemsetAsync(dgrad, 0, n_grad * 4, st));
+    // replay of the propagation (same packets, same streams, hence the same
+    // scattering and peeling record) with peeling accumulating gradients
+    r = run_propagate(ctx, in, n, nullptr, mem, nullptr, nullptr, nullptr, 0, true, &P);
+    if (r) return r;
+    if (mem == RASCAS_HOST) {
+        CK(cudaMemcpyAsync(grad, dgrad, n_grad * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
     return RASCAS_OK;
 }
 

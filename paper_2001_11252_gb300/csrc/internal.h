@@ -94,6 +94,12 @@ struct Params {
     float* pspec;
     float* pimg;
     float* pcube;
+    // adjoint of the peeled optical depths (peeling accumulates gradients
+    // instead of tallies when adj_grad is set)
+    const float* adj_g_cube;   // dL/dcube [ndir][npix][npix][nbin] (or null)
+    const float* adj_g_img;    // dL/dimage [ndir][npix][npix] (or null)
+    const float* adj_g_spec;   // dL/dspectrum [ndir][nbin] (or null)
+    float* adj_grad;           // [6][nleaf]: n_HI, vx, vy, vz, T, n_dust
     // run scratch
     unsigned long long* counters;  // [CNT_N]
     unsigned long long* head;      // work-queue head
@@ -135,6 +141,8 @@ cudaError_t launch_propagate(const Params& P, const PacketsIn& in, const Packets
 cudaError_t launch_ray_tau(const Params& P, long long n, const double* pos, const double* dir,
                            const double* nu, double* tau, int32_t* cells, double* lens, int cap,
                            int32_t* ncell, cudaStream_t st);
+cudaError_t launch_pack_fields(long long n, const float* nh, const float* vx, const float* vy, const float* vz,
+                               const float* T, const float* nd, const float* nm, float4* rec, cudaStream_t st);
 cudaError_t launch_eval_voigt(long long n, const float* a, const double* x, float* H, cudaStream_t st);
 cudaError_t launch_sample_upar(const Params& P, long long n, const double* x, const float* a,
                                const uint64_t* id, float* u, int32_t* ndraw, cudaStream_t st);

@@ -117,6 +117,69 @@ __device__ __noinline__ double ray_walk(const Params* __restrict__ G, double p0,
     return tau;
 }
 
+// second walk of a peeling ray for the adjoint: for every leaf crossed,
+// grad[j][leaf] += scale * L * l * d kappa / d theta_j (Sect. 3.1 opacities
+// differentiated in n_HI, v, T and n_dust)
+template <int NL>
+__device__ __noinline__ void ray_grad(const Params* __restrict__ G, double p0, double p1, double p2, Where w,
+                                      double k0, double k1, double k2, double nu_ext, float scale) {
+    const Params& P = *G;
+    double p[3] = {p0, p1, p2};
+    const double k[3] = {k0, k1, k2};
+    const double inv[3] = {k0 != 0.0 ? __drcp_rn(k0) : 0.0, k1 != 0.0 ? __drcp_rn(k1) : 0.0,
+                           k2 != 0.0 ? __drcp_rn(k2) : 0.0};
+    const float kf[3] = {(float)k0, (float)k1, (float)k2};
+    const long long nleaf = P.g.nleaf;
+    uint32_t sl = 0, nl = 0;
+    int zero_run = 0;
+    for (int guard = 0; guard < (1 << 26); ++guard) {
+        CellCache<NL> cc;
+        load_cell<NL>(P, P.g, w.leaf, cc);
+        double b = beta_of(cc, k);
+        double nu = to_gas(nu_ext, b);
+        int axis;
+        double tf = face_distance(p, k, inv, w, axis);
+        double tb = (cc.flags & kFlagBorder) ? border_distance(P.g, p, k, inv) : kInf;
+        bool border = tb <= tf;
+        double l = border ? tb : tf;
+        float dk[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, P.dust_sigma};
+        float4 r0 = __ldg(P.g.rec + 2 * w.leaf);
+        float4 r1 = __ldg(P.g.rec + 2 * w.leaf + 1);
+        const float Tm = fmaxf(r1.x, 1e-30f);
+        const float rs = rsqrtf(Tm);
+#pragma unroll
+        for (int i = 0; i < NL; ++i) {
+            const LineDev& L = P.line[i];
+            float x = (float)((nu - L.nu0) * cc.invdnu[i]);
+            float H, Ha, Hx;
+            voigt_derivs(cc.a[i], x, H, Ha, Hx);
+            float s0 = L.sig_pref * rs;
+            float nX = (L.dens == 1 ? r1.z : r0.x) * L.abund;
+            if (L.dens != 1) dk[0] += L.abund * s0 * H;
+            // x = (nu_ext / (1 + beta) - nu0) / dnu:  dx/dv_j = -(nu_gas / dnu) k_j / (c (1 + beta))
+            float dxdv = -(float)(nu * cc.invdnu[i]) / (float)(kC * (1.0 + b));
+            float t = nX * s0 * Hx * dxdv;
+            dk[1] += t * kf[0];
+            dk[2] += t * kf[1];
+            dk[3] += t * kf[2];
+            // sigma0, a and x all scale as T^(-1/2)
+            dk[4] += nX * s0 * (-0.5f / Tm) * (H + cc.a[i] * Ha + x * Hx);
+        }
+        const float f = scale * (float)(P.g.box_cm * l);
+        if (f != 0.0f) {
+#pragma unroll
+            for (int j = 0; j < 6; ++j)
+                if (dk[j] != 0.0f) atomicAdd(P.adj_grad + j * nleaf + w.leaf, f * dk[j]);
+        }
+        if (border) break;
+        zero_run = tf > 0.0 ? 0 : zero_run + 1;
+        if (zero_run > 64) break;
+        move_to_face(p, k, axis, tf, w);
+        wrap_periodic(P.g, p, k);
+        if (!next_leaf(P.g, p, k, axis, w, sl, nl)) break;
+    }
+}
+
 // one peeled contribution towards direction d (weight w per sr, gas-frame
 // frequency nu_o_gas of the event's leaf) into spectra, images and cubes
 template <int NL>
@@ -136,19 +199,31 @@ __device__ __noinline__ void peel_add(const Params* __restrict__ G, double p0, d
     double fb = floor(t * (double)nbin);
     bool chok = fb >= 0.0 && fb < (double)nbin;
     int ch = chok ? (int)fb : 0;
-    if (chok) atomicAdd(P.pspec + d * nbin + ch, f);
+    long long px = -1;
+    const long long npix2 = (long long)P.npix * P.npix;
     if (P.npix > 0) {
         double r0 = p0 - P.img_c[0], r1 = p1 - P.img_c[1], r2 = p2 - P.img_c[2];
         double u = r0 * P.eu[d][0] + r1 * P.eu[d][1] + r2 * P.eu[d][2];
         double v = r0 * P.ev[d][0] + r1 * P.ev[d][1] + r2 * P.ev[d][2];
         double fu = floor((u * P.inv_fov + 0.5) * (double)P.npix);
         double fv = floor((v * P.inv_fov + 0.5) * (double)P.npix);
-        if (fu >= 0.0 && fu < (double)P.npix && fv >= 0.0 && fv < (double)P.npix) {
-            long long px = (long long)fv * P.npix + (long long)fu;
-            long long npix2 = (long long)P.npix * P.npix;
-            atomicAdd(P.pimg + d * npix2 + px, f);
-            if (chok && P.cube) atomicAdd(P.pcube + (d * npix2 + px) * nbin + ch, f);
-        }
+        if (fu >= 0.0 && fu < (double)P.npix && fv >= 0.0 && fv < (double)P.npix)
+            px = (long long)fv * P.npix + (long long)fu;
+    }
+    if (P.adj_grad != nullptr) {
+        // adjoint: dL/dtheta_c = -G w exp(-tau) d tau / d theta_c, with G the
+        // gradient of the loss at this event's channel and pixel
+        float Gs = 0.0f;
+        if (chok && P.adj_g_spec) Gs += __ldg(P.adj_g_spec + d * nbin + ch);
+        if (px >= 0 && P.adj_g_img) Gs += __ldg(P.adj_g_img + d * npix2 + px);
+        if (px >= 0 && chok && P.cube && P.adj_g_cube) Gs += __ldg(P.adj_g_cube + (d * npix2 + px) * nbin + ch);
+        if (Gs != 0.0f && f != 0.0f) ray_grad<NL>(G, p0, p1, p2, w, k0, k1, k2, nu_ext, -Gs * f);
+        return;
+    }
+    if (chok) atomicAdd(P.pspec + d * nbin + ch, f);
+    if (px >= 0) {
+        atomicAdd(P.pimg + d * npix2 + px, f);
+        if (chok && P.cube) atomicAdd(P.pcube + (d * npix2 + px) * nbin + ch, f);
     }
 }
 
@@ -632,6 +707,22 @@ __global__ void k_ray_tau(const Params* __restrict__ G, long long n, const doubl
     tau[i] = ray_walk<NL>(G, p[0], p[1], p[2], w, k[0], k[1], k[2], nu[i], kInf, nullptr,
                           cells ? cells + i * cap : nullptr, lens ? lens + i * cap : nullptr, cap,
                           ncell ? ncell + i : nullptr);
+}
+
+__global__ void k_pack_fields(long long n, const float* nh, const float* vx, const float* vy, const float* vz,
+                              const float* T, const float* nd, const float* nm, float4* rec) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float flags = rec[2 * i + 1].w;   // the domain flags stay
+    rec[2 * i] = make_float4(nh[i], vx[i], vy[i], vz[i]);
+    rec[2 * i + 1] = make_float4(T[i], nd[i], nm ? nm[i] : 0.0f, flags);
+}
+
+cudaError_t launch_pack_fields(long long n, const float* nh, const float* vx, const float* vy, const float* vz,
+                               const float* T, const float* nd, const float* nm, float4* rec, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_pack_fields<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, nh, vx, vy, vz, T, nd, nm, rec);
+    return cudaGetLastError();
 }
 
 __global__ void k_eval_voigt(long long n, const float* a, const double* x, float* H) {
