@@ -33,8 +33,10 @@ def test_gpu_adjoint_matches_oracle():
     ctx.propagate(pk.pos, pk.dir, pk.nu, pk.ids, out=out)
     o = oracle.Oracle(wl)
     r, _ = o.run(threads=8)
+    # coupled histories: same fate, same number of scatterings, same final
+    # frequency to FP32-sampling accuracy (1e-8 relative ~ 1e-3 Doppler widths)
     same = (out["status"] == r["status"]) & (out["nscatt"] == r["nscatt"]) & \
-        (np.abs(out["nu"] - r["nu"]) <= 1e-12 * r["nu"])
+        (np.abs(out["nu"] - r["nu"]) <= 1e-8 * r["nu"])
     assert same.mean() > 0.8, same.mean()
     sel = np.nonzero(same)[0]
     sub = _subset(pk, sel)
@@ -75,5 +77,7 @@ def test_autograd_function():
     direct = ctx.peel_adjoint(*packets, g_cube=w.float())
     for j, f in enumerate(fields):
         assert f.grad is not None
-        assert torch.equal(f.grad, direct[j])
+        # same replay; float atomics may add in another order
+        scale = float(direct[j].abs().max()) + 1e-30
+        assert float((f.grad - direct[j]).abs().max()) <= 1e-5 * scale
     assert float(fields[0].grad.abs().sum()) > 0
