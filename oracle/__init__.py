@@ -141,6 +141,7 @@ def lib():
             L.ora_adjoint_events.argtypes = [C.POINTER(Cfg), C.c_void_p, i64, C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.c_void_p]
             L.ora_voigt_derivs.argtypes = [C.c_double, C.c_double, dp, dp, dp]
+            L.ora_emission.argtypes = [C.POINTER(Cfg), C.POINTER(State), C.POINTER(Tally)]
             for f in ("ora_sizeof_cfg", "ora_sizeof_state", "ora_sizeof_tally", "ora_sizeof_event"):
                 getattr(L, f).restype = i64
             assert L.ora_sizeof_cfg() == C.sizeof(Cfg)
@@ -347,10 +348,24 @@ class Oracle:
         lib().ora_init_state(C.byref(self.cfg), C.byref(s), _dp(p), _dp(k), float(nu), int(pid))
         return s
 
-    def event(self, s):
+    def event(self, s, record_events=0):
+        """Advance state s by one event; optionally return its peeling events."""
         ty, t = self._alloc_tally()
+        if record_events:
+            ev = np.zeros(record_events, dtype=EVENT_DTYPE)
+            ty.events, ty.cap = ev.ctypes.data, record_events
         r = lib().ora_event(C.byref(self.cfg), C.byref(s), C.byref(ty))
+        if record_events:
+            t["events"] = ev[: min(ty.nev, record_events)]
         return r, t
+
+    def emission_events(self, s, cap=64):
+        """Peeling events of the emission of a packet in state s."""
+        ty, t = self._alloc_tally()
+        ev = np.zeros(cap, dtype=EVENT_DTYPE)
+        ty.events, ty.cap = ev.ctypes.data, cap
+        lib().ora_emission(C.byref(self.cfg), C.byref(s), C.byref(ty))
+        return ev[: min(ty.nev, cap)]
 
 
 # ---------------------------------------------------------------- helpers

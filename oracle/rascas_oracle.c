@@ -713,6 +713,13 @@ static void peel_emission(const ora_cfg *cf, ora_tally *ty, const ora_state *s, 
     }
 }
 
+/* peeling of the emission of a packet in state s (its first event) */
+ORA_API void ora_emission(const ora_cfg *cf, const ora_state *s, ora_tally *ty)
+{
+    if (s->status != ORA_ACTIVE || cf->ndir < 1) return;
+    peel_emission(cf, ty, s, s->nu / (1.0 + beta_of(cf, s->leaf, s->k)));
+}
+
 static void scatter_dust(const ora_cfg *cf, ora_state *s, ora_tally *ty, double nu_gas)
 {
     double r_alb = u23(cf, s);

@@ -23,35 +23,71 @@ def _subset(pk, sel):
     return synth.Packets(pk.pos[sel], pk.dir[sel], pk.nu[sel], pk.ids[sel])
 
 
+def _state_from(o, rec, pid):
+    st = oracle.State()
+    st.p[:] = list(rec["p"]); st.k[:] = list(rec["k"]); st.nu = float(rec["nu"])
+    st.leaf, st.level = int(rec["leaf"]), int(rec["level"])
+    st.ijk[:] = [int(v) for v in rec["ijk"]]
+    st.pid = int(pid); st.ndraw = int(rec["ndraw"])
+    st.nscatt, st.nsteps, st.status = int(rec["nscatt"]), int(rec["nsteps"]), int(rec["status"])
+    return st
+
+
 def test_gpu_adjoint_matches_oracle():
+    """The GPU adjoint replays the GPU's own scattering record; the oracle
+    rebuilds that record step by step from the GPU trace (each event replayed
+    from the GPU's state, as in the per-step parity tests) and differentiates
+    it in FP64.  Whole histories are not compared: FP32 velocity sampling
+    makes the continuous state drift by ~1e-5 Doppler widths over thousands of
+    scatterings while the discrete history stays the same."""
     import paper_2001_11252_gb300 as rg
-    wl = _workload()
+    wl = _workload(200)
     ctx = rg.Context(0)
     ctx.setup(wl)
-    pk = wl.packets
-    out = {"status": np.zeros(pk.n, np.int32), "nscatt": np.zeros(pk.n, np.int64), "nu": np.zeros(pk.n)}
-    ctx.propagate(pk.pos, pk.dir, pk.nu, pk.ids, out=out)
     o = oracle.Oracle(wl)
-    r, _ = o.run(threads=8)
-    # coupled histories: same fate, same number of scatterings, same final
-    # frequency to FP32-sampling accuracy (1e-8 relative ~ 1e-3 Doppler widths)
-    same = (out["status"] == r["status"]) & (out["nscatt"] == r["nscatt"]) & \
-        (np.abs(out["nu"] - r["nu"]) <= 1e-8 * r["nu"])
-    assert same.mean() > 0.8, same.mean()
-    sel = np.nonzero(same)[0]
-    sub = _subset(pk, sel)
+    pk = wl.packets
+    cap = 3000
+    ev, cnt = ctx.trace(pk.pos, pk.dir, pk.nu, pk.ids, cap)
+    chosen, events = [], []
+    for i in range(pk.n):
+        n = int(cnt[i])
+        if n >= cap or ev[i, n - 1]["status"] == 0:
+            continue
+        recs = [o.emission_events(_state_from(o, ev[i, 0], pk.ids[i]))]
+        ok = True
+        for j in range(n - 1):
+            st = _state_from(o, ev[i, j], pk.ids[i])
+            _, t = o.event(st, record_events=64)
+            b = ev[i, j + 1]
+            if st.ndraw != b["ndraw"] or st.status != b["status"] or st.leaf != b["leaf"]:
+                ok = False
+                break
+            recs.append(t["events"])
+        if ok:
+            chosen.append(i)
+            events.append(np.concatenate(recs))
+    assert len(chosen) > 0.8 * pk.n, len(chosen)
+    sub = _subset(pk, np.array(chosen))
+    events = np.concatenate(events)
     rng = np.random.default_rng(11)
-    shape = (3, 8, 8, 24)
-    g = rng.normal(size=shape).astype(np.float32)
-    grad_gpu = ctx.peel_adjoint(sub.pos, sub.dir, sub.nu, sub.ids, g_cube=g)
-    _, tal = o.run(packets=sub, threads=8, record_events=2_000_000)
-    grad_ora = o.adjoint(tal["events"], g_cube=g.astype(np.float64))
-    for j, name in enumerate(FIELDS):
-        ref = grad_ora[j]
-        floor = 1e-4 * np.abs(ref).max() + 1e-300
-        rel = np.abs(grad_gpu[j] - ref) / (np.abs(ref) + floor)
-        print(name, "max rel", rel.max(), "max |grad|", np.abs(ref).max())
-        assert rel.max() < 2e-4, (name, rel.max())
+    gs = [np.ones((3, 8, 8, 24), np.float32), rng.normal(size=(3, 8, 8, 24)).astype(np.float32)]
+    for k, g in enumerate(gs):
+        grad_gpu = ctx.peel_adjoint(sub.pos, sub.dir, sub.nu, sub.ids, g_cube=g)
+        grad_ora = o.adjoint(events, g_cube=g.astype(np.float64))
+        for j, name in enumerate(FIELDS):
+            ref = grad_ora[j]
+            if k == 0:
+                # uniform weights: every cell to FP32 accuracy
+                floor = 1e-4 * np.abs(ref).max() + 1e-300
+                rel = np.abs(grad_gpu[j] - ref) / (np.abs(ref) + floor)
+                print(name, "uniform G: max rel", rel.max())
+                assert rel.max() < 2e-4, (name, rel.max())
+            else:
+                # random per-bin weights: an event within FP32 rounding of a
+                # pixel or channel edge may be binned on the other side
+                err = np.linalg.norm(grad_gpu[j] - ref) / (np.linalg.norm(ref) + 1e-300)
+                print(name, "random G: relative L2", err)
+                assert err < 2e-3, (name, err)
 
 
 def test_autograd_function():
