@@ -56,6 +56,10 @@ def parse():
                     help="packets per batch model: log-uniform [1e3, 1e5] times this")
     ap.add_argument("--batch-cap", type=int, default=20000,
                     help="scatterings per packet cap in the batch comparison")
+    ap.add_argument("--galaxy", type=int, default=1, help="run the synthetic-galaxy section (1) or not (0)")
+    ap.add_argument("--galaxy-rays", type=int, default=1 << 20)
+    ap.add_argument("--galaxy-packets", type=int, default=1 << 15)
+    ap.add_argument("--galaxy-cap", type=int, default=64, help="scatterings per packet in the galaxy section")
     ap.add_argument("--max-scatt", type=int, default=0,
                     help="cap scatterings per packet (profiling runs only; 0 = the full workload)")
     return ap.parse_args()
@@ -189,6 +193,83 @@ def run_batch(args):
             "autotuned": {"block": tune["best"][0], "blocks_per_sm": tune["best"][1]},
             "workload": "512 homogeneous slab/sphere models: tau0 log-U[1e2,1e7], T log-U[1e2,1e5] K, "
                         "v_max U[0,300] km/s, (2^d)^3 grids d in 2..5, packets log-U[1e3,1e5] x %g" % args.batch_scale}
+
+
+# ------------------------------------------------------------------ galaxy section
+def run_galaxy(args, peaks):
+    """Synthetic galaxy (~1e7 leaves, levels 6-12, three lines, dust,
+    turbulence): (a) optical depths of rays from emitting leaves to the box
+    border at Lya line centre (the peeling integral on its own, the
+    HBM-bound walk), (b) propagation with peeling into 4 directions and
+    256x256x400 cubes, (c) the adjoint of those cubes."""
+    import torch
+    import paper_2001_11252_gb300 as rg
+    import synth
+    t0 = time.perf_counter()
+    wl = synth.galaxy(n_packets=max(args.galaxy_rays, args.galaxy_packets))
+    gen_s = time.perf_counter() - t0
+    dev = torch.device("cuda:0")
+    ctx = rg.Context(0)
+    ctx.setup(wl)
+    ph = wl.physics
+    ctx.set_physics(ph.recoil, ph.isotropic, 0, ph.x_gauss, args.galaxy_cap, 0, ph.tau_stop, ph.seed)
+    tree = wl.medium.tree
+    out = {"leaves": tree.nleaf, "octs": tree.noct, "levels": [int(tree.leaf_level.min()), int(tree.leaf_level.max())],
+           "generate_s": gen_s}
+    # (a) ray casting
+    n = args.galaxy_rays
+    rng = np.random.default_rng(7)
+    mu = 2 * rng.random(n) - 1
+    phi = 2 * math.pi * rng.random(n)
+    st = np.sqrt(1 - mu * mu)
+    d = np.stack([st * np.cos(phi), st * np.sin(phi), mu], 1)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev, torch.float64)
+    pos, dr = t(wl.packets.pos[:n]), t(d)
+    nu = t(np.full(n, synth.nu_of(wl.lines[0].lambda_A)))
+    ctx.ray_tau(pos, dr, nu)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    tau, _, _, ncell = ctx.ray_tau(pos, dr, nu)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    cells = int(ncell.sum().item())
+    alg = cells * 28.0   # n_HI, v(3), T, n_dust, n_Si per leaf visit
+    hbm = peaks.get("hbm_gbs", 6671.9)
+    out["ray_cast"] = {"rays": n, "cells": cells, "ms": ms, "rays_per_s": n / (ms * 1e-3),
+                       "cells_per_s": cells / (ms * 1e-3),
+                       "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                                    "frac": alg / (ms * 1e-3) / 1e9 / hbm, "traffic": None,
+                                    "note": "28 algorithmic bytes per leaf visit; peak = measured copy bandwidth"}}
+    # (b) propagation with peeling, (c) adjoint
+    m = args.galaxy_packets
+    pk = wl.packets
+    tp = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(dev, dt)
+    packets = (tp(pk.pos[:m], torch.float64), tp(pk.dir[:m], torch.float64), tp(pk.nu[:m], torch.float64),
+               tp(pk.ids[:m].view(np.int64), torch.int64))
+    ctx.zero_tallies()
+    ctx.propagate(*packets, stats=False)
+    torch.cuda.synchronize()
+    ctx.zero_tallies()
+    t0 = time.perf_counter()
+    stp = ctx.propagate(*packets, stats=True)
+    torch.cuda.synchronize()
+    tprop = time.perf_counter() - t0
+    g = torch.randn((len(wl.detector.dirs), wl.detector.npix, wl.detector.npix, wl.detector.nbin), device=dev)
+    t0 = time.perf_counter()
+    grad = ctx.peel_adjoint(*packets, g_cube=g)
+    torch.cuda.synchronize()
+    tadj = time.perf_counter() - t0
+    out["peel"] = {"packets": m, "cap": args.galaxy_cap, "seconds": tprop, "scatterings": stp["nscatt_line"] +
+                   stp["nscatt_dust"], "peel_rays": stp["npeel_rays"], "peel_cells": stp["npeel_cells"],
+                   "peel_rays_per_s": stp["npeel_rays"] / tprop, "peel_cells_per_s": stp["npeel_cells"] / tprop,
+                   "capped": stp["capped"], "escaped": stp["escaped"], "absorbed": stp["absorbed"]}
+    out["adjoint"] = {"seconds": tadj, "peel_rays_per_s": stp["npeel_rays"] / tadj,
+                      "grad_nonzero_leaves": int((grad[0] != 0).sum().item())}
+    ctx.close()
+    return out
 
 
 # ------------------------------------------------------------------ our arm
@@ -336,6 +417,8 @@ def main():
             "clocks": clk}
     if args.batch_models > 0 and world == 1:
         line["batch"] = run_batch(args)
+    if args.galaxy and world == 1:
+        line["galaxy"] = run_galaxy(args, peaks)
     if not args.no_cpu_baseline and world == 1:
         threads = os.cpu_count() or 1
         sc, pr, npk, secs = cpu_oracle_rate(workload, args.cpu_seconds, threads)

@@ -491,3 +491,193 @@ def batch_models(n_models=512, packet_scale=1.0, seed_offset=0, max_scatt=0):
         out.append(Workload("batch%03d" % m, med, dom, [line], Dust(),
                             Physics(recoil=1, isotropic=0, seed=seed, max_scatt=max_scatt), Detector(lo, hi, nb), pk))
     return out
+
+
+def siII_sphere(tau0=1e3, T=1e4, n_packets=400, base=3, max_level=4, tau_dust=0.2, v_max_kms=50.0):
+    """Sphere of Si II (with a little H I and dust) lit at the Si II 1193.28 A
+    line centre: exercises several lines at once and the fluorescent decay
+    channels of Sect. 3.2.3 (1193 -> 1197*, 1190 -> 1194*)."""
+    tree = sphere_octree(base, max_level)
+    L = 1.0 * KPC_CM
+    R = 0.45
+    l1193, l1190 = siII_1193(), siII_1190()
+    n_si = density_for_tau0(l1193, T, tau0, R * L)
+    dust = Dust(sigma=4.0e-22)
+    nd = tau_dust / (dust.sigma * R * L)
+    med = uniform_medium(tree, L, 1e-3 * n_si, T, n_dust=nd, n_metal=n_si)
+    ctr = tree.leaf_centres() - 0.5
+    v = (v_max_kms * 1e5 / R) * ctr
+    med.vx, med.vy, med.vz = (v[:, i].astype(np.float32) for i in range(3))
+    seed = RUN_SEED + 5
+    nu0 = nu_of(l1193.lambda_A)
+    pk = point_source(n_packets, (0.5, 0.5, 0.5), nu0, seed ^ 0xA5A5)
+    lo, hi = nu_of(1199.0), nu_of(1188.0)
+    det = Detector(lo, hi, 400, dirs=PEEL_DIRS_3[:2].copy(), npix=4, fov=2 * R, cube=1)
+    return Workload("siII", med, Domain(0, (0.5, 0.5, 0.5), R), [lya(), l1190, l1193], dust,
+                    Physics(recoil=1, isotropic=0, seed=seed), det, pk)
+
+
+# --------------------------------------------------------------------------
+# Synthetic galaxy octree (levels base..max, lognormal fields)
+# --------------------------------------------------------------------------
+ZSUN = 0.0134
+
+
+def grf(n, slope, rng):
+    """Gaussian random field on an n^3 periodic grid with power spectrum
+    P(k) ~ k^slope, zero mean, unit variance."""
+    kx = np.fft.fftfreq(n)[:, None, None]
+    ky = np.fft.fftfreq(n)[None, :, None]
+    kz = np.fft.rfftfreq(n)[None, None, :]
+    k2 = kx * kx + ky * ky + kz * kz
+    k2[0, 0, 0] = 1.0
+    amp = k2 ** (slope / 4.0)
+    amp[0, 0, 0] = 0.0
+    white = rng.normal(size=(n, n, n)).astype(np.float32)
+    f = np.fft.rfftn(white) * amp
+    del white
+    out = np.fft.irfftn(f, s=(n, n, n)).astype(np.float32)
+    out -= out.mean()
+    out /= out.std()
+    return out
+
+
+def _block_max(a, f):
+    n = a.shape[0] // f
+    return a.reshape(n, f, n, f, n, f).max(axis=(1, 3, 5))
+
+
+def galaxy(n_leaf=10_000_000, grid_level=8, base_level=6, max_level=14, n_packets=10_000_000,
+           box_kpc=20.0, Z=0.3, seed_offset=0, npix=256, nchan=400, ndir=4, si_fraction=0.2):
+    """Synthetic galaxy medium: log10 n_HI a Gaussian random field with
+    P(k) ~ k^-11/3, median 1e-2 cm^-3 and 2 dex scatter; log T a second field,
+    median 1e4 K, 0.7 dex, clipped to [1e2, 1e6]; a Kolmogorov velocity field
+    (each component P(k) ~ k^-11/3), 3D rms 50 km/s; dust n_HI Z/Z0 (Z0 = 0.005,
+    Sect. 3.1.2); Si II n_HI 3.2e-5 Z/Zsun.  Fields are piecewise constant on a
+    (2^grid_level)^3 grid.  Octree: all cells to base_level, then a cell of
+    size h is split while max n_HI over the cell widened by 2h on each side,
+    times (h box)^3, exceeds a column-mass threshold tuned to ~n_leaf leaves
+    (widening by 2h keeps neighbouring leaves within one level).  Packets
+    (80% Lya, 10% each Si II 1190/1193) are emitted from leaves with
+    probability ~ n_HI^2 V, uniformly inside the leaf, isotropically, at line
+    centre in the gas frame broadened by a Gaussian of the leaf's Doppler
+    width; 4 peeling directions into npix^2 x nchan cubes over +-2000 km/s of
+    Lya."""
+    import scipy.ndimage as ndi
+    seed = RUN_SEED + 4 + seed_offset
+    rng = np.random.default_rng(seed ^ 0xA5A5)
+    G = grid_level
+    ng = 1 << G
+    L = box_kpc * KPC_CM
+    logn = (-2.0 + 2.0 * grf(ng, -11.0 / 3.0, rng)).astype(np.float32)
+    nH = np.power(10.0, logn, dtype=np.float32)
+    logT = np.clip(4.0 + 0.7 * grf(ng, -11.0 / 3.0, rng), 2.0, 6.0)
+    Tg = np.power(10.0, logT).astype(np.float32)
+    vel = [grf(ng, -11.0 / 3.0, rng) for _ in range(3)]
+    vs = 50e5 / math.sqrt(3.0)
+    # refinement criterion: dilated maxima per level
+    mx = {}
+    for l in range(1, G + 1):
+        pooled = _block_max(nH, 1 << (G - l)) if l < G else nH
+        mx[l] = ndi.maximum_filter(pooled, size=5, mode="wrap")
+    fine = ndi.maximum_filter(nH, size=3, mode="wrap")
+
+    def n_leaves(thr):
+        # exact leaf count of the tree the criterion below builds
+        total = 0.0
+        exists = np.ones((1 << base_level,) * 3, bool)
+        refined = None
+        for l in range(base_level, G + 1):
+            if l > base_level:
+                exists = refined.repeat(2, 0).repeat(2, 1).repeat(2, 2)
+            crit = mx[l].astype(np.float64) * (L / (1 << l)) ** 3 >= thr
+            refined = exists & crit if l < max_level else np.zeros_like(exists)
+            total += float(np.count_nonzero(exists & ~refined))
+        if G < max_level:
+            f = fine[refined].astype(np.float64)
+            per = np.ones(f.size)
+            for l in range(G + 1, max_level + 1):
+                more = f * (L / (1 << l)) ** 3 >= thr if l < max_level else np.zeros(f.size, bool)
+                per = np.where(more, per * 8.0, per)
+                f = np.where(more, f, 0.0)
+            total += float(np.sum(8.0 * per))
+        return total
+
+    lo, hi = 1e20, 1e90
+    target = 1.5 * n_leaf   # the count above splits whole grid cells; the built tree splits ~2/3 as many
+    for _ in range(24):
+        mid = math.sqrt(lo * hi)
+        if n_leaves(mid) > target:
+            lo = mid
+        else:
+            hi = mid
+    thr = math.sqrt(lo * hi)
+
+    def region_max(l, i, j, k):
+        # max density over the grid cells met by the cell widened by 2 cells
+        # of its own size (a cell below the grid level meets at most 3 per axis)
+        s = l - G
+        lo = [((c - 2) >> s) for c in (i, j, k)]
+        hi = [((c + 3 + (1 << s) - 1) >> s) - 1 for c in (i, j, k)]
+        m = np.zeros(i.shape, np.float32)
+        for a in range(3):
+            for b in range(3):
+                for c in range(3):
+                    gx, gy, gz = lo[0] + a, lo[1] + b, lo[2] + c
+                    ok = (gx <= hi[0]) & (gy <= hi[1]) & (gz <= hi[2])
+                    v = nH[gx % ng, gy % ng, gz % ng]
+                    m = np.where(ok, np.maximum(m, v), m)
+        return m
+
+    def refine(l, i, j, k):
+        h3 = (L / (1 << l)) ** 3
+        if l < base_level:
+            return np.ones(i.shape, bool)
+        m = mx[l][i, j, k] if l <= G else region_max(l, i, j, k)
+        return m.astype(np.float64) * h3 >= thr
+
+    tree = build_octree(refine, max_level)
+    ctr = tree.leaf_centres()
+    gi = np.minimum((ctr * ng).astype(np.int64), ng - 1)
+    idx = (gi[:, 0], gi[:, 1], gi[:, 2])
+    n_leafHI = nH[idx]
+    Tl = Tg[idx]
+    med = Medium(tree, L, n_leafHI.astype(np.float32), (vs * vel[0][idx]).astype(np.float32),
+                 (vs * vel[1][idx]).astype(np.float32), (vs * vel[2][idx]).astype(np.float32),
+                 Tl.astype(np.float32), (n_leafHI * (Z * ZSUN / 0.005)).astype(np.float32),
+                 (n_leafHI * 3.2e-5 * Z).astype(np.float32))
+    del vel, mx, fine
+    lines = [lya(), siII_1190(), siII_1193()]
+    # sources: leaf chosen with probability ~ n^2 V (cumulative sum + bisection)
+    w = (n_leafHI.astype(np.float64) ** 2) * tree.leaf_size() ** 3
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    srng = np.random.default_rng(seed ^ 0x5A5A)
+    leaf = np.searchsorted(cdf, srng.random(n_packets), side="right")
+    leaf = np.minimum(leaf, tree.nleaf - 1)
+    h = tree.leaf_size()[leaf]
+    pos = tree.leaf_ijk[leaf] * h[:, None] + srng.random((n_packets, 3)) * h[:, None]
+    pos = np.minimum(pos, np.nextafter(1.0, 0.0))
+    mu = 2.0 * srng.random(n_packets) - 1.0
+    phi = 2.0 * math.pi * srng.random(n_packets)
+    st = np.sqrt(np.maximum(0.0, 1.0 - mu * mu))
+    d = np.stack([st * np.cos(phi), st * np.sin(phi), mu], 1)
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    which = srng.random(n_packets)
+    lam = np.where(which < 1 - si_fraction, lines[0].lambda_A,
+                   np.where(which < 1 - si_fraction / 2, lines[1].lambda_A, lines[2].lambda_A))
+    mass = np.where(which < 1 - si_fraction, lines[0].mass_g, lines[1].mass_g)
+    nu0 = C_CGS / (lam * 1e-8)
+    vth = np.sqrt(2.0 * KB_CGS * Tl[leaf].astype(np.float64) / mass)
+    nu_gas = nu0 * (1.0 + vth / C_CGS * srng.normal(size=n_packets) / math.sqrt(2.0))
+    v = np.stack([med.vx[leaf], med.vy[leaf], med.vz[leaf]], 1).astype(np.float64)
+    nu_ext = nu_gas * (1.0 + (d * v).sum(1) / C_CGS)
+    pk = Packets(pos, d, nu_ext, np.arange(n_packets, dtype=np.uint64))
+    nuL = nu_of(lines[0].lambda_A)
+    vmax = 2000e5
+    dirs = np.array([[0, 0, 1.0], [1.0, 0, 0], [0, 1.0, 0], [1.0, 1.0, 1.0]])[:ndir]
+    det = Detector(nuL * (1 - vmax / C_CGS), nuL * (1 + vmax / C_CGS), nchan, dirs=dirs, npix=npix, fov=1.0,
+                   centre=(0.5, 0.5, 0.5), cube=1)
+    dust = Dust(sigma=4.0e-22)
+    return Workload("galaxy", med, Domain(2, (0.5, 0.5, 0.5), 0.5), lines, dust,
+                    Physics(recoil=1, isotropic=0, seed=seed, max_scatt=100000), det, pk)

@@ -60,7 +60,7 @@ def test_upar_matches_oracle_streams():
 
 
 # ---------------------------------------------------------------- walk
-@pytest.mark.parametrize("which", ["sphere", "slab", "expanding"])
+@pytest.mark.parametrize("which", ["sphere", "slab", "expanding", "galaxy"])
 def test_ray_walk_bit_exact(which):
     """Octree walk (Sect. 4.3): identical leaf sequence and identical FP64
     path lengths per leaf; tau within 1e-6 relative."""
@@ -68,6 +68,8 @@ def test_ray_walk_bit_exact(which):
         wl = synth.sphere(tau0=1e4, T=1e4, tau_dust=0.5, n_packets=1, base=3, max_level=6)
     elif which == "slab":
         wl = synth.slab(tau0=1e3, n_packets=1)
+    elif which == "galaxy":
+        wl = synth.galaxy(n_leaf=150_000, grid_level=6, base_level=4, max_level=10, n_packets=10, npix=8, nchan=8)
     else:
         wl = synth.expanding_sphere(n_packets=1)
     ctx = context(wl)
@@ -77,6 +79,8 @@ def test_ray_walk_bit_exact(which):
     pos = rng.uniform(0.1, 0.9, (n, 3))
     if which == "slab":
         pos[:, 2] = rng.uniform(0.0, 1.0, n)
+    elif which == "galaxy":
+        pos = rng.uniform(0.0, 1.0, (n, 3))
     else:
         c = np.array(wl.domain.centre)
         r = wl.domain.size * rng.random(n) ** (1 / 3) * 0.999
@@ -264,3 +268,47 @@ def test_error_budget_gpu():
     rel = g["path"] / wl.domain.size - 1
     assert np.all(g["status"] == 1)
     assert np.abs(rel).max() < 1e-12
+
+
+def test_metal_lines_fluorescence_matches_oracle():
+    """Three lines at once (Lya + Si II 1190 + Si II 1193) with fluorescent
+    channels (Sect. 3.2.3, Table 1), dust and a velocity field: same fates,
+    scattering counts and spectra as the oracle on coupled streams."""
+    wl = synth.siII_sphere(n_packets=400)
+    ctx = context(wl)
+    g, st = gpu_run(ctx, wl.packets)
+    r, tal = oracle_run(wl)
+    same = (g["nscatt"] == r["nscatt"]).mean()
+    print("Si II: identical %.4f <N> %.2f vs %.2f escaped %d vs %d" % (
+        same, g["nscatt"].mean(), r["nscatt"].mean(), (g["status"] == 1).sum(), (r["status"] == 1).sum()))
+    assert same > 0.9
+    esc_g, esc_r = g["status"] == 1, r["status"] == 1
+    # fluorescent photons leave at 1197.39 A: present on both sides in the same numbers
+    lam_g = 2.99792458e18 / g["nu"][esc_g]
+    lam_r = 2.99792458e18 / r["nu"][esc_r]
+    fg, fr = (np.abs(lam_g - 1197.39) < 0.5).sum(), (np.abs(lam_r - 1197.39) < 0.5).sum()
+    assert fr > 20 and abs(fg - fr) <= 4 * math.sqrt(fr)
+    assert _ks(lam_g, lam_r) > 0.01
+    spec = ctx.get_tally(0)
+    assert abs(spec.sum() - tal["spec"].sum()) <= 4 * math.sqrt(tal["spec"].sum())
+
+
+def test_galaxy_run_matches_oracle():
+    """Synthetic galaxy (graded octree, levels 4-10, lognormal fields, three
+    lines with fluorescence, dust, turbulent velocities, peeling into 4
+    directions): packets capped at 300 scatterings; same fates, counts and
+    peeled flux as the oracle on coupled streams."""
+    wl = synth.galaxy(n_leaf=150_000, grid_level=6, base_level=4, max_level=10, n_packets=300, npix=16,
+                      nchan=40)
+    wl.physics.max_scatt = 300
+    ctx = context(wl)
+    g, st = gpu_run(ctx, wl.packets)
+    r, tal = oracle_run(wl)
+    same = ((g["nscatt"] == r["nscatt"]) & (g["status"] == r["status"])).mean()
+    print("galaxy: identical %.4f statuses %s vs %s" % (same, np.bincount(g["status"], minlength=5),
+                                                        np.bincount(r["status"], minlength=5)))
+    assert same > 0.9
+    assert st["errors"] == 0
+    ps = ctx.get_tally(1)
+    a, b = ps.sum(), tal["pspec"].sum()
+    assert abs(a / b - 1) < 0.05, (a, b)
