@@ -309,6 +309,9 @@ def test_galaxy_run_matches_oracle():
                                                         np.bincount(r["status"], minlength=5)))
     assert same > 0.9
     assert st["errors"] == 0
+    # packets are born in the densest leaves: the peeled flux may vanish
+    # (every peeling ray beyond tau = 50); both sides must agree either way
     ps = ctx.get_tally(1)
-    a, b = ps.sum(), tal["pspec"].sum()
-    assert abs(a / b - 1) < 0.05, (a, b)
+    a, b = float(ps.sum()), float(tal["pspec"].sum())
+    assert abs(a - b) <= 0.05 * max(a, b) + 1e-30, (a, b)
+    assert st["npeel_rays"] == tal["npeel"]
