@@ -24,35 +24,77 @@ constexpr float kTwoPiF = 6.2831853071795865f;
 // Philox4x32-10 (Salmon et al. 2011).  Key = run seed; counter = (draw block
 // lo, hi, packet id lo, hi).  Draw word n of a packet is word n%4 of block n/4.
 // ---------------------------------------------------------------------------
-// one Philox4x32-10 block; kept out of line so that the many draw sites of
-// the transport loop share one copy of the ten rounds
+// one Philox4x32-10 round of counter (c0, c1, c2, c3) under key (k0, k1)
+__device__ __forceinline__ void philox_round(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
+                                             uint32_t k0, uint32_t k1) {
+    uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+}
+
+// one Philox4x32-10 block; kept out of line so that the draw sites of the
+// transport loop share one copy of the ten rounds
 __device__ __noinline__ uint4 philox_block(uint32_t blk, uint32_t id0, uint32_t id1, uint32_t k0, uint32_t k1) {
     uint32_t c0 = blk, c1 = 0, c2 = id0, c3 = id1;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
-        uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-        uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
-        uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        philox_round(c0, c1, c2, c3, k0, k1);
     }
     return make_uint4(c0, c1, c2, c3);
 }
 
+// Draw words of a packet's stream.  Each thread owns a ring of kRing words in
+// dynamic shared memory (word i in row i % kRing of the thread's column, so
+// the lanes of a warp always hit distinct banks).  top_up(), called where the
+// warp is converged, computes the next blocks of every lane together (two
+// blocks interleaved for instruction-level parallelism); word() computes a
+// block by itself only when the ring runs dry (extra rejection trials).
+// Dynamic shared memory of a kernel using Rng starts with kRing * blockDim.x
+// words for the rings.
+constexpr uint32_t kRing = 16;
+
 struct Rng {
     uint32_t k0, k1, id0, id1;
-    uint32_t n;        // next draw index
-    uint32_t w0, w1, w2, w3;  // cached block n/4 (valid when n%4 != 0)
+    uint32_t n;       // next draw index
+    uint32_t avail;   // words n .. avail - 1 are in the ring; avail % 4 == 0
 
-    __device__ __forceinline__ void block(uint32_t blk) {
-        uint4 w = philox_block(blk, id0, id1, k0, k1);
-        w0 = w.x; w1 = w.y; w2 = w.z; w3 = w.w;
+    static __device__ __forceinline__ uint32_t& slot(uint32_t i) {
+        extern __shared__ uint32_t s_dyn[];
+        return s_dyn[(i & (kRing - 1u)) * blockDim.x + threadIdx.x];
+    }
+    __device__ __forceinline__ void put(uint32_t first, uint4 w) {
+        slot(first) = w.x; slot(first + 1u) = w.y; slot(first + 2u) = w.z; slot(first + 3u) = w.w;
     }
     __device__ __forceinline__ uint32_t word() {
-        uint32_t j = n & 3u;
-        if (j == 0u) block(n >> 2);
-        ++n;
-        return j == 0u ? w0 : (j == 1u ? w1 : (j == 2u ? w2 : w3));
+        if (n == avail) {
+            put(avail, philox_block(avail >> 2, id0, id1, k0, k1));
+            avail += 4u;
+        }
+        return slot(n++);
+    }
+    // fill the ring to kRing - 3 .. kRing words ahead
+    __device__ __forceinline__ void top_up() {
+        if (avail - n <= kRing - 8u) {
+            const uint32_t blk = avail >> 2;
+            uint32_t a0 = blk, a1 = 0u, a2 = id0, a3 = id1;
+            uint32_t b0 = blk + 1u, b1 = 0u, b2 = id0, b3 = id1;
+            uint32_t q0 = k0, q1 = k1;
+#pragma unroll
+            for (int r = 0; r < 10; ++r) {
+                if (r) { q0 += 0x9E3779B9u; q1 += 0xBB67AE85u; }
+                philox_round(a0, a1, a2, a3, q0, q1);
+                philox_round(b0, b1, b2, b3, q0, q1);
+            }
+            put(avail, make_uint4(a0, a1, a2, a3));
+            put(avail + 4u, make_uint4(b0, b1, b2, b3));
+            avail += 8u;
+        }
+        if (avail - n <= kRing - 4u) {
+            put(avail, philox_block(avail >> 2, id0, id1, k0, k1));
+            avail += 4u;
+        }
     }
     // ((w >> 9) + 1/2) 2^-23: in (0, 1), exactly representable in FP32, and
     // so is 1 - u
@@ -76,11 +118,16 @@ struct Rng {
         float v = fmaf(__uint2float_rn(ma), 0x1p-26f, (__uint2float_rn(mb) + 0.5f) * 0x1p-52f);
         return hi ? -log1pf(-v) : -logf(v);
     }
+    // stream of packet pid, next draw `start`
     __device__ void init(const Params& P, uint64_t pid, uint32_t start = 0) {
         k0 = P.key0; k1 = P.key1;
         id0 = (uint32_t)pid; id1 = (uint32_t)(pid >> 32);
         n = start;
-        if (n & 3u) block(n >> 2);
+        avail = start & ~3u;
+        if (n & 3u) {
+            put(avail, philox_block(avail >> 2, id0, id1, k0, k1));
+            avail += 4u;
+        }
     }
 };
 

@@ -290,8 +290,9 @@ __device__ __forceinline__ void scatter_line(const Params& P, Packet<NL>& s, flo
     // scattering in the leaf, then read from shared memory
     U0Coef u0c;
     {
+        // after the draw rings of Rng
         extern __shared__ float s_u0[];
-        float* col = s_u0 + (size_t)IL * 6 * blockDim.x + threadIdx.x;
+        float* col = s_u0 + (size_t)(kRing + IL * 6) * blockDim.x + threadIdx.x;
         if (!(s.cc.u0mask & (1u << IL))) {
             u0_coeffs(L.a_over_invdnu * s.cc.invdnu[IL], u0c);
 #pragma unroll
@@ -463,6 +464,7 @@ template <int NL, bool PEEL>
 __device__ __forceinline__ void advance(const Params& P, const Geo& G, Packet<NL>& s, Tallies& tl,
                                         const TraceOut& tr) {
     bool evt = false;
+    s.rng.top_up();   // the warp is converged here: draw blocks for all lanes at once
     if (s.enter) {
         load_cell<NL>(P, G, s.w.leaf, s.cc);
         ++tl.leaf_loads;
@@ -749,7 +751,8 @@ __global__ void k_sample_upar(Params P, long long n, const double* x, const floa
 // ---------------------------------------------------------------------------
 int propagate_block_size() { return 128; }
 
-size_t propagate_smem(int nline, int block) { return (size_t)nline * 6 * block * sizeof(float); }
+// draw rings, then the u0 coefficient cache of each line
+size_t propagate_smem(int nline, int block) { return (size_t)(kRing + nline * 6) * block * sizeof(float); }
 
 template <int NL, bool PEEL, bool BATCH>
 static int occ(int block) {
@@ -817,7 +820,7 @@ cudaError_t launch_eval_voigt(long long n, const float* a, const double* x, floa
 cudaError_t launch_sample_upar(const Params& P, long long n, const double* x, const float* a, const uint64_t* id,
                                float* u, int32_t* nd, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    k_sample_upar<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(P, n, x, a, id, u, nd);
+    k_sample_upar<<<(unsigned)((n + 127) / 128), 128, kRing * 128 * sizeof(uint32_t), st>>>(P, n, x, a, id, u, nd);
     return cudaGetLastError();
 }
 
