@@ -60,6 +60,11 @@ def parse():
     ap.add_argument("--galaxy-rays", type=int, default=1 << 20)
     ap.add_argument("--galaxy-packets", type=int, default=1 << 15)
     ap.add_argument("--galaxy-cap", type=int, default=64, help="scatterings per packet in the galaxy section")
+    ap.add_argument("--galaxy-thin", type=float, default=1e-8,
+                    help="density scale of the lower-column copy of the galaxy used for peeling and its adjoint")
+    ap.add_argument("--section", default="all", choices=["all", "main", "batch", "galaxy"],
+                    help="all (default): the headline line with the batch and galaxy sections; "
+                         "batch / galaxy: that section alone, printed as its own JSON line")
     ap.add_argument("--max-scatt", type=int, default=0,
                     help="cap scatterings per packet (profiling runs only; 0 = the full workload)")
     return ap.parse_args()
@@ -249,24 +254,43 @@ def run_galaxy(args, peaks):
     tp = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(dev, dt)
     packets = (tp(pk.pos[:m], torch.float64), tp(pk.dir[:m], torch.float64), tp(pk.nu[:m], torch.float64),
                tp(pk.ids[:m].view(np.int64), torch.int64))
-    ctx.zero_tallies()
-    ctx.propagate(*packets, stats=False)
-    torch.cuda.synchronize()
-    ctx.zero_tallies()
-    t0 = time.perf_counter()
-    stp = ctx.propagate(*packets, stats=True)
-    torch.cuda.synchronize()
-    tprop = time.perf_counter() - t0
+
+    def peel_run(label):
+        ctx.zero_tallies()
+        ctx.propagate(*packets, stats=False)
+        torch.cuda.synchronize()
+        ctx.zero_tallies()
+        t0 = time.perf_counter()
+        stp = ctx.propagate(*packets, stats=True)
+        torch.cuda.synchronize()
+        tprop = time.perf_counter() - t0
+        rays, cells = stp["npeel_rays"], stp["npeel_cells"]
+        return stp, {"medium": label, "packets": m, "cap": args.galaxy_cap, "seconds": tprop,
+                     "scatterings": stp["nscatt_line"] + stp["nscatt_dust"], "peel_rays": rays, "peel_cells": cells,
+                     "cells_per_ray": cells / max(1, rays), "peel_rays_per_s": rays / tprop,
+                     "peel_cells_per_s": cells / tprop, "capped": stp["capped"], "escaped": stp["escaped"],
+                     "absorbed": stp["absorbed"]}
+
+    # as generated: packets born in the densest leaves, every peeling ray
+    # stopped at tau = 50 within its first leaf
+    _, out["peel"] = peel_run("as generated (tau0 ~ 1e9-1e15 from the sources)")
+    # the same octree and fields with every density scaled by --galaxy-thin:
+    # peeling rays cross the galaxy and the adjoint has work to do
+    mm = wl.medium
+    sc = args.galaxy_thin
+    nm = getattr(mm, "n_metal", None)
+    ctx.update_fields(np.asarray(mm.n_HI, np.float32) * sc, mm.vx, mm.vy, mm.vz, mm.T,
+                      np.asarray(mm.n_dust, np.float32) * sc, None if nm is None else np.asarray(nm, np.float32) * sc)
+    stp, out["peel_thin"] = peel_run("densities x %g" % sc)
     g = torch.randn((len(wl.detector.dirs), wl.detector.npix, wl.detector.npix, wl.detector.nbin), device=dev)
+    ctx.peel_adjoint(*packets, g_cube=g)
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     grad = ctx.peel_adjoint(*packets, g_cube=g)
     torch.cuda.synchronize()
     tadj = time.perf_counter() - t0
-    out["peel"] = {"packets": m, "cap": args.galaxy_cap, "seconds": tprop, "scatterings": stp["nscatt_line"] +
-                   stp["nscatt_dust"], "peel_rays": stp["npeel_rays"], "peel_cells": stp["npeel_cells"],
-                   "peel_rays_per_s": stp["npeel_rays"] / tprop, "peel_cells_per_s": stp["npeel_cells"] / tprop,
-                   "capped": stp["capped"], "escaped": stp["escaped"], "absorbed": stp["absorbed"]}
-    out["adjoint"] = {"seconds": tadj, "peel_rays_per_s": stp["npeel_rays"] / tadj,
+    out["adjoint"] = {"medium": "densities x %g" % sc, "seconds": tadj,
+                      "peel_rays_per_s": stp["npeel_rays"] / tadj,
                       "grad_nonzero_leaves": int((grad[0] != 0).sum().item())}
     ctx.close()
     return out
@@ -277,6 +301,17 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.section in ("batch", "galaxy"):
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        res = run_batch(args) if args.section == "batch" else run_galaxy(args, peaks)
+        print(json.dumps({"section": args.section, args.section: res}), flush=True)
+        return
     import torch
     import paper_2001_11252_gb300 as rg
 
@@ -415,9 +450,9 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps,
             "clocks": clk}
-    if args.batch_models > 0 and world == 1:
+    if args.batch_models > 0 and world == 1 and args.section == "all":
         line["batch"] = run_batch(args)
-    if args.galaxy and world == 1:
+    if args.galaxy and world == 1 and args.section == "all":
         line["galaxy"] = run_galaxy(args, peaks)
     if not args.no_cpu_baseline and world == 1:
         threads = os.cpu_count() or 1

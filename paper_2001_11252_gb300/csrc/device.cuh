@@ -11,6 +11,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include "internal.h"
+#include "bits.cuh"
 
 namespace rg {
 
@@ -350,17 +351,15 @@ struct Where {
     int i, j, k;   // integer coordinates of the leaf at its level
 };
 
-__device__ __forceinline__ int dir_coord(double p, double k, double scale) {
-    double y = p * scale;   // exact: scale is a power of two
-    return k < 0.0 ? __double2int_ru(y) - 1 : __double2int_rd(y);
-}
+// integer coordinate at level L of the cell holding p + eps k (bits.cuh)
+__device__ __forceinline__ int dir_coord(double p, double k, int L) { return cell_coord(p, is_neg(k), L); }
 
 // slab domains are periodic in x and y (Sect. 4): bring p + eps k into the box
 __device__ __forceinline__ void wrap_periodic(const Geo& G, double p[3], const double k[3]) {
     if (G.dom_kind != 1) return;
 #pragma unroll
     for (int ax = 0; ax < 2; ++ax) {
-        int c = dir_coord(p[ax], k[ax], 2.0);
+        int c = dir_coord(p[ax], k[ax], 1);
         if (c >= 2) p[ax] = p[ax] - 1.0;
         else if (c < 0) p[ax] = p[ax] + 1.0;
     }
@@ -407,9 +406,8 @@ __device__ __forceinline__ bool locate(const Geo& G, int tx, int ty, int tz, Whe
 
 __device__ __forceinline__ bool locate_point(const Geo& G, const double p[3], const double k[3],
                                              Where& w, uint32_t& loads) {
-    double sc = (double)(1 << G.max_level);
-    return locate(G, dir_coord(p[0], k[0], sc), dir_coord(p[1], k[1], sc), dir_coord(p[2], k[2], sc),
-                  w, loads);
+    const int L = G.max_level;
+    return locate(G, dir_coord(p[0], k[0], L), dir_coord(p[1], k[1], L), dir_coord(p[2], k[2], L), w, loads);
 }
 
 // Neighbour search after crossing a face (Sect. 4.3): the target is first
@@ -419,10 +417,9 @@ __device__ __forceinline__ bool next_leaf(const Geo& G, const double p[3], const
                                           int axis, Where& w, uint32_t& son_loads,
                                           uint32_t& nbor_loads) {
     const int L = G.max_level;
-    double sc = (double)(1 << L);
     int t[3];
 #pragma unroll
-    for (int ax = 0; ax < 3; ++ax) t[ax] = dir_coord(p[ax], k[ax], sc);
+    for (int ax = 0; ax < 3; ++ax) t[ax] = dir_coord(p[ax], k[ax], L);
     const int n = 1 << L;
     if ((unsigned)t[0] >= (unsigned)n || (unsigned)t[1] >= (unsigned)n || (unsigned)t[2] >= (unsigned)n)
         return false;
@@ -437,7 +434,7 @@ __device__ __forceinline__ bool next_leaf(const Geo& G, const double p[3], const
         return true;
     }
     if (l >= 2) {
-        const bool up = axis == 0 ? k[0] > 0.0 : (axis == 1 ? k[1] > 0.0 : k[2] > 0.0);
+        const bool up = is_pos(axis == 0 ? k[0] : (axis == 1 ? k[1] : k[2]));
         int face = 2 * axis + (up ? 1 : 0);
         int4 a = __ldg(G.nbr + 2 * w.oct);
         int4 b = __ldg(G.nbr + 2 * w.oct + 1);
@@ -465,22 +462,24 @@ __device__ __forceinline__ bool next_leaf(const Geo& G, const double p[3], const
 }
 
 // distance along k from p to the exit face of leaf w (FP64, exactly the
-// oracle's (face - p) * (1/k)); axis = crossed axis, ties to the lowest axis
+// oracle's (face - p) * (1/k)); axis = crossed axis, ties to the lowest axis.
+// Face coordinates, the choice of the minimum and the clamp at zero run on
+// the integer pipes (bits.cuh).
 __device__ __forceinline__ double face_distance(const double p[3], const double k[3],
                                                 const double inv[3], const Where& w, int& axis) {
-    double h = ldexp(1.0, -w.level);
     const int c[3] = {w.i, w.j, w.k};
-    double best = __longlong_as_double(0x7ff0000000000000ULL);  // +inf
+    int64_t best = INT64_MAX;
     int ba = -1;
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-        if (k[ax] == 0.0) continue;
-        double face = __dmul_rn((double)(k[ax] > 0.0 ? c[ax] + 1 : c[ax]), h);
-        double t = __dmul_rn(__dsub_rn(face, p[ax]), inv[ax]);
+        if (is_zero(k[ax])) continue;
+        double face = dyadic((uint32_t)(is_pos(k[ax]) ? c[ax] + 1 : c[ax]), w.level);
+        int64_t t = order_key(__dmul_rn(__dsub_rn(face, p[ax]), inv[ax]));
         if (t < best) { best = t; ba = ax; }
     }
     axis = ba;
-    return best < 0.0 ? 0.0 : best;
+    if (ba < 0) return __longlong_as_double(0x7ff0000000000000LL);   // +inf (k = 0)
+    return best < 0 ? 0.0 : bitsd(best);
 }
 
 // distance along k from p to the domain border (FP64, same operation order as
@@ -515,27 +514,24 @@ __device__ __forceinline__ double border_distance(const Geo& G, const double p[3
 // smallest distance from p to any face of leaf w (box units, FP64), for the
 // guaranteed-inside budget of the scattering loop
 __device__ __forceinline__ double inner_distance(const double p[3], const Where& w) {
-    double h = ldexp(1.0, -w.level);
-    int c[3] = {w.i, w.j, w.k};
-    double best = h;
+    const int c[3] = {w.i, w.j, w.k};
+    int64_t best = order_key(dyadic(1u, w.level));
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-        double lo = __dmul_rn((double)c[ax], h);
-        double d1 = __dsub_rn(p[ax], lo);
-        double d2 = __dsub_rn(__dadd_rn(lo, h), p[ax]);
-        best = fmin(best, fmin(d1, d2));
+        double lo = dyadic((uint32_t)c[ax], w.level), hi = dyadic((uint32_t)c[ax] + 1u, w.level);
+        int64_t d1 = order_key(__dsub_rn(p[ax], lo)), d2 = order_key(__dsub_rn(hi, p[ax]));
+        best = min(best, min(d1, d2));
     }
-    return best;
+    return from_key(best);
 }
 
 // move to the exit face along `axis` and snap the crossing coordinate
 __device__ __forceinline__ void move_to_face(double p[3], const double k[3], int axis, double t,
                                              const Where& w) {
-    double h = ldexp(1.0, -w.level);
     const int c[3] = {w.i, w.j, w.k};
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) {
-        if (ax == axis) p[ax] = __dmul_rn((double)(k[ax] > 0.0 ? c[ax] + 1 : c[ax]), h);
+        if (ax == axis) p[ax] = dyadic((uint32_t)(is_pos(k[ax]) ? c[ax] + 1 : c[ax]), w.level);
         else p[ax] = __fma_rn(t, k[ax], p[ax]);
     }
 }
@@ -648,6 +644,70 @@ __device__ __forceinline__ float opacity(const Params& P, const CellCache<NL>& c
     for (int i = 0; i < NL; ++i) {
         double x = (nu - P.line[i].nu0) * cc.invdnu[i];
         kl[i] = cc.kap0[i] * voigt_h(cc.a[i], x);
+        tot += kl[i];
+    }
+    return tot;
+}
+
+// ---------------------------------------------------------------------------
+// Opacity along a ray at fixed external frequency and direction (the peeling
+// integral and its adjoint, Sect. 3.1 opacities in each leaf's frame), with no
+// FP64 instruction per leaf: the gas-frame offset nu_gas - nu0_i and the
+// Doppler offset x_i are formed in FP32 pairs (~1e-13 relative), so x keeps
+// the accuracy of the FP64 expression to_gas(nu_ext, beta) - nu0 over 1/Delta nu.
+// ---------------------------------------------------------------------------
+template <int NL>
+struct RayNu {
+    f2 nu;         // nu_ext
+    f2 d[NL];      // nu_ext - nu0_i
+    f2 k[3];       // direction
+};
+
+template <int NL>
+__device__ __forceinline__ void ray_nu(const Params& P, double nu_ext, const double k[3], RayNu<NL>& r) {
+    r.nu = f2_of(nu_ext);
+#pragma unroll
+    for (int i = 0; i < NL; ++i) r.d[i] = f2_of(nu_ext - P.line[i].nu0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) r.k[j] = f2_of(k[j]);
+}
+
+// 1/sqrt(T) as a pair: r + r (1 - T r^2) / 2 with T r^2 formed exactly
+__device__ __forceinline__ f2 rsqrt_pair(float T, float& rs) {
+    rs = rsqrtf(T);
+    float t = T * rs;
+    float te = __fmaf_rn(T, rs, -t);   // T rs = t + te
+    float e = __fmaf_rn(-t, rs, 1.0f) - te * rs;
+    return fast_two_sum(rs, 0.5f * rs * e);
+}
+
+// kappa (cm^-1) of the leaf record (r0, r1) at the ray's frequency, per line
+// in kl[] and each line's Doppler offset in xh[], xl[]; beta = k . v / c
+// returned as a pair
+template <int NL>
+__device__ __forceinline__ float ray_opacity(const Params& P, const RayNu<NL>& R, float4 r0, float4 r1,
+                                             float kl[NL], float xh[NL], float xl[NL], f2& beta) {
+    constexpr double kInvC = 1.0 / kC;
+    const f2 invc = {(float)kInvC, (float)(kInvC - (double)(float)kInvC)};
+    f2 kv = f2_mul_f(R.k[0], r0.y);
+    kv = f2_add(kv, f2_mul_f(R.k[1], r0.z));
+    kv = f2_add(kv, f2_mul_f(R.k[2], r0.w));
+    beta = f2_mul(kv, invc);
+    // nu_gas = nu_ext (1 + s), s = -b + b^2 - b^3 + b^4 - b^5 (to_gas)
+    const float bh = beta.h;
+    const float tail = bh * bh * (1.0f - bh * (1.0f - bh * (1.0f - bh)));
+    const f2 dn = f2_mul(R.nu, f2_add_f(f2_neg(beta), tail));
+    float rs;
+    const f2 rr = rsqrt_pair(fmaxf(r1.x, 1e-30f), rs);
+    float tot = r1.y * P.dust_sigma;
+#pragma unroll
+    for (int i = 0; i < NL; ++i) {
+        const LineDev& L = P.line[i];
+        const f2 x = f2_mul(f2_mul(f2_add(R.d[i], dn), f2{L.invdnu_h, L.invdnu_l}), rr);
+        const float n = (L.dens == 1 ? r1.z : r0.x) * L.abund;
+        xh[i] = x.h;
+        xl[i] = x.l;
+        kl[i] = n * L.sig_pref * rs * voigt_h2(L.a_pref * rs, x.h, x.l);
         tot += kl[i];
     }
     return tot;

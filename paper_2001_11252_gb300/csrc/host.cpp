@@ -71,7 +71,7 @@ struct rascas_ctx {
     rascas_detector det{};
     Params P{};
     DevBuf d_spec, d_pspec, d_pimg, d_pcube, d_counters, d_params;
-    DevBuf stage_in, stage_out, stage_aux, stage_adj;
+    DevBuf stage_in, stage_out, stage_aux, stage_adj, ray_init;
     // batch of independent models
     struct Batch {
         int nmodels = 0, nbin = 0, nline_at_load = 0;
@@ -317,7 +317,7 @@ int rascas_destroy(rascas_ctx* ctx) {
     cudaSetDevice(ctx->device);
     for (DevBuf* b : {&ctx->d_rec, &ctx->d_son, &ctx->d_nbr, &ctx->d_top, &ctx->d_spec, &ctx->d_pspec,
                       &ctx->d_pimg, &ctx->d_pcube, &ctx->d_counters, &ctx->d_params, &ctx->stage_in,
-                      &ctx->stage_out, &ctx->stage_aux, &ctx->stage_adj})
+                      &ctx->stage_out, &ctx->stage_aux, &ctx->stage_adj, &ctx->ray_init})
         b->release();
     auto& B = ctx->batch;
     for (DevBuf* b : {&B.d_rec, &B.d_son, &B.d_nbr, &B.d_top, &B.d_geo, &B.d_first, &B.d_pos, &B.d_dir, &B.d_nu,
@@ -402,6 +402,8 @@ int rascas_set_lines(rascas_ctx* ctx, const rascas_line* lines, int32_t nline, c
         double vp = std::sqrt(2.0 * kKB / L.mass_g);
         D.vth_pref = vp;
         D.invdnu_pref = kC / (L.nu0 * vp);
+        D.invdnu_h = (float)D.invdnu_pref;
+        D.invdnu_l = (float)(D.invdnu_pref - (double)D.invdnu_h);
         D.dnu_pref = L.nu0 * vp / kC;
         D.nu0_gap = lines[0].nu0 - L.nu0;
         D.a_pref = (float)(L.A_ul * kC / (4.0 * kPi * L.nu0 * vp));
@@ -734,8 +736,11 @@ int rascas_ray_tau(rascas_ctx* ctx, int64_t n, const double* pos, const double* 
         CK(cudaMemcpyAsync((void*)dnu, nu, N * 8, cudaMemcpyHostToDevice, st));
     }
     CK(cudaMemcpyAsync(ctx->d_params.p, &ctx->P, sizeof(Params), cudaMemcpyHostToDevice, st));
+    CK(ctx->ray_init.ensure(N * sizeof(rg::RayInit)));
+    CK(cudaMemsetAsync(ctx->P.head, 0, sizeof(unsigned long long), st));
     CK(rg::launch_ray_tau(ctx->P, (long long)n, dpos, ddir, dnu, dtau, dcells, dlens, cap,
-                          (mem == RASCAS_HOST || ncell) ? dncell : nullptr, st));
+                          (mem == RASCAS_HOST || ncell) ? dncell : nullptr, (rg::RayInit*)ctx->ray_init.p, ctx->sms,
+                          st));
     if (mem == RASCAS_HOST) {
         CK(cudaMemcpyAsync(tau, dtau, N * 8, cudaMemcpyDeviceToHost, st));
         if (ncell) CK(cudaMemcpyAsync(ncell, dncell, N * 4, cudaMemcpyDeviceToHost, st));

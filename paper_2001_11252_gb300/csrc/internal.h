@@ -33,6 +33,7 @@ struct LineDev {
     float nu0_f;
     double vth_pref;     // sqrt(2 k_B / m): v_th = vth_pref * sqrt(T)
     double invdnu_pref;  // c / nu0 / vth_pref: 1/Delta nu_D = invdnu_pref / sqrt(T)
+    float invdnu_h, invdnu_l;  // invdnu_pref as an FP32 pair (hi + lo)
     double dnu_pref;     // nu0 vth_pref / c: Delta nu_D = dnu_pref sqrt(T)
     double nu0_gap;      // nu0 of line 0 minus nu0 of this line
     float a_pref;        // A_ul / (4 pi nu0 / c * vth_pref): a = a_pref / sqrt(T)
@@ -138,9 +139,20 @@ struct TraceOut {
 // launchers (kernels.cu)
 cudaError_t launch_propagate(const Params& P, const PacketsIn& in, const PacketsOut& out,
                              const TraceOut& tr, int grid, int block, cudaStream_t st);
+// start state of one ray of rascas_ray_tau, written by a set-up pass
+struct RayInit {
+    double p[3], k[3], inv[3];
+    int w[6];              // leaf, oct, level, i, j, k; w[0] < 0: outside the box
+    float nu[2];           // nu_ext as an FP32 pair
+    float kp[3][2];        // direction as FP32 pairs
+    float d[kMaxLines][2]; // nu_ext - nu0_i as FP32 pairs
+};
+static_assert(sizeof(RayInit) % 16 == 0, "RayInit keeps 16-byte alignment");
+
+// init: scratch of n RayInit on the device
 cudaError_t launch_ray_tau(const Params& P, long long n, const double* pos, const double* dir,
-                           const double* nu, double* tau, int32_t* cells, double* lens, int cap,
-                           int32_t* ncell, cudaStream_t st);
+                           const double* nu, double* tau, int32_t* cells, double* lens, int cap, int32_t* ncell,
+                           RayInit* init, int sms, cudaStream_t st);
 cudaError_t launch_pack_fields(long long n, const float* nh, const float* vx, const float* vy, const float* vz,
                                const float* T, const float* nd, const float* nm, float4* rec, cudaStream_t st);
 cudaError_t launch_eval_voigt(long long n, const float* a, const double* x, float* H, cudaStream_t st);

@@ -13,6 +13,7 @@
 // lines and peeling directions are unrolled).  The peeling ray walk, which is
 // long and called from several places, is a separate function that reads the
 // problem description through a device-side copy of the parameters.
+#include <algorithm>
 #include <cstdint>
 #include <cuda_runtime.h>
 #include "device.cuh"
@@ -65,56 +66,89 @@ __device__ __forceinline__ void dir_from(float kx, float ky, float kz, float mu,
 }
 
 // ---------------------------------------------------------------------------
-// peeling ray: optical depth from p (in leaf w) along direction k to the
-// domain border at external frequency nu_ext; stops once tau > tau_stop.
-// G is the device-side copy of the parameters.
+// Optical depth along a ray (the peeling integral, Sect. 3.1 opacities summed
+// over the leaves of the walk of Sect. 4.3) from p in leaf w along k to the
+// domain border at external frequency nu_ext.  Per leaf: the record (32 B),
+// the FP32-pair opacity, the FP64 face distance, the integer neighbour
+// search; tau is summed as an FP32 pair.
 // ---------------------------------------------------------------------------
+template <int NL>
+struct Ray {
+    double p[3], k[3], inv[3];
+    Where w;
+    RayNu<NL> R;
+    f2 tau;
+    int n, zero_run;
+};
+
+template <int NL>
+__device__ __forceinline__ void ray_start(const Params& P, Ray<NL>& r, double p0, double p1, double p2, Where w,
+                                          double k0, double k1, double k2, double nu_ext) {
+    r.p[0] = p0; r.p[1] = p1; r.p[2] = p2;
+    r.k[0] = k0; r.k[1] = k1; r.k[2] = k2;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) r.inv[j] = is_zero(r.k[j]) ? 0.0 : __drcp_rn(r.k[j]);
+    r.w = w;
+    ray_nu<NL>(P, nu_ext, r.k, r.R);
+    r.tau = f2{0.0f, 0.0f};
+    r.n = 0;
+    r.zero_run = 0;
+}
+
+// one leaf of the walk; true when the ray is done (border, box edge, tau
+// beyond tstop, or a stuck walk)
+template <int NL>
+__device__ __forceinline__ bool ray_step(const Params& P, Ray<NL>& r, float tstop, int32_t* cells, double* lens,
+                                         int cap, uint32_t& sl, uint32_t& nl) {
+    const float4 r0 = __ldg(P.g.rec + 2 * r.w.leaf);
+    const float4 r1 = __ldg(P.g.rec + 2 * r.w.leaf + 1);
+    float kl[NL], xh[NL], xl[NL];
+    f2 beta;
+    const float kap = ray_opacity<NL>(P, r.R, r0, r1, kl, xh, xl, beta);
+    int axis;
+    const double tf = face_distance(r.p, r.k, r.inv, r.w, axis);
+    bool border = false;
+    double l = tf;
+    if (__float_as_int(r1.w) & kFlagBorder) {
+        const double tb = border_distance(P.g, r.p, r.k, r.inv);
+        border = order_key(tb) <= order_key(tf);
+        if (border) l = tb;
+    }
+    r.tau = f2_add_f(r.tau, kap * (float)l * P.g.box_cm_f);
+    if (cells != nullptr && r.n < cap) {
+        cells[r.n] = r.w.leaf;
+        lens[r.n] = l;
+    }
+    ++r.n;
+    if (border || r.tau.h > tstop) return true;
+    r.zero_run = order_key(tf) > 0 ? 0 : r.zero_run + 1;
+    if (r.zero_run > 64) return true;
+    move_to_face(r.p, r.k, axis, tf, r.w);
+    wrap_periodic(P.g, r.p, r.k);
+    return !next_leaf(P.g, r.p, r.k, axis, r.w, sl, nl);
+}
+
+__device__ __forceinline__ float tau_stop_f(double tau_stop) {
+    return tau_stop >= 3.0e38 ? __int_as_float(0x7f800000) : (float)tau_stop;
+}
+
+// peeling ray walked by one thread (G is the device-side parameter copy)
 template <int NL>
 __device__ __noinline__ double ray_walk(const Params* __restrict__ G, double p0, double p1, double p2,
                                         Where w, double k0, double k1, double k2, double nu_ext,
-                                        double tau_stop, Tallies* tl, int32_t* cells, double* lens, int cap,
-                                        int32_t* ncell) {
+                                        double tau_stop, Tallies* tl) {
     const Params& P = *G;
-    double p[3] = {p0, p1, p2};
-    const double k[3] = {k0, k1, k2};
-    const double inv[3] = {k0 != 0.0 ? __drcp_rn(k0) : 0.0, k1 != 0.0 ? __drcp_rn(k1) : 0.0,
-                           k2 != 0.0 ? __drcp_rn(k2) : 0.0};
-    double tau = 0.0;
-    int n = 0, zero_run = 0;
-    uint32_t sl = 0, nl = 0, ll = 0;
-    for (int guard = 0; guard < (1 << 26); ++guard) {
-        CellCache<NL> cc;
-        load_cell<NL>(P, P.g, w.leaf, cc);
-        ++ll;
-        double nu = to_gas(nu_ext, beta_of(cc, k));
-        float kl[NL];
-        float kap = opacity<NL>(P, cc, nu, kl);
-        int axis;
-        double tf = face_distance(p, k, inv, w, axis);
-        double tb = (cc.flags & kFlagBorder) ? border_distance(P.g, p, k, inv) : kInf;
-        bool border = tb <= tf;
-        double l = border ? tb : tf;
-        tau = __dadd_rn(tau, __dmul_rn(__dmul_rn((double)kap, l), P.g.box_cm));
-        if (cells != nullptr && n < cap) {
-            cells[n] = w.leaf;
-            lens[n] = l;
-        }
-        ++n;
-        if (border || tau > tau_stop) break;
-        zero_run = tf > 0.0 ? 0 : zero_run + 1;
-        if (zero_run > 64) break;
-        move_to_face(p, k, axis, tf, w);
-        wrap_periodic(P.g, p, k);
-        if (!next_leaf(P.g, p, k, axis, w, sl, nl)) break;
-    }
-    if (tl) {
-        tl->peel_cells += n;
-        tl->leaf_loads += ll;
-        tl->son_loads += sl;
-        tl->nbor_loads += nl;
-    }
-    if (ncell) *ncell = n;
-    return tau;
+    Ray<NL> r;
+    ray_start<NL>(P, r, p0, p1, p2, w, k0, k1, k2, nu_ext);
+    const float tstop = tau_stop_f(tau_stop);
+    uint32_t sl = 0, nl = 0;
+    for (int guard = 0; guard < (1 << 26); ++guard)
+        if (ray_step<NL>(P, r, tstop, nullptr, nullptr, 0, sl, nl)) break;
+    tl->peel_cells += r.n;
+    tl->leaf_loads += r.n;
+    tl->son_loads += sl;
+    tl->nbor_loads += nl;
+    return f2_val(r.tau);
 }
 
 // second walk of a peeling ray for the adjoint: for every leaf crossed,
@@ -126,53 +160,63 @@ __device__ __noinline__ void ray_grad(const Params* __restrict__ G, double p0, d
     const Params& P = *G;
     double p[3] = {p0, p1, p2};
     const double k[3] = {k0, k1, k2};
-    const double inv[3] = {k0 != 0.0 ? __drcp_rn(k0) : 0.0, k1 != 0.0 ? __drcp_rn(k1) : 0.0,
-                           k2 != 0.0 ? __drcp_rn(k2) : 0.0};
+    const double inv[3] = {is_zero(k0) ? 0.0 : __drcp_rn(k0), is_zero(k1) ? 0.0 : __drcp_rn(k1),
+                           is_zero(k2) ? 0.0 : __drcp_rn(k2)};
     const float kf[3] = {(float)k0, (float)k1, (float)k2};
+    RayNu<NL> R;
+    ray_nu<NL>(P, nu_ext, k, R);
+    const float Lb = P.g.box_cm_f;
     const long long nleaf = P.g.nleaf;
     uint32_t sl = 0, nl = 0;
     int zero_run = 0;
     for (int guard = 0; guard < (1 << 26); ++guard) {
-        CellCache<NL> cc;
-        load_cell<NL>(P, P.g, w.leaf, cc);
-        double b = beta_of(cc, k);
-        double nu = to_gas(nu_ext, b);
+        const float4 r0 = __ldg(P.g.rec + 2 * w.leaf);
+        const float4 r1 = __ldg(P.g.rec + 2 * w.leaf + 1);
+        float kl[NL], xh[NL], xl[NL];
+        f2 beta;
+        ray_opacity<NL>(P, R, r0, r1, kl, xh, xl, beta);
         int axis;
-        double tf = face_distance(p, k, inv, w, axis);
-        double tb = (cc.flags & kFlagBorder) ? border_distance(P.g, p, k, inv) : kInf;
-        bool border = tb <= tf;
-        double l = border ? tb : tf;
+        const double tf = face_distance(p, k, inv, w, axis);
+        bool border = false;
+        double l = tf;
+        if (__float_as_int(r1.w) & kFlagBorder) {
+            const double tb = border_distance(P.g, p, k, inv);
+            border = order_key(tb) <= order_key(tf);
+            if (border) l = tb;
+        }
         float dk[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, P.dust_sigma};
-        float4 r0 = __ldg(P.g.rec + 2 * w.leaf);
-        float4 r1 = __ldg(P.g.rec + 2 * w.leaf + 1);
         const float Tm = fmaxf(r1.x, 1e-30f);
         const float rs = rsqrtf(Tm);
+        // nu_gas = nu_ext (1 + s) with 1 + s = 1 / (1 + beta)
+        const float opb = 1.0f + beta.h;
+        const float nug = R.nu.h / opb;
 #pragma unroll
         for (int i = 0; i < NL; ++i) {
             const LineDev& L = P.line[i];
-            float x = (float)((nu - L.nu0) * cc.invdnu[i]);
+            const float a = L.a_pref * rs;
+            const float x = xh[i];
             float H, Ha, Hx;
-            voigt_derivs(cc.a[i], x, H, Ha, Hx);
-            float s0 = L.sig_pref * rs;
-            float nX = (L.dens == 1 ? r1.z : r0.x) * L.abund;
+            voigt_derivs(a, x, H, Ha, Hx);
+            const float s0 = L.sig_pref * rs;
+            const float nX = (L.dens == 1 ? r1.z : r0.x) * L.abund;
             if (L.dens != 1) dk[0] += L.abund * s0 * H;
             // x = (nu_ext / (1 + beta) - nu0) / dnu:  dx/dv_j = -(nu_gas / dnu) k_j / (c (1 + beta))
-            float dxdv = -(float)(nu * cc.invdnu[i]) / (float)(kC * (1.0 + b));
-            float t = nX * s0 * Hx * dxdv;
+            const float dxdv = -(nug * L.invdnu_h * rs) / ((float)kC * opb);
+            const float t = nX * s0 * Hx * dxdv;
             dk[1] += t * kf[0];
             dk[2] += t * kf[1];
             dk[3] += t * kf[2];
             // sigma0, a and x all scale as T^(-1/2)
-            dk[4] += nX * s0 * (-0.5f / Tm) * (H + cc.a[i] * Ha + x * Hx);
+            dk[4] += nX * s0 * (-0.5f / Tm) * (H + a * Ha + x * Hx);
         }
-        const float f = scale * (float)(P.g.box_cm * l);
+        const float f = scale * Lb * (float)l;
         if (f != 0.0f) {
 #pragma unroll
             for (int j = 0; j < 6; ++j)
                 if (dk[j] != 0.0f) atomicAdd(P.adj_grad + j * nleaf + w.leaf, f * dk[j]);
         }
         if (border) break;
-        zero_run = tf > 0.0 ? 0 : zero_run + 1;
+        zero_run = order_key(tf) > 0 ? 0 : zero_run + 1;
         if (zero_run > 64) break;
         move_to_face(p, k, axis, tf, w);
         wrap_periodic(P.g, p, k);
@@ -191,7 +235,7 @@ __device__ __noinline__ void peel_add(const Params* __restrict__ G, double p0, d
     double b = __fma_rn(k0, (double)vx, __fma_rn(k1, (double)vy, k2 * (double)vz)) * (1.0 / kC);
     double nu_ext = to_ext(nu_o_gas, b);
     ++tl->peel_rays;
-    double tau = ray_walk<NL>(G, p0, p1, p2, w, k0, k1, k2, nu_ext, P.tau_stop, tl, nullptr, nullptr, 0, nullptr);
+    double tau = ray_walk<NL>(G, p0, p1, p2, w, k0, k1, k2, nu_ext, P.tau_stop, tl);
     if (tau > P.tau_stop) return;
     float f = wt * expf(-(float)tau);
     const int nbin = P.g.nbin;
@@ -690,10 +734,13 @@ k_propagate(const __grid_constant__ Params P, PacketsIn in, PacketsOut out, Trac
 // ---------------------------------------------------------------------------
 // ray optical depths (peeling integral without cut-off) and probes
 // ---------------------------------------------------------------------------
+// Set-up of each ray: periodic wrap, the leaf holding the start point, 1/k
+// and the FP32-pair frequency constants (the FP64 work of a ray, done here
+// with every lane busy rather than by single lanes inside the walk)
 template <int NL>
-__global__ void k_ray_tau(const Params* __restrict__ G, long long n, const double* pos, const double* dir,
-                          const double* nu, double* tau, int32_t* cells, double* lens, int cap, int32_t* ncell) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_ray_prep(const Params* __restrict__ G, long long n, const double* pos, const double* dir,
+                           const double* nu, RayInit* init) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const Params& P = *G;
     double p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
@@ -701,14 +748,101 @@ __global__ void k_ray_tau(const Params* __restrict__ G, long long n, const doubl
     uint32_t loads = 0;
     wrap_periodic(P.g, p, k);
     Where w;
-    if (!locate_point(P.g, p, k, w, loads)) {
-        tau[i] = 0.0;
-        if (ncell) ncell[i] = 0;
-        return;
+    RayInit r;
+    if (!locate_point(P.g, p, k, w, loads)) w.leaf = -1, w.oct = w.level = w.i = w.j = w.k = 0;
+    RayNu<NL> R;
+    ray_nu<NL>(P, nu[i], k, R);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        r.p[j] = p[j];
+        r.k[j] = k[j];
+        r.inv[j] = is_zero(k[j]) ? 0.0 : __drcp_rn(k[j]);
+        r.kp[j][0] = R.k[j].h;
+        r.kp[j][1] = R.k[j].l;
     }
-    tau[i] = ray_walk<NL>(G, p[0], p[1], p[2], w, k[0], k[1], k[2], nu[i], kInf, nullptr,
-                          cells ? cells + i * cap : nullptr, lens ? lens + i * cap : nullptr, cap,
-                          ncell ? ncell + i : nullptr);
+    r.w[0] = w.leaf; r.w[1] = w.oct; r.w[2] = w.level; r.w[3] = w.i; r.w[4] = w.j; r.w[5] = w.k;
+    r.nu[0] = R.nu.h;
+    r.nu[1] = R.nu.l;
+#pragma unroll
+    for (int j = 0; j < kMaxLines; ++j) {
+        r.d[j][0] = j < NL ? R.d[j < NL ? j : 0].h : 0.0f;
+        r.d[j][1] = j < NL ? R.d[j < NL ? j : 0].l : 0.0f;
+    }
+    init[i] = r;
+}
+
+template <int NL>
+__device__ __forceinline__ void ray_load(const RayInit* __restrict__ in, long long i, Ray<NL>& r) {
+    const RayInit& q = in[i];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        r.p[j] = q.p[j];
+        r.k[j] = q.k[j];
+        r.inv[j] = q.inv[j];
+        r.R.k[j] = f2{q.kp[j][0], q.kp[j][1]};
+    }
+    r.w.leaf = q.w[0]; r.w.oct = q.w[1]; r.w.level = q.w[2]; r.w.i = q.w[3]; r.w.j = q.w[4]; r.w.k = q.w[5];
+    r.R.nu = f2{q.nu[0], q.nu[1]};
+#pragma unroll
+    for (int j = 0; j < NL; ++j) r.R.d[j] = f2{q.d[j][0], q.d[j][1]};
+    r.tau = f2{0.0f, 0.0f};
+    r.n = 0;
+    r.zero_run = 0;
+}
+
+// Persistent walk: each lane walks one ray leaf by leaf and takes the next ray
+// from the queue head as soon as its ray is done, so the lanes of a warp stay
+// busy whatever the spread of ray lengths.
+template <int NL>
+__global__ void __launch_bounds__(128) k_ray_tau(const Params* __restrict__ G, long long n,
+                                                 const RayInit* __restrict__ init, double* tau, int32_t* cells,
+                                                 double* lens, int cap, int32_t* ncell) {
+    const Params& P = *G;
+    const unsigned lane = threadIdx.x & 31u;
+    Ray<NL> r;
+    long long i = -1;
+    bool active = false, drained = false;
+    uint32_t sl = 0, nl = 0, steps = 0;
+    const float tstop = __int_as_float(0x7f800000);
+    for (;;) {
+        const bool want = !active && !drained;
+        const unsigned m = __ballot_sync(kFull, want);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            unsigned long long base = 0;
+            if ((int)lane == leader) base = atomicAdd(P.head, (unsigned long long)__popc(m));
+            base = __shfl_sync(kFull, base, leader);
+            if (want) {
+                i = (long long)base + __popc(m & ((1u << lane) - 1u));
+                if (i < n) {
+                    ray_load<NL>(init, i, r);
+                    if (r.w.leaf >= 0) {
+                        steps = 0;
+                        active = true;
+                    } else {
+                        tau[i] = 0.0;
+                        if (ncell) ncell[i] = 0;
+                    }
+                } else {
+                    drained = true;
+                }
+            }
+        }
+        if (!__any_sync(kFull, active)) {
+            if (__all_sync(kFull, drained)) break;
+            continue;
+        }
+        if (active) {
+            bool done = ray_step<NL>(P, r, tstop, cells ? cells + i * cap : nullptr, lens ? lens + i * cap : nullptr,
+                                     cap, sl, nl);
+            if (++steps >= (1u << 26)) done = true;
+            if (done) {
+                tau[i] = f2_val(r.tau);
+                if (ncell) ncell[i] = r.n;
+                active = false;
+            }
+        }
+    }
 }
 
 __global__ void k_pack_fields(long long n, const float* nh, const float* vx, const float* vy, const float* vz,
@@ -795,17 +929,36 @@ cudaError_t launch_propagate(const Params& P, const PacketsIn& in, const Packets
     }
 }
 
+template <int NL>
+static int ray_occ() {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ray_tau<NL>, 128, 0);
+    return nb > 0 ? nb : 1;
+}
+
+// the queue head P.head must be zero on entry
 cudaError_t launch_ray_tau(const Params& P, long long n, const double* pos, const double* dir, const double* nu,
-                           double* tau, int32_t* cells, double* lens, int cap, int32_t* ncell, cudaStream_t st) {
+                           double* tau, int32_t* cells, double* lens, int cap, int32_t* ncell, RayInit* init,
+                           int sms, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    int block = 128;
-    unsigned grid = (unsigned)((n + block - 1) / block);
+    const int block = 128;
+    const int per_sm = P.nline == 1 ? ray_occ<1>() : P.nline == 2 ? ray_occ<2>() : P.nline == 3 ? ray_occ<3>()
+                                                                                               : ray_occ<4>();
+    const long long need = (n + block - 1) / block;
+    const unsigned grid = (unsigned)std::min<long long>(need, (long long)sms * per_sm);
+    const unsigned gp = (unsigned)need;
     const Params* G = P.self;
     switch (P.nline) {
-        case 1: k_ray_tau<1><<<grid, block, 0, st>>>(G, n, pos, dir, nu, tau, cells, lens, cap, ncell); break;
-        case 2: k_ray_tau<2><<<grid, block, 0, st>>>(G, n, pos, dir, nu, tau, cells, lens, cap, ncell); break;
-        case 3: k_ray_tau<3><<<grid, block, 0, st>>>(G, n, pos, dir, nu, tau, cells, lens, cap, ncell); break;
-        case 4: k_ray_tau<4><<<grid, block, 0, st>>>(G, n, pos, dir, nu, tau, cells, lens, cap, ncell); break;
+#define RG_RAY(NLV)                                                                          \
+    case NLV:                                                                                \
+        k_ray_prep<NLV><<<gp, block, 0, st>>>(G, n, pos, dir, nu, init);                     \
+        k_ray_tau<NLV><<<grid, block, 0, st>>>(G, n, init, tau, cells, lens, cap, ncell);    \
+        break;
+        RG_RAY(1)
+        RG_RAY(2)
+        RG_RAY(3)
+        RG_RAY(4)
+#undef RG_RAY
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
