@@ -202,14 +202,24 @@ int rascas_set_physics(rascas_ctx *ctx, const rascas_physics *phys);
 /* Also zeroes the tallies (their shapes follow the detector). */
 int rascas_set_detector(rascas_ctx *ctx, const rascas_detector *det);
 int rascas_zero_tallies(rascas_ctx *ctx);
+/* Capacity, in 64-byte records, of the device buffer of peeling rays (one per
+ * emission or scattering and observer direction, Sect. 3.1 peeling) that the
+ * scattering kernel appends and the peel kernel then walks and tallies.  When
+ * it fills, the packets in flight are parked in device memory and resumed
+ * once the records are walked: results do not depend on the capacity, only
+ * the number of rounds does.  Default 2^23 records (512 MiB); a value below
+ * the floor set by the launch shape (a few resident-thread multiples) is
+ * raised to it.  RASCAS_E_ARG if records < 1. */
+int rascas_set_peel_capacity(rascas_ctx *ctx, int64_t records);
 
 /* ---- the hot path -------------------------------------------------------- */
 
 /* Propagate n packets until each escapes, is absorbed or is capped, peeling
  * at emission and at every scattering when the detector has directions.
  * Tallies accumulate across calls.  in/out pointers follow `mem`; out may be
- * NULL; stats may be NULL (then the call does not synchronise when
- * mem == RASCAS_DEVICE). */
+ * NULL; stats may be NULL (then, without peeling, the call does not
+ * synchronise when mem == RASCAS_DEVICE; with peeling it synchronises once per
+ * round of the peeling-ray buffer, see rascas_set_peel_capacity). */
 int rascas_propagate(rascas_ctx *ctx, const rascas_packets_in *in, int64_t n,
                      const rascas_packets_out *out, int mem, rascas_run_stats *stats);
 

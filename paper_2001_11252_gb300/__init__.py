@@ -10,7 +10,7 @@ below are handed to the library as raw device pointers on the current torch
 stream; numpy arrays are passed as host buffers.
 """
 from ._native import (  # noqa: F401
-    Context, Stats, Event, lib, library_path,
+    Context, Stats, Event, RascasError, lib, library_path,
     TALLY_SPECTRUM, TALLY_PEEL_SPECTRA, TALLY_PEEL_IMAGES, TALLY_PEEL_CUBES,
     PK_ACTIVE, PK_ESCAPED, PK_ABSORBED, PK_CAPPED, PK_ERROR,
     DOMAIN_SPHERE, DOMAIN_SLAB, DOMAIN_CUBE, BATCH_PERSISTENT, BATCH_PER_MODEL,

@@ -121,6 +121,7 @@ def lib():
             "rascas_set_physics": [vp, C.POINTER(Physics)],
             "rascas_set_detector": [vp, C.POINTER(Detector)],
             "rascas_zero_tallies": [vp],
+            "rascas_set_peel_capacity": [vp, i64],
             "rascas_propagate": [vp, C.POINTER(PacketsIn), i64, C.POINTER(PacketsOut), C.c_int, C.POINTER(Stats)],
             "rascas_get_tally": [vp, C.c_int, vp, C.c_size_t, C.c_int],
             "rascas_ray_tau": [vp, i64, vp, vp, vp, vp, vp, vp, i32, vp, C.c_int],
@@ -278,6 +279,9 @@ class Context:
 
     def zero_tallies(self):
         self._ck(self._L.rascas_zero_tallies(self._h), "zero_tallies")
+
+    def set_peel_capacity(self, records):
+        self._ck(self._L.rascas_set_peel_capacity(self._h, int(records)), "set_peel_capacity")
 
     def setup(self, wl):
         """Load a workload description (medium, domain, lines, dust, physics,

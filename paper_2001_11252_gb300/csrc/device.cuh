@@ -119,6 +119,14 @@ struct Rng {
         float v = fmaf(__uint2float_rn(ma), 0x1p-26f, (__uint2float_rn(mb) + 0.5f) * 0x1p-52f);
         return hi ? -log1pf(-v) : -logf(v);
     }
+    // refill the ring after the packet state was restored from memory
+    __device__ __forceinline__ void resume() {
+        avail = n & ~3u;
+        if (n & 3u) {
+            put(avail, philox_block(avail >> 2, id0, id1, k0, k1));
+            avail += 4u;
+        }
+    }
     // stream of packet pid, next draw `start`
     __device__ void init(const Params& P, uint64_t pid, uint32_t start = 0) {
         k0 = P.key0; k1 = P.key1;

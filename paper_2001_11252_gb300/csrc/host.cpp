@@ -24,6 +24,8 @@ constexpr double kH = 6.62607015e-27;
 constexpr double kME = 9.1093837015e-28;
 constexpr double kE = 4.803204712570263e-10;
 constexpr double kPi = 3.14159265358979323846;
+// peeling records per round of deferred peeling (64 B each)
+constexpr unsigned long long kPeelCap = 1ull << 23;
 
 struct DevBuf {
     void* p = nullptr;
@@ -72,6 +74,8 @@ struct rascas_ctx {
     Params P{};
     DevBuf d_spec, d_pspec, d_pimg, d_pcube, d_counters, d_params;
     DevBuf stage_in, stage_out, stage_aux, stage_adj, ray_init;
+    DevBuf peel_rec, peel_save, peel_flag, peel_ctl;   // deferred peeling
+    unsigned long long peel_cap = kPeelCap;
     // batch of independent models
     struct Batch {
         int nmodels = 0, nbin = 0, nline_at_load = 0;
@@ -317,7 +321,8 @@ int rascas_destroy(rascas_ctx* ctx) {
     cudaSetDevice(ctx->device);
     for (DevBuf* b : {&ctx->d_rec, &ctx->d_son, &ctx->d_nbr, &ctx->d_top, &ctx->d_spec, &ctx->d_pspec,
                       &ctx->d_pimg, &ctx->d_pcube, &ctx->d_counters, &ctx->d_params, &ctx->stage_in,
-                      &ctx->stage_out, &ctx->stage_aux, &ctx->stage_adj, &ctx->ray_init})
+                      &ctx->stage_out, &ctx->stage_aux, &ctx->stage_adj, &ctx->ray_init, &ctx->peel_rec,
+                      &ctx->peel_save, &ctx->peel_flag, &ctx->peel_ctl})
         b->release();
     auto& B = ctx->batch;
     for (DevBuf* b : {&B.d_rec, &B.d_son, &B.d_nbr, &B.d_top, &B.d_geo, &B.d_first, &B.d_pos, &B.d_dir, &B.d_nu,
@@ -479,7 +484,13 @@ int rascas_set_detector(rascas_ctx* ctx, const rascas_detector* d) {
         if (!(n2 > 0)) return fail(ctx, RASCAS_E_ARG, "detector: zero direction");
         double nn = std::sqrt(n2);
         double n[3] = {d->dirs[i][0] / nn, d->dirs[i][1] / nn, d->dirs[i][2] / nn};
-        for (int ax = 0; ax < 3; ++ax) P.dirs[i][ax] = n[ax];
+        for (int ax = 0; ax < 3; ++ax) {
+            P.dirs[i][ax] = n[ax];
+            // 1/k correctly rounded, as the walk's face distances need it
+            P.dir_inv[i][ax] = n[ax] != 0.0 ? 1.0 / n[ax] : 0.0;
+            P.dir_kp[i][ax][0] = (float)n[ax];
+            P.dir_kp[i][ax][1] = (float)(n[ax] - (double)(float)n[ax]);
+        }
         // image plane basis: Duff et al. (2017)
         double sg = std::copysign(1.0, n[2]);
         double a = -1.0 / (sg + n[2]);
@@ -502,6 +513,12 @@ int rascas_set_detector(rascas_ctx* ctx, const rascas_detector* d) {
     P.pcube = P.cube ? (float*)ctx->d_pcube.p : nullptr;
     ctx->has_det = true;
     return rascas_zero_tallies(ctx);
+}
+
+int rascas_set_peel_capacity(rascas_ctx* ctx, int64_t records) {
+    if (!ctx || records < 1) return fail(ctx, RASCAS_E_ARG, "set_peel_capacity: records must be >= 1");
+    ctx->peel_cap = (unsigned long long)records;
+    return RASCAS_OK;
 }
 
 int rascas_zero_tallies(rascas_ctx* ctx) {
@@ -617,10 +634,44 @@ int run_propagate(rascas_ctx* ctx, const rascas_packets_in* in, int64_t n, const
         CK(cudaEventCreate(&e1));
         CK(cudaEventRecord(e0, st));
     }
-    CK(cudaMemcpyAsync(ctx->d_params.p, &P, sizeof(Params), cudaMemcpyHostToDevice, st));
-    if (n > 0) {
-        int grid = persistent_grid(ctx, P.ndir > 0);
-        CK(rg::launch_propagate(P, din, dout, tr, grid, rg::propagate_block_size(), st));
+    if (n > 0 && P.ndir > 0) {
+        // deferred peeling: rounds of (scattering kernel appending peeling
+        // rays, peel kernel walking them) until no packet was parked
+        const int grid = persistent_grid(ctx, true), block = rg::propagate_block_size();
+        const size_t threads = (size_t)grid * block;
+        const unsigned long long margin = (unsigned long long)threads * (2 * P.ndir + 1) + 4096;
+        const unsigned long long cap = std::max<unsigned long long>(ctx->peel_cap, 4 * margin);
+        CK(ctx->peel_rec.ensure(cap * sizeof(rg::PeelRec)));
+        CK(ctx->peel_save.ensure(threads * rg::packet_save_bytes(P.nline)));
+        CK(ctx->peel_flag.ensure(threads * sizeof(int)));
+        CK(ctx->peel_ctl.ensure(4 * sizeof(unsigned long long)));
+        unsigned long long* ctl = (unsigned long long*)ctx->peel_ctl.p;
+        P.peel_rec = (rg::PeelRec*)ctx->peel_rec.p;
+        P.peel_count = ctl;
+        P.peel_head = ctl + 1;
+        P.suspended = (unsigned int*)(ctl + 2);
+        P.peel_cap = cap;
+        P.peel_hw = cap - margin;
+        P.save = ctx->peel_save.p;
+        P.save_flag = (int*)ctx->peel_flag.p;
+        CK(cudaMemsetAsync(P.save_flag, 0, threads * sizeof(int), st));
+        CK(cudaMemcpyAsync(ctx->d_params.p, &P, sizeof(Params), cudaMemcpyHostToDevice, st));
+        for (long long round = 0;; ++round) {
+            CK(cudaMemsetAsync(ctl, 0, 4 * sizeof(unsigned long long), st));
+            CK(rg::launch_propagate(P, din, dout, tr, grid, block, st));
+            CK(rg::launch_peel(P, ctx->sms, st));
+            unsigned int parked = 0;
+            CK(cudaMemcpyAsync(&parked, P.suspended, sizeof(parked), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (parked == 0) break;
+            if (round > (1LL << 30)) return fail(ctx, RASCAS_E_STATE, "propagate: peeling rounds do not end");
+        }
+    } else {
+        CK(cudaMemcpyAsync(ctx->d_params.p, &P, sizeof(Params), cudaMemcpyHostToDevice, st));
+        if (n > 0) {
+            int grid = persistent_grid(ctx, false);
+            CK(rg::launch_propagate(P, din, dout, tr, grid, rg::propagate_block_size(), st));
+        }
     }
     if (stats) CK(cudaEventRecord(e1, st));
     if (mem == RASCAS_HOST && n > 0) {

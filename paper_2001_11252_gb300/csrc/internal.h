@@ -69,6 +69,17 @@ struct Geo {
     float* spec;
 };
 
+// one peeling ray (Sect. 3.1 peeling): written by the scattering kernel at an
+// emission or a scattering, walked and tallied by the peel kernel
+struct PeelRec {
+    double p[3];       // event position (box units)
+    double nu_ext;     // external-frame frequency towards the observer (Hz)
+    int w[6];          // leaf, oct, level, i, j, k of the event's leaf
+    float wt;          // weight per sr
+    int d;             // observer direction
+};
+static_assert(sizeof(PeelRec) == 64, "PeelRec is one 64-byte record");
+
 struct Params {
     const Params* self;    // device-side copy of these parameters (read by the peeling walk)
     Geo g;                 // the medium of a single-model run
@@ -101,6 +112,19 @@ struct Params {
     const float* adj_g_img;    // dL/dimage [ndir][npix][npix] (or null)
     const float* adj_g_spec;   // dL/dspectrum [ndir][nbin] (or null)
     float* adj_grad;           // [6][nleaf]: n_HI, vx, vy, vz, T, n_dust
+    // deferred peeling: the scattering kernel appends PeelRec records; a warp
+    // whose reservation starts at or past peel_hw suspends its packets (state
+    // to save[], flag in save_flag[], one slot per thread of the launch) so
+    // that the peel kernel can drain the records before the next round
+    PeelRec* peel_rec;
+    unsigned long long* peel_count;   // records appended this round
+    unsigned long long* peel_head;    // queue head of the peel kernel
+    unsigned long long peel_cap, peel_hw;
+    void* save;
+    int* save_flag;
+    unsigned int* suspended;          // warps suspended this round
+    double dir_inv[kMaxDirs][3];      // 1 / dirs (0 where a component is 0)
+    float dir_kp[kMaxDirs][3][2];     // dirs as FP32 pairs
     // run scratch
     unsigned long long* counters;  // [CNT_N]
     unsigned long long* head;      // work-queue head
@@ -150,6 +174,12 @@ struct RayInit {
 static_assert(sizeof(RayInit) % 16 == 0, "RayInit keeps 16-byte alignment");
 
 // init: scratch of n RayInit on the device
+// deferred peeling: walk and tally the records of one round (reads the
+// record count from P.peel_count; P.peel_head must be zero on entry)
+cudaError_t launch_peel(const Params& P, int sms, cudaStream_t st);
+// bytes of one suspended packet state for nline lines
+size_t packet_save_bytes(int nline);
+
 cudaError_t launch_ray_tau(const Params& P, long long n, const double* pos, const double* dir,
                            const double* nu, double* tau, int32_t* cells, double* lens, int cap, int32_t* ncell,
                            RayInit* init, int sms, cudaStream_t st);

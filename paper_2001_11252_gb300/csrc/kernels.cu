@@ -47,6 +47,7 @@ struct Packet {
     float budget;          // path length guaranteed to stay inside the leaf
     int status, zero_run;
     bool tau_fresh, enter, fresh, inv_ok;
+    bool halt;             // the peel record buffer passed its high-water mark: suspend
     CellCache<NL> cc;
 };
 
@@ -132,143 +133,91 @@ __device__ __forceinline__ float tau_stop_f(double tau_stop) {
     return tau_stop >= 3.0e38 ? __int_as_float(0x7f800000) : (float)tau_stop;
 }
 
-// peeling ray walked by one thread (G is the device-side parameter copy)
+// adjoint walk of one leaf: grad[j][leaf] += scale L l d kappa / d theta_j
+// (Sect. 3.1 opacities differentiated in n_HI, v, T and n_dust); true when
+// the ray is done
 template <int NL>
-__device__ __noinline__ double ray_walk(const Params* __restrict__ G, double p0, double p1, double p2,
-                                        Where w, double k0, double k1, double k2, double nu_ext,
-                                        double tau_stop, Tallies* tl) {
-    const Params& P = *G;
-    Ray<NL> r;
-    ray_start<NL>(P, r, p0, p1, p2, w, k0, k1, k2, nu_ext);
-    const float tstop = tau_stop_f(tau_stop);
-    uint32_t sl = 0, nl = 0;
-    for (int guard = 0; guard < (1 << 26); ++guard)
-        if (ray_step<NL>(P, r, tstop, nullptr, nullptr, 0, sl, nl)) break;
-    tl->peel_cells += r.n;
-    tl->leaf_loads += r.n;
-    tl->son_loads += sl;
-    tl->nbor_loads += nl;
-    return f2_val(r.tau);
+__device__ __forceinline__ bool ray_grad_step(const Params& P, Ray<NL>& r, float scale, uint32_t& sl, uint32_t& nl) {
+    const float4 r0 = __ldg(P.g.rec + 2 * r.w.leaf);
+    const float4 r1 = __ldg(P.g.rec + 2 * r.w.leaf + 1);
+    float kl[NL], xh[NL], xl[NL];
+    f2 beta;
+    ray_opacity<NL>(P, r.R, r0, r1, kl, xh, xl, beta);
+    int axis;
+    const double tf = face_distance(r.p, r.k, r.inv, r.w, axis);
+    bool border = false;
+    double l = tf;
+    if (__float_as_int(r1.w) & kFlagBorder) {
+        const double tb = border_distance(P.g, r.p, r.k, r.inv);
+        border = order_key(tb) <= order_key(tf);
+        if (border) l = tb;
+    }
+    float dk[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, P.dust_sigma};
+    const float Tm = fmaxf(r1.x, 1e-30f);
+    const float rs = rsqrtf(Tm);
+    // nu_gas = nu_ext / (1 + beta)
+    const float opb = 1.0f + beta.h;
+    const float nug = r.R.nu.h / opb;
+    const float kf[3] = {r.R.k[0].h, r.R.k[1].h, r.R.k[2].h};
+#pragma unroll
+    for (int i = 0; i < NL; ++i) {
+        const LineDev& L = P.line[i];
+        const float a = L.a_pref * rs;
+        const float x = xh[i];
+        float H, Ha, Hx;
+        voigt_derivs(a, x, H, Ha, Hx);
+        const float s0 = L.sig_pref * rs;
+        const float nX = (L.dens == 1 ? r1.z : r0.x) * L.abund;
+        if (L.dens != 1) dk[0] += L.abund * s0 * H;
+        // x = (nu_ext / (1 + beta) - nu0) / dnu:  dx/dv_j = -(nu_gas / dnu) k_j / (c (1 + beta))
+        const float dxdv = -(nug * L.invdnu_h * rs) / ((float)kC * opb);
+        const float t = nX * s0 * Hx * dxdv;
+        dk[1] += t * kf[0];
+        dk[2] += t * kf[1];
+        dk[3] += t * kf[2];
+        // sigma0, a and x all scale as T^(-1/2)
+        dk[4] += nX * s0 * (-0.5f / Tm) * (H + a * Ha + x * Hx);
+    }
+    const float f = scale * P.g.box_cm_f * (float)l;
+    if (f != 0.0f) {
+        const long long nleaf = P.g.nleaf;
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+            if (dk[j] != 0.0f) atomicAdd(P.adj_grad + j * nleaf + r.w.leaf, f * dk[j]);
+    }
+    if (border) return true;
+    r.zero_run = order_key(tf) > 0 ? 0 : r.zero_run + 1;
+    if (r.zero_run > 64) return true;
+    move_to_face(r.p, r.k, axis, tf, r.w);
+    wrap_periodic(P.g, r.p, r.k);
+    return !next_leaf(P.g, r.p, r.k, axis, r.w, sl, nl);
 }
 
-// second walk of a peeling ray for the adjoint: for every leaf crossed,
-// grad[j][leaf] += scale * L * l * d kappa / d theta_j (Sect. 3.1 opacities
-// differentiated in n_HI, v, T and n_dust)
+// one peeling ray towards direction d (weight wt per sr, gas-frame frequency
+// nu_o_gas in the event's leaf), appended to the record buffer for the peel
+// kernel; one atomic per converged group of lanes.  A reservation at or past
+// the high-water mark asks the packet's warp to suspend.
 template <int NL>
-__device__ __noinline__ void ray_grad(const Params* __restrict__ G, double p0, double p1, double p2, Where w,
-                                      double k0, double k1, double k2, double nu_ext, float scale) {
-    const Params& P = *G;
-    double p[3] = {p0, p1, p2};
-    const double k[3] = {k0, k1, k2};
-    const double inv[3] = {is_zero(k0) ? 0.0 : __drcp_rn(k0), is_zero(k1) ? 0.0 : __drcp_rn(k1),
-                           is_zero(k2) ? 0.0 : __drcp_rn(k2)};
-    const float kf[3] = {(float)k0, (float)k1, (float)k2};
-    RayNu<NL> R;
-    ray_nu<NL>(P, nu_ext, k, R);
-    const float Lb = P.g.box_cm_f;
-    const long long nleaf = P.g.nleaf;
-    uint32_t sl = 0, nl = 0;
-    int zero_run = 0;
-    for (int guard = 0; guard < (1 << 26); ++guard) {
-        const float4 r0 = __ldg(P.g.rec + 2 * w.leaf);
-        const float4 r1 = __ldg(P.g.rec + 2 * w.leaf + 1);
-        float kl[NL], xh[NL], xl[NL];
-        f2 beta;
-        ray_opacity<NL>(P, R, r0, r1, kl, xh, xl, beta);
-        int axis;
-        const double tf = face_distance(p, k, inv, w, axis);
-        bool border = false;
-        double l = tf;
-        if (__float_as_int(r1.w) & kFlagBorder) {
-            const double tb = border_distance(P.g, p, k, inv);
-            border = order_key(tb) <= order_key(tf);
-            if (border) l = tb;
-        }
-        float dk[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, P.dust_sigma};
-        const float Tm = fmaxf(r1.x, 1e-30f);
-        const float rs = rsqrtf(Tm);
-        // nu_gas = nu_ext (1 + s) with 1 + s = 1 / (1 + beta)
-        const float opb = 1.0f + beta.h;
-        const float nug = R.nu.h / opb;
-#pragma unroll
-        for (int i = 0; i < NL; ++i) {
-            const LineDev& L = P.line[i];
-            const float a = L.a_pref * rs;
-            const float x = xh[i];
-            float H, Ha, Hx;
-            voigt_derivs(a, x, H, Ha, Hx);
-            const float s0 = L.sig_pref * rs;
-            const float nX = (L.dens == 1 ? r1.z : r0.x) * L.abund;
-            if (L.dens != 1) dk[0] += L.abund * s0 * H;
-            // x = (nu_ext / (1 + beta) - nu0) / dnu:  dx/dv_j = -(nu_gas / dnu) k_j / (c (1 + beta))
-            const float dxdv = -(nug * L.invdnu_h * rs) / ((float)kC * opb);
-            const float t = nX * s0 * Hx * dxdv;
-            dk[1] += t * kf[0];
-            dk[2] += t * kf[1];
-            dk[3] += t * kf[2];
-            // sigma0, a and x all scale as T^(-1/2)
-            dk[4] += nX * s0 * (-0.5f / Tm) * (H + a * Ha + x * Hx);
-        }
-        const float f = scale * Lb * (float)l;
-        if (f != 0.0f) {
-#pragma unroll
-            for (int j = 0; j < 6; ++j)
-                if (dk[j] != 0.0f) atomicAdd(P.adj_grad + j * nleaf + w.leaf, f * dk[j]);
-        }
-        if (border) break;
-        zero_run = order_key(tf) > 0 ? 0 : zero_run + 1;
-        if (zero_run > 64) break;
-        move_to_face(p, k, axis, tf, w);
-        wrap_periodic(P.g, p, k);
-        if (!next_leaf(P.g, p, k, axis, w, sl, nl)) break;
-    }
-}
-
-// one peeled contribution towards direction d (weight w per sr, gas-frame
-// frequency nu_o_gas of the event's leaf) into spectra, images and cubes
-template <int NL>
-__device__ __noinline__ void peel_add(const Params* __restrict__ G, double p0, double p1, double p2, Where w,
-                                      float vx, float vy, float vz, int d, float wt, double nu_o_gas,
-                                      Tallies* tl) {
-    const Params& P = *G;
-    const double k0 = P.dirs[d][0], k1 = P.dirs[d][1], k2 = P.dirs[d][2];
-    double b = __fma_rn(k0, (double)vx, __fma_rn(k1, (double)vy, k2 * (double)vz)) * (1.0 / kC);
-    double nu_ext = to_ext(nu_o_gas, b);
-    ++tl->peel_rays;
-    double tau = ray_walk<NL>(G, p0, p1, p2, w, k0, k1, k2, nu_ext, P.tau_stop, tl);
-    if (tau > P.tau_stop) return;
-    float f = wt * expf(-(float)tau);
-    const int nbin = P.g.nbin;
-    double t = __dmul_rn(__dsub_rn(nu_ext, P.g.nu_lo), P.g.nu_inv_range);
-    double fb = floor(t * (double)nbin);
-    bool chok = fb >= 0.0 && fb < (double)nbin;
-    int ch = chok ? (int)fb : 0;
-    long long px = -1;
-    const long long npix2 = (long long)P.npix * P.npix;
-    if (P.npix > 0) {
-        double r0 = p0 - P.img_c[0], r1 = p1 - P.img_c[1], r2 = p2 - P.img_c[2];
-        double u = r0 * P.eu[d][0] + r1 * P.eu[d][1] + r2 * P.eu[d][2];
-        double v = r0 * P.ev[d][0] + r1 * P.ev[d][1] + r2 * P.ev[d][2];
-        double fu = floor((u * P.inv_fov + 0.5) * (double)P.npix);
-        double fv = floor((v * P.inv_fov + 0.5) * (double)P.npix);
-        if (fu >= 0.0 && fu < (double)P.npix && fv >= 0.0 && fv < (double)P.npix)
-            px = (long long)fv * P.npix + (long long)fu;
-    }
-    if (P.adj_grad != nullptr) {
-        // adjoint: dL/dtheta_c = -G w exp(-tau) d tau / d theta_c, with G the
-        // gradient of the loss at this event's channel and pixel
-        float Gs = 0.0f;
-        if (chok && P.adj_g_spec) Gs += __ldg(P.adj_g_spec + d * nbin + ch);
-        if (px >= 0 && P.adj_g_img) Gs += __ldg(P.adj_g_img + d * npix2 + px);
-        if (px >= 0 && chok && P.cube && P.adj_g_cube) Gs += __ldg(P.adj_g_cube + (d * npix2 + px) * nbin + ch);
-        if (Gs != 0.0f && f != 0.0f) ray_grad<NL>(G, p0, p1, p2, w, k0, k1, k2, nu_ext, -Gs * f);
-        return;
-    }
-    if (chok) atomicAdd(P.pspec + d * nbin + ch, f);
-    if (px >= 0) {
-        atomicAdd(P.pimg + d * npix2 + px, f);
-        if (chok && P.cube) atomicAdd(P.pcube + (d * npix2 + px) * nbin + ch, f);
-    }
+__device__ __forceinline__ void peel_emit(const Params& P, Packet<NL>& s, int d, float wt, double nu_o_gas,
+                                          Tallies& tl) {
+    const double b = __fma_rn(P.dirs[d][0], (double)s.cc.vx,
+                              __fma_rn(P.dirs[d][1], (double)s.cc.vy, P.dirs[d][2] * (double)s.cc.vz)) * (1.0 / kC);
+    const double nu_ext = to_ext(nu_o_gas, b);
+    const unsigned m = __activemask();
+    const int lane = (int)(threadIdx.x & 31u), leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(P.peel_count, (unsigned long long)__popc(m));
+    base = __shfl_sync(m, base, leader);
+    const unsigned long long slot = base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
+    if (base >= P.peel_hw) s.halt = true;
+    ++tl.peel_rays;
+    if (slot >= P.peel_cap) return;   // cannot happen: peel_hw leaves room for every resident thread
+    PeelRec& r = P.peel_rec[slot];
+    r.p[0] = s.p0; r.p[1] = s.p1; r.p[2] = s.p2;
+    r.nu_ext = nu_ext;
+    r.w[0] = s.w.leaf; r.w[1] = s.w.oct; r.w[2] = s.w.level; r.w[3] = s.w.i; r.w[4] = s.w.j; r.w[5] = s.w.k;
+    r.wt = wt;
+    r.d = d;
 }
 
 // ---------------------------------------------------------------------------
@@ -291,7 +240,7 @@ __device__ __forceinline__ void scatter_dust(const Params& P, Packet<NL>& s, Tal
             if (d < P.ndir) {
                 float muo = s.kx * (float)P.dirs[d][0] + s.ky * (float)P.dirs[d][1] + s.kz * (float)P.dirs[d][2];
                 float wt = phase_p(PH_HG, muo, P.dust_g) * (1.0f / kTwoPiF);
-                peel_add<NL>(P.self, s.p0, s.p1, s.p2, s.w, s.cc.vx, s.cc.vy, s.cc.vz, d, wt, nu_gas, &tl);
+                peel_emit<NL>(P, s, d, wt, nu_gas, tl);
             }
         }
     }
@@ -395,7 +344,7 @@ __device__ __forceinline__ void scatter_line(const Params& P, Packet<NL>& s, flo
                     nu_o = __fma_rn(nu_in, (double)f, nu_in);
                 }
                 float wt = phase_p(kind, muo, 0.0f) * (1.0f / kTwoPiF);
-                peel_add<NL>(P.self, s.p0, s.p1, s.p2, s.w, s.cc.vx, s.cc.vy, s.cc.vz, d, wt, nu_o, &tl);
+                peel_emit<NL>(P, s, d, wt, nu_o, tl);
             }
         }
     }
@@ -462,6 +411,7 @@ __device__ __forceinline__ void begin_packet(const Params& P, const Geo& G, cons
     s.status = RASCAS_PK_ACTIVE_;
     s.enter = true;
     s.fresh = true;
+    s.halt = false;
     wrap_periodic(G, p, k);
     s.p0 = p[0]; s.p1 = p[1]; s.p2 = p[2];
     if (!locate_point(G, p, k, s.w, tl.son_loads)) {
@@ -522,8 +472,7 @@ __device__ __forceinline__ void advance(const Params& P, const Geo& G, Packet<NL
 #pragma unroll
             for (int d = 0; d < kMaxDirs; ++d)
                 if (d < P.ndir)
-                    peel_add<NL>(P.self, s.p0, s.p1, s.p2, s.w, s.cc.vx, s.cc.vy, s.cc.vz, d,
-                                 1.0f / (2.0f * kTwoPiF), nu_gas, &tl);
+                    peel_emit<NL>(P, s, d, 1.0f / (2.0f * kTwoPiF), nu_gas, tl);
         }
         s.fresh = false;
     }
@@ -679,7 +628,28 @@ k_propagate(const __grid_constant__ Params P, PacketsIn in, PacketsOut out, Trac
     const unsigned lane = threadIdx.x & 31u;
     bool have = false, drained = false;
     s.mi = 0;
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (PEEL && P.save_flag[gt]) {
+        // a packet suspended by the previous round of this launch shape
+        s = static_cast<const Packet<NL>*>(P.save)[gt];
+        s.rng.resume();
+        s.cc.u0mask = 0u;
+        s.halt = false;
+        P.save_flag[gt] = 0;
+        have = true;
+    }
     for (;;) {
+        if (PEEL && __any_sync(kFull, have && s.halt)) {
+            // the record buffer is nearly full: park this warp's packets for
+            // the next round, after the peel kernel has drained the records
+            if (have) {
+                s.halt = false;
+                static_cast<Packet<NL>*>(P.save)[gt] = s;
+                P.save_flag[gt] = 1;
+            }
+            if (lane == 0) atomicAdd(P.suspended, 1u);
+            break;
+        }
         bool want = !have && !drained;
         unsigned m = __ballot_sync(kFull, want);
         if (m) {
@@ -845,6 +815,139 @@ __global__ void __launch_bounds__(128) k_ray_tau(const Params* __restrict__ G, l
     }
 }
 
+// ---------------------------------------------------------------------------
+// Deferred peeling (Sect. 3.1 peeling; adjoint of the peeled optical depths):
+// each lane walks one record's ray leaf by leaf and takes the next record as
+// soon as its ray is done.  Forward: w exp(-tau) into the spectrum, image and
+// cube bins of the record.  Adjoint (P.adj_grad set): the ray is walked a
+// second time with the scale -G w exp(-tau), G the loss gradient at those bins.
+// ---------------------------------------------------------------------------
+template <int NL>
+__device__ __forceinline__ void ray_from_rec(const Params& P, const PeelRec& q, Ray<NL>& r) {
+    const int d = q.d;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        r.p[j] = q.p[j];
+        r.k[j] = P.dirs[d][j];
+        r.inv[j] = P.dir_inv[d][j];
+        r.R.k[j] = f2{P.dir_kp[d][j][0], P.dir_kp[d][j][1]};
+    }
+    r.w.leaf = q.w[0]; r.w.oct = q.w[1]; r.w.level = q.w[2]; r.w.i = q.w[3]; r.w.j = q.w[4]; r.w.k = q.w[5];
+    r.R.nu = f2_of(q.nu_ext);
+#pragma unroll
+    for (int i = 0; i < NL; ++i) r.R.d[i] = f2_of(q.nu_ext - P.line[i].nu0);
+    r.tau = f2{0.0f, 0.0f};
+    r.n = 0;
+    r.zero_run = 0;
+}
+
+// spectrum channel (or -1) and image pixel (or -1) of a peeled contribution
+__device__ __forceinline__ void peel_bins(const Params& P, const PeelRec& q, int& ch, long long& px) {
+    const int nbin = P.g.nbin;
+    const double t = __dmul_rn(__dsub_rn(q.nu_ext, P.g.nu_lo), P.g.nu_inv_range);
+    const double fb = floor(t * (double)nbin);
+    ch = (fb >= 0.0 && fb < (double)nbin) ? (int)fb : -1;
+    px = -1;
+    if (P.npix > 0) {
+        const int d = q.d;
+        const double r0 = q.p[0] - P.img_c[0], r1 = q.p[1] - P.img_c[1], r2 = q.p[2] - P.img_c[2];
+        const double u = r0 * P.eu[d][0] + r1 * P.eu[d][1] + r2 * P.eu[d][2];
+        const double v = r0 * P.ev[d][0] + r1 * P.ev[d][1] + r2 * P.ev[d][2];
+        const double fu = floor((u * P.inv_fov + 0.5) * (double)P.npix);
+        const double fv = floor((v * P.inv_fov + 0.5) * (double)P.npix);
+        if (fu >= 0.0 && fu < (double)P.npix && fv >= 0.0 && fv < (double)P.npix)
+            px = (long long)fv * P.npix + (long long)fu;
+    }
+}
+
+template <int NL>
+__global__ void __launch_bounds__(128) k_peel(const Params* __restrict__ G) {
+    const Params& P = *G;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned long long cnt = *P.peel_count;
+    const unsigned long long n = cnt < P.peel_cap ? cnt : P.peel_cap;
+    const float tstop = tau_stop_f(P.tau_stop);
+    const bool adj = P.adj_grad != nullptr;
+    const long long npix2 = (long long)P.npix * P.npix;
+    Ray<NL> r;
+    PeelRec q;
+    unsigned long long i = 0;
+    bool active = false, drained = false;
+    int phase = 0;           // 0: optical depth, 1: adjoint walk
+    float scale = 0.0f;
+    uint32_t sl = 0, nl = 0, steps = 0, cells = 0;
+    for (;;) {
+        const bool want = !active && !drained;
+        const unsigned m = __ballot_sync(kFull, want);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            unsigned long long base = 0;
+            if ((int)lane == leader) base = atomicAdd(P.peel_head, (unsigned long long)__popc(m));
+            base = __shfl_sync(kFull, base, leader);
+            if (want) {
+                i = base + __popc(m & ((1u << lane) - 1u));
+                if (i < n) {
+                    q = P.peel_rec[i];
+                    ray_from_rec<NL>(P, q, r);
+                    phase = 0;
+                    steps = 0;
+                    active = true;
+                } else {
+                    drained = true;
+                }
+            }
+        }
+        if (!__any_sync(kFull, active)) {
+            if (__all_sync(kFull, drained)) break;
+            continue;
+        }
+        if (active) {
+            bool done;
+            if (phase == 0) done = ray_step<NL>(P, r, tstop, nullptr, nullptr, 0, sl, nl);
+            else done = ray_grad_step<NL>(P, r, scale, sl, nl);
+            if (++steps >= (1u << 26)) done = true;
+            if (done && phase == 0) {
+                cells += r.n;
+                active = false;
+                const double tau = f2_val(r.tau);
+                if (tau <= P.tau_stop) {
+                    const float f = q.wt * expf(-(float)tau);
+                    int ch;
+                    long long px;
+                    peel_bins(P, q, ch, px);
+                    const int nbin = P.g.nbin, d = q.d;
+                    if (adj) {
+                        float Gs = 0.0f;
+                        if (ch >= 0 && P.adj_g_spec) Gs += __ldg(P.adj_g_spec + d * nbin + ch);
+                        if (px >= 0 && P.adj_g_img) Gs += __ldg(P.adj_g_img + d * npix2 + px);
+                        if (px >= 0 && ch >= 0 && P.cube && P.adj_g_cube)
+                            Gs += __ldg(P.adj_g_cube + (d * npix2 + px) * nbin + ch);
+                        if (Gs != 0.0f && f != 0.0f) {
+                            ray_from_rec<NL>(P, q, r);
+                            scale = -Gs * f;
+                            phase = 1;
+                            steps = 0;
+                            active = true;
+                        }
+                    } else {
+                        if (ch >= 0) atomicAdd(P.pspec + d * nbin + ch, f);
+                        if (px >= 0) {
+                            atomicAdd(P.pimg + d * npix2 + px, f);
+                            if (ch >= 0 && P.cube) atomicAdd(P.pcube + (d * npix2 + px) * nbin + ch, f);
+                        }
+                    }
+                }
+            } else if (done) {
+                active = false;
+            }
+        }
+    }
+    flush(P, cells, CNT_PEEL_CELLS);
+    flush(P, cells, CNT_LEAF_LOADS);
+    flush(P, sl, CNT_SON_LOADS);
+    flush(P, nl, CNT_NBOR_LOADS);
+}
+
 __global__ void k_pack_fields(long long n, const float* nh, const float* vx, const float* vy, const float* vz,
                               const float* T, const float* nd, const float* nm, float4* rec) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -934,6 +1037,34 @@ static int ray_occ() {
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ray_tau<NL>, 128, 0);
     return nb > 0 ? nb : 1;
+}
+
+template <int NL>
+static int peel_occ() {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_peel<NL>, 128, 0);
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_peel(const Params& P, int sms, cudaStream_t st) {
+    const Params* G = P.self;
+    switch (P.nline) {
+        case 1: k_peel<1><<<sms * peel_occ<1>(), 128, 0, st>>>(G); break;
+        case 2: k_peel<2><<<sms * peel_occ<2>(), 128, 0, st>>>(G); break;
+        case 3: k_peel<3><<<sms * peel_occ<3>(), 128, 0, st>>>(G); break;
+        case 4: k_peel<4><<<sms * peel_occ<4>(), 128, 0, st>>>(G); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+size_t packet_save_bytes(int nline) {
+    switch (nline) {
+        case 1: return sizeof(Packet<1>);
+        case 2: return sizeof(Packet<2>);
+        case 3: return sizeof(Packet<3>);
+        default: return sizeof(Packet<4>);
+    }
 }
 
 // the queue head P.head must be zero on entry
