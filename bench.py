@@ -44,9 +44,9 @@ ISSUE_PEAK_NOTE = "152 SMs x 4 schedulers x 1 warp-instruction/clock x SM clock"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--packets", type=int, default=1 << 16)
+    ap.add_argument("--packets", type=int, default=1 << 18)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -58,7 +58,7 @@ def parse():
                     help="scatterings per packet cap in the batch comparison")
     ap.add_argument("--galaxy", type=int, default=1, help="run the synthetic-galaxy section (1) or not (0)")
     ap.add_argument("--galaxy-rays", type=int, default=1 << 20)
-    ap.add_argument("--galaxy-packets", type=int, default=1 << 15)
+    ap.add_argument("--galaxy-packets", type=int, default=1 << 18)
     ap.add_argument("--galaxy-cap", type=int, default=64, help="scatterings per packet in the galaxy section")
     ap.add_argument("--galaxy-thin", type=float, default=1e-8,
                     help="density scale of the lower-column copy of the galaxy used for peeling and its adjoint")

@@ -24,16 +24,21 @@ namespace rg {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr double kInf = __builtin_huge_val();
 
+// per-thread event counters of the transport kernel, kept in shared memory
+// (they are touched rarely; registers are the scarce resource there): 15
+// words per thread so that the lanes of a warp fall in distinct banks
 struct Tallies {
     uint32_t cross, peel_rays, peel_cells, trials, leaf_loads, son_loads, nbor_loads;
     uint32_t scatt_line, scatt_dust;
+    uint32_t pk, esc, abs, cap, err;
+    uint32_t pad;
 };
+static_assert(sizeof(Tallies) == 15 * 4, "odd word stride");
 
 template <int NL>
 struct Packet {
     double p0, p1, p2;     // position (box units)
     double kd0, kd1, kd2;  // direction used by the FP64 geometry (the sampled FP32 one, or the exact input)
-    double i0, i1, i2;     // 1/k per axis (valid when inv_ok)
     double tau;            // optical depth left to the next interaction (formed from tauf when tau_fresh)
     double path;           // distance travelled (box units)
     double nu_enter;       // external-frame frequency when the packet entered its leaf
@@ -46,7 +51,7 @@ struct Packet {
     float tauf;            // FP32 copy of tau
     float budget;          // path length guaranteed to stay inside the leaf
     int status, zero_run;
-    bool tau_fresh, enter, fresh, inv_ok;
+    bool tau_fresh, enter, fresh;
     bool halt;             // the peel record buffer passed its high-water mark: suspend
     CellCache<NL> cc;
 };
@@ -247,7 +252,6 @@ __device__ __forceinline__ void scatter_dust(const Params& P, Packet<NL>& s, Tal
     if (!P.keep_dir) {
         dir_from(s.kx, s.ky, s.kz, mu, st, r_phi, s.kx, s.ky, s.kz);
         s.kd0 = (double)s.kx; s.kd1 = (double)s.ky; s.kd2 = (double)s.kz;
-        s.inv_ok = false;
     }
     ++tl.scatt_dust;
 }
@@ -361,7 +365,6 @@ __device__ __forceinline__ void scatter_line(const Params& P, Packet<NL>& s, flo
     if (!P.keep_dir) {
         s.kx = ox; s.ky = oy; s.kz = oz;
         s.kd0 = (double)ox; s.kd1 = (double)oy; s.kd2 = (double)oz;
-        s.inv_ok = false;
     }
     ++tl.scatt_line;
 }
@@ -406,7 +409,6 @@ __device__ __forceinline__ void begin_packet(const Params& P, const Geo& G, cons
     s.nsteps = 0;
     s.path = 0.0;
     s.budget = 0.0f;
-    s.inv_ok = false;
     s.zero_run = 0;
     s.status = RASCAS_PK_ACTIVE_;
     s.enter = true;
@@ -428,8 +430,7 @@ __device__ __forceinline__ void begin_packet(const Params& P, const Geo& G, cons
 
 template <int NL>
 __device__ __forceinline__ void finish_packet(const Params& P, const Geo& G, const Packet<NL>& s, const PacketsOut& out,
-                                              uint32_t& c_pk, uint32_t& c_esc, uint32_t& c_abs, uint32_t& c_cap,
-                                              uint32_t& c_err) {
+                                              Tallies& tl) {
     double nu_ext = nu_ext_now<NL>(P, s);
     long long i = s.idx;
     if (out.status) out.status[i] = s.status;
@@ -438,11 +439,11 @@ __device__ __forceinline__ void finish_packet(const Params& P, const Geo& G, con
     if (out.path) out.path[i] = s.path;
     if (out.pos) { out.pos[3 * i] = s.p0; out.pos[3 * i + 1] = s.p1; out.pos[3 * i + 2] = s.p2; }
     if (out.dir) { out.dir[3 * i] = s.kd0; out.dir[3 * i + 1] = s.kd1; out.dir[3 * i + 2] = s.kd2; }
-    ++c_pk;
-    c_esc += s.status == RASCAS_PK_ESCAPED_;
-    c_abs += s.status == RASCAS_PK_ABSORBED_;
-    c_cap += s.status == RASCAS_PK_CAPPED_;
-    c_err += s.status == RASCAS_PK_ERROR_;
+    ++tl.pk;
+    tl.esc += s.status == RASCAS_PK_ESCAPED_;
+    tl.abs += s.status == RASCAS_PK_ABSORBED_;
+    tl.cap += s.status == RASCAS_PK_CAPPED_;
+    tl.err += s.status == RASCAS_PK_ERROR_;
     if (s.status == RASCAS_PK_ESCAPED_ && G.spec != nullptr) {
         double t = __dmul_rn(__dsub_rn(nu_ext, G.nu_lo), G.nu_inv_range);
         double fb = floor(t * (double)G.nbin);
@@ -502,14 +503,11 @@ __device__ __forceinline__ void advance(const Params& P, const Geo& G, Packet<NL
                 s.tau_fresh = false;
             }
             const double k[3] = {s.kd0, s.kd1, s.kd2};
-            if (!s.inv_ok) {
-                s.i0 = k[0] != 0.0 ? __drcp_rn(k[0]) : 0.0;
-                s.i1 = k[1] != 0.0 ? __drcp_rn(k[1]) : 0.0;
-                s.i2 = k[2] != 0.0 ? __drcp_rn(k[2]) : 0.0;
-                s.inv_ok = true;
-            }
+            // 1/k (the direction changes at almost every scattering, so it
+            // is formed here rather than kept)
+            const double inv[3] = {is_zero(k[0]) ? 0.0 : __drcp_rn(k[0]), is_zero(k[1]) ? 0.0 : __drcp_rn(k[1]),
+                                   is_zero(k[2]) ? 0.0 : __drcp_rn(k[2])};
             double p[3] = {s.p0, s.p1, s.p2};
-            const double inv[3] = {s.i0, s.i1, s.i2};
             int axis;
             double tf = face_distance(p, k, inv, s.w, axis);
             double tb = border_leaf ? border_distance(G, p, k, inv) : kInf;
@@ -620,11 +618,12 @@ __device__ __forceinline__ int model_of(const Params& P, long long idx) {
 }
 
 template <int NL, bool PEEL, bool BATCH>
-__global__ void __launch_bounds__(128, PEEL ? 2 : 4)
+__global__ void __launch_bounds__(128, 4)
 k_propagate(const __grid_constant__ Params P, PacketsIn in, PacketsOut out, TraceOut tr) {
     Packet<NL> s;
-    Tallies tl = {};
-    uint32_t c_pk = 0, c_esc = 0, c_abs = 0, c_cap = 0, c_err = 0;
+    extern __shared__ uint32_t s_dyn[];
+    Tallies& tl = reinterpret_cast<Tallies*>(s_dyn + (kRing + 6 * NL) * blockDim.x)[threadIdx.x];
+    tl = Tallies{};
     const unsigned lane = threadIdx.x & 31u;
     bool have = false, drained = false;
     s.mi = 0;
@@ -680,16 +679,16 @@ k_propagate(const __grid_constant__ Params P, PacketsIn in, PacketsOut out, Trac
             const Geo& G = BATCH ? P.models[s.mi] : P.g;
             if (s.status == RASCAS_PK_ACTIVE_) advance<NL, PEEL>(P, G, s, tl, tr);
             if (s.status != RASCAS_PK_ACTIVE_) {
-                finish_packet<NL>(P, G, s, out, c_pk, c_esc, c_abs, c_cap, c_err);
+                finish_packet<NL>(P, G, s, out, tl);
                 have = false;
             }
         }
     }
-    flush(P, c_pk, CNT_PACKETS);
-    flush(P, c_esc, CNT_ESCAPED);
-    flush(P, c_abs, CNT_ABSORBED);
-    flush(P, c_cap, CNT_CAPPED);
-    flush(P, c_err, CNT_ERRORS);
+    flush(P, tl.pk, CNT_PACKETS);
+    flush(P, tl.esc, CNT_ESCAPED);
+    flush(P, tl.abs, CNT_ABSORBED);
+    flush(P, tl.cap, CNT_CAPPED);
+    flush(P, tl.err, CNT_ERRORS);
     flush(P, tl.scatt_line, CNT_SCATT_LINE);
     flush(P, tl.scatt_dust, CNT_SCATT_DUST);
     flush(P, tl.cross, CNT_CROSS);
@@ -988,8 +987,10 @@ __global__ void k_sample_upar(Params P, long long n, const double* x, const floa
 // ---------------------------------------------------------------------------
 int propagate_block_size() { return 128; }
 
-// draw rings, then the u0 coefficient cache of each line
-size_t propagate_smem(int nline, int block) { return (size_t)(kRing + nline * 6) * block * sizeof(float); }
+// draw rings, the u0 coefficient cache of each line, the event counters
+size_t propagate_smem(int nline, int block) {
+    return (size_t)(kRing + nline * 6) * block * sizeof(float) + (size_t)block * sizeof(Tallies);
+}
 
 template <int NL, bool PEEL, bool BATCH>
 static int occ(int block) {
