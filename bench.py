@@ -36,8 +36,14 @@ WORKLOAD = ("static H I + dust sphere: 8^3 root refined to 64^3-equivalent octre
             "tau0=1e6 centre-to-edge, T=1e4 K, tau_dust=1, albedo 0.32, packets from the centre at x=0")
 # warp instructions executed per scattering by k_propagate on this workload:
 # smsp__inst_executed.sum / scatterings of one ncu capture (65536 packets capped
-# at 1e4 scatterings each, profiles/k_propagate_sphere_tau1e6.md)
-INST_PER_SCATT = 58313234500 / (65536 * 9767.794143676758)
+# at 1e4 scatterings each, profiles/k_propagate_sphere_tau1e6.md), and the
+# active lanes per warp instruction of the same capture
+INST_PER_SCATT = 36008436139 / 640142157
+LANES_PER_INST = 19.12
+# DRAM bytes per leaf visit of k_ray_tau on the synthetic galaxy
+# (dram__bytes_read.sum + dram__bytes_write.sum of one capture of 2^18 rays,
+# 59 732 805 leaf visits, profiles/k_ray_tau_galaxy.md)
+RAY_DRAM_BYTES_PER_VISIT = (3.987451e9 + 16.796928e6) / 59732805
 ISSUE_PEAK_NOTE = "152 SMs x 4 schedulers x 1 warp-instruction/clock x SM clock"
 
 
@@ -246,8 +252,11 @@ def run_galaxy(args, peaks):
     out["ray_cast"] = {"rays": n, "cells": cells, "ms": ms, "rays_per_s": n / (ms * 1e-3),
                        "cells_per_s": cells / (ms * 1e-3),
                        "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
-                                    "frac": alg / (ms * 1e-3) / 1e9 / hbm, "traffic": None,
-                                    "note": "28 algorithmic bytes per leaf visit; peak = measured copy bandwidth"}}
+                                    "frac": alg / (ms * 1e-3) / 1e9 / hbm,
+                                    "traffic": RAY_DRAM_BYTES_PER_VISIT * cells,
+                                    "note": "28 algorithmic bytes per leaf visit; peak = measured copy bandwidth; "
+                                            "traffic = DRAM bytes per leaf visit of a 2^18-ray ncu capture x the "
+                                            "visits of this launch"}}
     # (b) propagation with peeling, (c) adjoint
     m = args.galaxy_packets
     pk = wl.packets
@@ -426,9 +435,14 @@ def main():
     roof = None
     if INST_PER_SCATT:
         ach = INST_PER_SCATT * scatt / (t_ms * 1e-3) / 1e9
+        lane_peak = 152 * 128 * sm_mhz * 1e6 / 1e12   # T lane-instructions / s
+        lane_ach = INST_PER_SCATT * LANES_PER_INST * scatt / (t_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": issue_peak, "unit": "Gwarp-inst/s",
                 "frac": ach / issue_peak, "traffic": None,
-                "peak_note": ISSUE_PEAK_NOTE + " (median SM clock under load %.0f MHz)" % sm_mhz}
+                "peak_note": ISSUE_PEAK_NOTE + " (median SM clock under load %.0f MHz)" % sm_mhz,
+                "lanes": {"achieved": lane_ach, "peak": lane_peak, "unit": "Tlane-inst/s", "frac": lane_ach / lane_peak,
+                          "note": "the same count x %.2f active lanes per warp instruction, against 152 SMs x 128 "
+                                  "lanes x SM clock: divergence shows here" % LANES_PER_INST}}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": issue_peak, "unit": "Gwarp-inst/s", "frac": None,
                 "traffic": None, "peak_note": ISSUE_PEAK_NOTE}
