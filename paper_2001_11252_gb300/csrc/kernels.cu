@@ -56,10 +56,10 @@ struct Packet {
     CellCache<NL> cc;
 };
 
-__device__ __forceinline__ void dir_from(float kx, float ky, float kz, float mu, float st, float r_phi,
-                                         float& ox, float& oy, float& oz) {
-    float3 e1, e2;
-    onb(kx, ky, kz, e1, e2);
+// k_out = mu k + sin(theta) (cos(phi) e1 + sin(phi) e2), phi = 2 pi r_phi, for an
+// orthonormal basis (e1, e2) of the plane perpendicular to k
+__device__ __forceinline__ void dir_from_basis(float kx, float ky, float kz, const float3& e1, const float3& e2,
+                                               float mu, float st, float r_phi, float& ox, float& oy, float& oz) {
     float sn, cs;
     sincospif(2.0f * r_phi, &sn, &cs);
     float x = mu * kx + st * (cs * e1.x + sn * e2.x);
@@ -69,6 +69,13 @@ __device__ __forceinline__ void dir_from(float kx, float ky, float kz, float mu,
     ox = x * nn;
     oy = y * nn;
     oz = z * nn;
+}
+
+__device__ __forceinline__ void dir_from(float kx, float ky, float kz, float mu, float st, float r_phi,
+                                         float& ox, float& oy, float& oz) {
+    float3 e1, e2;
+    onb(kx, ky, kz, e1, e2);
+    dir_from_basis(kx, ky, kz, e1, e2, mu, st, r_phi, ox, oy, oz);
 }
 
 // ---------------------------------------------------------------------------
@@ -327,7 +334,7 @@ __device__ __forceinline__ void scatter_line(const Params& P, Packet<NL>& s, flo
     float mu = mu_sample(kind, r_mu, 0.0f, st);
     float ox = kx, oy = ky, oz = kz;
     if (P.keep_dir) mu = 1.0f;
-    else dir_from(kx, ky, kz, mu, st, r_phi, ox, oy, oz);
+    else dir_from_basis(kx, ky, kz, e1, e2, mu, st, r_phi, ox, oy, oz);
     const float vthc = s.cc.vth_c[IL];
     // recoil term (1 - mu) h nu / (m c^2) of Eq. (nuout_nuin)
     const float recp = P.recoil ? L.recoil_pref * (P.line[0].nu0_f + s.xh * s.cc.dnu0_f) : 0.0f;
@@ -395,7 +402,7 @@ __device__ __forceinline__ double nu_ext_now(const Params& P, const Packet<NL>& 
 
 // packet start: read the initial condition, key its random stream, find its
 // leaf, draw its first tau_event (Sect. 2: PPIC lists; Sect. 3)
-template <int NL>
+template <int NL, bool TRACE>
 __device__ __forceinline__ void begin_packet(const Params& P, const Geo& G, const PacketsIn& in, long long idx,
                                              Packet<NL>& s, Tallies& tl, const TraceOut& tr) {
     s.idx = idx;
@@ -421,7 +428,7 @@ __device__ __forceinline__ void begin_packet(const Params& P, const Geo& G, cons
         s.enter = false;
         s.w.leaf = -1; s.w.oct = 0; s.w.level = 0; s.w.i = s.w.j = s.w.k = 0;
     }
-    if (tr.nev) trace_record<NL>(s, tr, s.nu_enter);
+    if (TRACE && tr.nev) trace_record<NL>(s, tr, s.nu_enter);
     if (s.status == RASCAS_PK_ACTIVE_) {
         s.tauf = s.rng.tau_event();
         s.tau_fresh = true;
@@ -455,7 +462,7 @@ __device__ __forceinline__ void finish_packet(const Params& P, const Geo& G, con
 // walk step -- an interaction inside the leaf, a face crossing, or the
 // escape through the domain border (Sect. 3, Sect. 4.3).  Each phase appears
 // once, so the loop body stays small for the instruction cache.
-template <int NL, bool PEEL>
+template <int NL, bool PEEL, bool TRACE>
 __device__ __forceinline__ void advance(const Params& P, const Geo& G, Packet<NL>& s, Tallies& tl,
                                         const TraceOut& tr) {
     bool evt = false;
@@ -590,14 +597,14 @@ __device__ __forceinline__ void advance(const Params& P, const Geo& G, Packet<NL
             }
             evt = true;
             if (s.status == RASCAS_PK_ACTIVE_) {
-                if (tr.nev) trace_record<NL>(s, tr, nu_ext_now<NL>(P, s));
+                if (TRACE && tr.nev) trace_record<NL>(s, tr, nu_ext_now<NL>(P, s));
                 evt = false;
                 s.tauf = s.rng.tau_event();
                 s.tau_fresh = true;
             }
         }
     }
-    if (evt && tr.nev) trace_record<NL>(s, tr, nu_ext_now<NL>(P, s));
+    if (TRACE && evt && tr.nev) trace_record<NL>(s, tr, nu_ext_now<NL>(P, s));
 }
 
 __device__ __forceinline__ void flush(const Params& P, unsigned long long v, int which) {
@@ -617,7 +624,7 @@ __device__ __forceinline__ int model_of(const Params& P, long long idx) {
     return lo;
 }
 
-template <int NL, bool PEEL, bool BATCH>
+template <int NL, bool PEEL, bool BATCH, bool TRACE>
 __global__ void __launch_bounds__(128, 4)
 k_propagate(const __grid_constant__ Params P, PacketsIn in, PacketsOut out, TraceOut tr) {
     Packet<NL> s;
@@ -661,9 +668,9 @@ k_propagate(const __grid_constant__ Params P, PacketsIn in, PacketsOut out, Trac
                 if (idx < in.n) {
                     if constexpr (BATCH) {
                         s.mi = model_of(P, idx);
-                        begin_packet<NL>(P, P.models[s.mi], in, idx, s, tl, tr);
+                        begin_packet<NL, TRACE>(P, P.models[s.mi], in, idx, s, tl, tr);
                     } else {
-                        begin_packet<NL>(P, P.g, in, idx, s, tl, tr);
+                        begin_packet<NL, TRACE>(P, P.g, in, idx, s, tl, tr);
                     }
                     have = true;
                 } else {
@@ -677,7 +684,7 @@ k_propagate(const __grid_constant__ Params P, PacketsIn in, PacketsOut out, Trac
         }
         if (have) {
             const Geo& G = BATCH ? P.models[s.mi] : P.g;
-            if (s.status == RASCAS_PK_ACTIVE_) advance<NL, PEEL>(P, G, s, tl, tr);
+            if (s.status == RASCAS_PK_ACTIVE_) advance<NL, PEEL, TRACE>(P, G, s, tl, tr);
             if (s.status != RASCAS_PK_ACTIVE_) {
                 finish_packet<NL>(P, G, s, out, tl);
                 have = false;
@@ -995,7 +1002,8 @@ size_t propagate_smem(int nline, int block) {
 template <int NL, bool PEEL, bool BATCH>
 static int occ(int block) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate<NL, PEEL, BATCH>, block, propagate_smem(NL, block));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate<NL, PEEL, BATCH, false>, block,
+                                                  propagate_smem(NL, block));
     return nb;
 }
 
@@ -1016,9 +1024,12 @@ template <int NL>
 static cudaError_t launch_nl(const Params& P, const PacketsIn& in, const PacketsOut& out, const TraceOut& tr,
                              int grid, int block, cudaStream_t st) {
     size_t smem = propagate_smem(NL, block);
-    if (P.nmodels > 0) k_propagate<NL, false, true><<<grid, block, smem, st>>>(P, in, out, tr);
-    else if (P.ndir > 0) k_propagate<NL, true, false><<<grid, block, smem, st>>>(P, in, out, tr);
-    else k_propagate<NL, false, false><<<grid, block, smem, st>>>(P, in, out, tr);
+    // per-event traces are recorded by single-model runs without peeling only
+    if (tr.nev && (P.nmodels > 0 || P.ndir > 0)) return cudaErrorInvalidValue;
+    if (P.nmodels > 0) k_propagate<NL, false, true, false><<<grid, block, smem, st>>>(P, in, out, tr);
+    else if (P.ndir > 0) k_propagate<NL, true, false, false><<<grid, block, smem, st>>>(P, in, out, tr);
+    else if (tr.nev) k_propagate<NL, false, false, true><<<grid, block, smem, st>>>(P, in, out, tr);
+    else k_propagate<NL, false, false, false><<<grid, block, smem, st>>>(P, in, out, tr);
     return cudaGetLastError();
 }
 
