@@ -150,10 +150,10 @@ __device__ __forceinline__ float voigt_h(float a, double x) {
     float x2 = (float)x2d;
     float lo = (float)(x2d - (double)x2);
     float e = expf(-x2) * (1.0f - lo);
-    float z = (x2 - 0.855f) / (x2 + 3.42f);
+    float z = __fdividef(x2 - 0.855f, x2 + 3.42f);
     float q = 0.0f;
     if (z > 0.0f) {
-        q = z * (1.0f + 21.0f / x2) * a / (kPiF * (x2 + 1.0f)) *
+        q = z * (1.0f + __fdividef(21.0f, x2)) * __fdividef(a, kPiF * (x2 + 1.0f)) *
             (0.1117f + z * (4.421f + z * (-9.207f + 5.674f * z)));
     }
     return kSqrtPiF * q + e;
@@ -165,10 +165,10 @@ __device__ __forceinline__ float voigt_h2(float a, float xh, float xl) {
     float x2 = xh * xh;
     float lo = fmaf(xh, xh, -x2) + 2.0f * xh * xl;
     float e = expf(-x2) * (1.0f - lo);
-    float z = (x2 - 0.855f) / (x2 + 3.42f);
+    float z = __fdividef(x2 - 0.855f, x2 + 3.42f);
     float q = 0.0f;
     if (z > 0.0f) {
-        q = z * (1.0f + 21.0f / x2) * a / (kPiF * (x2 + 1.0f)) *
+        q = z * (1.0f + __fdividef(21.0f, x2)) * __fdividef(a, kPiF * (x2 + 1.0f)) *
             (0.1117f + z * (4.421f + z * (-9.207f + 5.674f * z)));
     }
     return kSqrtPiF * q + e;
@@ -257,26 +257,27 @@ __device__ __forceinline__ float sample_upar(Rng& rng, float x, float a, const U
         return sg * (1.0f / xa + sqrtf(-logf(r1)) * cospif(2.0f * r2));
     }
     float u0 = u0_eval(u0c, xa);
-    float t = (u0 - xa) / a;
+    float t = __fdividef(u0 - xa, a);
     float A, B;
     if (t < 0.0f) {
-        A = atanf(-1.0f / t);
+        A = atanf(__fdividef(-1.0f, t));
         B = kPiF - A;
     } else if (t > 0.0f) {
-        B = atanf(1.0f / t);
+        B = atanf(__fdividef(1.0f, t));
         A = kPiF - B;
     } else {
         A = B = 0.5f * kPiF;
     }
     float e0 = expf(-u0 * u0);
-    float p = A / (A + e0 * B);
+    float p = __fdividef(A, A + e0 * B);
     float u0sq = u0 * u0;
     for (uint32_t n = 0; n < (1u << 22); ++n) {
         float r1 = rng.u23(), r2 = rng.u23(), r3 = rng.u23();
         ++trials;
         const bool b1 = r1 <= p;
         float tn = tanf(b1 ? A * r2 : B * (1.0f - r2));
-        float u = b1 ? xa - a / tn : xa + a / tn;
+        const float q = __fdividef(a, tn);
+        float u = b1 ? xa - q : xa + q;
         float lim = b1 ? 0.0f : u0sq;
         if (r3 <= expf(lim - u * u)) return sg * u;
     }
@@ -306,12 +307,12 @@ __device__ __forceinline__ float mu_sample(int kind, float r, float g, float& st
         const float c1 = core ? 14.0f : 6.0f, c2 = core ? 24.0f : 8.0f;
         if (mu < 0.0f) {
             float v = fmaxf(0.0f, 1.0f + mu);
-            v = c2 * r / (v * v - 3.0f * v + c1);
+            v = __fdividef(c2 * r, v * v - 3.0f * v + c1);
             st = sqrtf(fmaxf(0.0f, v * (2.0f - v)));
             return v - 1.0f;
         }
         float w = fmaxf(0.0f, 1.0f - mu);
-        w = c2 * (1.0f - r) / (w * w - 3.0f * w + c1);
+        w = __fdividef(c2 * (1.0f - r), w * w - 3.0f * w + c1);
         st = sqrtf(fmaxf(0.0f, w * (2.0f - w)));
         return 1.0f - w;
     }
@@ -343,7 +344,7 @@ __device__ __forceinline__ float phase_p(int kind, float mu, float g) {
 // orthonormal basis (b1, b2) perpendicular to unit n: Duff et al. (2017)
 __device__ __forceinline__ void onb(float nx, float ny, float nz, float3& b1, float3& b2) {
     float sg = copysignf(1.0f, nz);
-    float a = -1.0f / (sg + nz);
+    float a = __fdividef(-1.0f, sg + nz);
     float b = nx * ny * a;
     b1 = make_float3(1.0f + sg * nx * nx * a, sg * b, -sg * nx);
     b2 = make_float3(b, sg + ny * ny * a, -ny);

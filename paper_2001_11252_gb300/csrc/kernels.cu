@@ -366,7 +366,7 @@ __device__ __forceinline__ void scatter_line(const Params& P, Packet<NL>& s, flo
     } else {
         // nu_out = nu_in (1 + f)  <=>  x_out = x_in + (nu0/Delta nu + x_in) f
         float rec = (1.0f - mu) * recp;
-        float f = ((uout - upar) * vthc - rec) / (1.0f + rec);
+        float f = __fdividef((uout - upar) * vthc - rec, 1.0f + rec);
         pair_add(s.xh, s.xl, (s.cc.q0 + s.xh) * f);
     }
     if (!P.keep_dir) {
@@ -496,7 +496,7 @@ __device__ __forceinline__ void advance(const Params& P, const Geo& G, Packet<NL
         float li_f = 0.0f;
         double li_d = 0.0;
         if (!border_leaf) {
-            li_f = s.tauf / (kap * G.box_cm_f);
+            li_f = __fdividef(s.tauf, kap * G.box_cm_f);
             float dec = __fmaf_ru(li_f, 1.0f + 0x1p-20f, 4e-16f);
             if (dec < s.budget) {
                 s.budget = __fsub_rd(s.budget, dec);

@@ -210,21 +210,30 @@ def test_sphere_run_matches_oracle(tau_dust):
 
 def test_expanding_sphere_peeling_matches_oracle():
     """Expanding sphere with dust, recoil and core/wing phase functions,
-    peeled into 3 directions (spectra, images, cubes)."""
-    n = 200
+    peeled into 3 directions (spectra, images, cubes).  Peeled totals are
+    Monte Carlo estimates: the oracle runs the packets in 8 groups of 100, and
+    the GPU total must lie within 4 sigma of the oracle's (sigma from the
+    spread of the group totals, x sqrt(2) for the difference of two
+    estimates)."""
+    n, groups = 800, 8
     wl = synth.expanding_sphere(N_HI=1e19, n_packets=n, npix=16, nchan=40)
     ctx = context(wl)
     g, st = gpu_run(ctx, wl.packets)
-    r, tal = oracle_run(wl)
+    o = oracle.Oracle(wl)
+    m = n // groups
+    parts = [o.run(lo=k * m, hi=(k + 1) * m, threads=8) for k in range(groups)]
+    r = {k: np.concatenate([p[0][k] for p in parts]) for k in ("nscatt", "status")}
+    tal = {k: sum(p[1][k] for p in parts) for k in ("pspec", "pimg", "pcube")}
     same = (g["nscatt"] == r["nscatt"]).mean()
     print("expanding: identical %.4f <N> %.1f vs %.1f" % (same, g["nscatt"].mean(), r["nscatt"].mean()))
     ps = ctx.get_tally(1)
     pi = ctx.get_tally(2)
     pc = ctx.get_tally(3)
-    # tallies: same totals within Monte Carlo noise; cube marginals = image
     for d in range(3):
-        a, b = ps[d].sum(), tal["pspec"][d].sum()
-        assert abs(a / b - 1) < 0.1, (d, a, b)
+        a, b = float(ps[d].sum()), float(tal["pspec"][d].sum())
+        sig = np.std([p[1]["pspec"][d].sum() for p in parts], ddof=1) * math.sqrt(groups)
+        print("direction %d: peeled %.4g vs %.4g (sigma %.3g)" % (d, a, b, sig))
+        assert abs(a - b) <= 4 * math.sqrt(2) * sig + 1e-3 * b, (d, a, b, sig)
     assert np.allclose(pc.sum(-1), pi, rtol=1e-4, atol=1e-9) or pc.sum() <= pi.sum() * (1 + 1e-5)
     if same > 0.95:
         assert np.allclose(ps, tal["pspec"], rtol=2e-3, atol=1e-6 * ps.max())
