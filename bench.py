@@ -82,6 +82,25 @@ def workload(n):
     return wl
 
 
+def shard_first(rank, step, warmup, steps, n):
+    """First packet id of `step` on `rank`: every rank owns its own id ranges
+    (weak scaling: packets are independent, so ranks exchange nothing while
+    they propagate)."""
+    return (rank * (warmup + steps + 1) + step) * n
+
+
+def reduce_over_ranks(dist, dev, t, counts):
+    """(max of t, sums of counts) over the ranks; the identity on one rank."""
+    if dist is None:
+        return t, list(counts)
+    import torch
+    v = torch.tensor([t], dtype=torch.float64, device=dev)
+    dist.all_reduce(v, op=dist.ReduceOp.MAX)
+    c = torch.tensor(list(counts), dtype=torch.float64, device=dev)
+    dist.all_reduce(c)
+    return float(v.item()), [float(x) for x in c.tolist()]
+
+
 def packets(wl, first, n):
     import synth
     return synth.point_source(n, (0.5, 0.5, 0.5), wl.packets.nu[0], wl.physics.seed ^ 0xA5A5 ^ first, first_id=first)
@@ -345,8 +364,7 @@ def main():
     ctx.set_stream(stream)
 
     def dev_packets(step):
-        first = (rank * (args.warmup + args.steps + 1) + step) * P
-        pk = packets(wl, first, P)
+        pk = packets(wl, shard_first(rank, step, args.warmup, args.steps, P), P)
         t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(dev, dt)
         return pk, (t(pk.pos, torch.float64), t(pk.dir, torch.float64), t(pk.nu, torch.float64),
                     t(pk.ids.view(np.int64), torch.int64))
@@ -382,18 +400,10 @@ def main():
     loads = sum(s["leaf_loads"] for s in stats_all)
     sons = sum(s["son_loads"] for s in stats_all)
     nbrs = sum(s["nbor_loads"] for s in stats_all)
-    tmax = t_ms
-    tot_scatt, tot_pk = scatt, pk_done
-    if dist:
-        v = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(v, op=dist.ReduceOp.MAX)
-        tmax = float(v.item())
-        c = torch.tensor([scatt, pk_done], dtype=torch.float64, device=dev)
-        dist.all_reduce(c)
-        tot_scatt, tot_pk = float(c[0].item()), float(c[1].item())
+    tmax, (tot_scatt, tot_pk) = reduce_over_ranks(dist, dev, t_ms, (scatt, pk_done))
 
     # ---- end to end through the C ABI with host buffers (copies in the timed region)
-    e2e_inputs = [packets(wl, (rank * (args.warmup + args.steps + 1) + args.warmup + i) * P, P)
+    e2e_inputs = [packets(wl, shard_first(rank, args.warmup + i, args.warmup, args.steps, P), P)
                   for i in range(args.steps)]
     outs = [{"status": np.zeros(P, np.int32), "nscatt": np.zeros(P, np.int64), "nu": np.zeros(P)}
             for _ in range(args.steps)]
@@ -408,13 +418,7 @@ def main():
         e2e_scatt += st["nscatt_line"] + st["nscatt_dust"]
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        v = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(v, op=dist.ReduceOp.MAX)
-        e2e_s = float(v.item())
-        c = torch.tensor([e2e_scatt], dtype=torch.float64, device=dev)
-        dist.all_reduce(c)
-        e2e_scatt = float(c[0].item())
+    e2e_s, (e2e_scatt,) = reduce_over_ranks(dist, dev, e2e_s, (e2e_scatt,))
     h2d = P * (3 + 3 + 1 + 1) * 8
     d2h = P * (4 + 8 + 8)
 
