@@ -413,6 +413,26 @@ def sphere(tau0=1e6, T=1e4, tau_dust=0.0, n_packets=1_000_000, base=3, max_level
                     Physics(recoil=recoil, isotropic=isotropic, seed=seed), Detector(lo, hi, nb), pk)
 
 
+def deuterium_sphere(N_HI=2e19, T=1e4, d_over_h=3.0e-5, n_packets=10000, base=3, max_level=6, xrange=20.0,
+                     with_d=True, seed_offset=0):
+    """Static sphere of H I mixed with deuterium (Appendix A, Fig.
+    sphere_deuterium_effect): centre-to-edge column N_HI, T, D/H, no dust,
+    Lya packets at the centre at the H line centre (x_in = 0), core/wing
+    phase functions, no recoil; spectrum in the H line's Doppler units over
+    +-xrange.  with_d=False gives the pure H I sphere on the same packets."""
+    tree = sphere_octree(base, max_level)
+    L = 1.0 * KPC_CM
+    R = 0.45
+    h = lya()
+    lines = [h, d_lya(d_over_h)] if with_d else [h]
+    med = uniform_medium(tree, L, N_HI / (R * L), T)
+    seed = RUN_SEED + 6 + seed_offset
+    pk = point_source(n_packets, (0.5, 0.5, 0.5), nu_of(h.lambda_A), seed ^ 0xA5A5)
+    lo, hi, nb = x_axis(h, T, -xrange, xrange, 200)
+    return Workload("deuterium_sphere", med, Domain(0, (0.5, 0.5, 0.5), R), lines, Dust(sigma=4.0e-22),
+                    Physics(recoil=0, isotropic=0, seed=seed), Detector(lo, hi, nb), pk)
+
+
 PEEL_DIRS_3 = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0],
                         [1.0 / math.sqrt(3.0)] * 3])
 
