@@ -90,6 +90,19 @@ def siII_1193():
                 density=1, phase=1, channels=[(1.40e9, 1197.39)])
 
 
+def feII_2344():
+    """Fe II 2344.21 A (A=1.73e8, f=0.114) with fluorescent 2365.55* (A=5.90e7)
+    and 2381.49* (A=3.10e7): the UV1 multiplet line with three channels."""
+    return Line("FeII_2344", 2344.21, 1.73e8, 0.114, 55.845 * AMU_CGS,
+                density=1, phase=1, channels=[(5.90e7, 2365.55), (3.10e7, 2381.49)])
+
+
+def feII_2374():
+    """Fe II 2374.46 A (A=4.25e7, f=0.0359) with fluorescent 2396.35* (A=2.59e8)."""
+    return Line("FeII_2374", 2374.46, 4.25e7, 0.0359, 55.845 * AMU_CGS,
+                density=1, phase=1, channels=[(2.59e8, 2396.35)])
+
+
 def nu_of(lambda_A):
     return C_CGS / (lambda_A * 1e-8)
 
@@ -535,6 +548,24 @@ def siII_sphere(tau0=1e3, T=1e4, n_packets=400, base=3, max_level=4, tau_dust=0.
     det = Detector(lo, hi, 400, dirs=PEEL_DIRS_3[:2].copy(), npix=4, fov=2 * R, cube=1)
     return Workload("siII", med, Domain(0, (0.5, 0.5, 0.5), R), [lya(), l1190, l1193], dust,
                     Physics(recoil=1, isotropic=0, seed=seed), det, pk)
+
+
+def feII_sphere(tau0=1e4, T=1e4, n_packets=4000, base=3, max_level=4, seed_offset=0):
+    """Static sphere of Fe II (UV1 lines 2344 and 2374, Table 1) lit at the
+    2344.21 A line centre at its centre, no dust: a photon scatters in 2344
+    until it decays through a fluorescent channel (2365.55* or 2381.49*, where
+    the gas is transparent) or escapes in the resonant line.  Escape spectrum
+    over 2335-2405 A."""
+    tree = sphere_octree(base, max_level)
+    L = 1.0 * KPC_CM
+    R = 0.45
+    l2344, l2374 = feII_2344(), feII_2374()
+    n_fe = density_for_tau0(l2344, T, tau0, R * L)
+    med = uniform_medium(tree, L, 0.0, T, n_metal=n_fe)
+    seed = RUN_SEED + 7 + seed_offset
+    pk = point_source(n_packets, (0.5, 0.5, 0.5), nu_of(l2344.lambda_A), seed ^ 0xA5A5)
+    return Workload("feII", med, Domain(0, (0.5, 0.5, 0.5), R), [l2344, l2374], Dust(sigma=4.0e-22),
+                    Physics(recoil=0, isotropic=0, seed=seed), Detector(nu_of(2405.0), nu_of(2335.0), 700), pk)
 
 
 # --------------------------------------------------------------------------
