@@ -38,8 +38,8 @@ WORKLOAD = ("static H I + dust sphere: 8^3 root refined to 64^3-equivalent octre
 # smsp__inst_executed.sum / scatterings of one ncu capture (65536 packets capped
 # at 1e4 scatterings each, profiles/k_propagate_sphere_tau1e6.md), and the
 # active lanes per warp instruction of the same capture
-INST_PER_SCATT = 36008436139 / 640142157
-LANES_PER_INST = 19.12
+INST_PER_SCATT = 34047718982 / 640157743
+LANES_PER_INST = 18.91
 # DRAM bytes per leaf visit of k_ray_tau on the synthetic galaxy
 # (dram__bytes_read.sum + dram__bytes_write.sum of one capture of 2^18 rays,
 # 59 732 805 leaf visits, profiles/k_ray_tau_galaxy.md)
@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--packets", type=int, default=1 << 18)
+    ap.add_argument("--packets", type=int, default=1_000_000,
+                    help="packets per step (the workload's 1e6 packets: fewer leave the GPU idle while the last, "
+                         "longest packets finish)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
