@@ -435,14 +435,17 @@ __device__ __forceinline__ bool next_leaf(const Geo& G, const double p[3], const
     const int l = w.level;
     const int sh = L - l;
     int fi = w.i >> 1, fj = w.j >> 1, fk = w.k >> 1;
+    // the cell to descend from: the father's child, else the father's
+    // neighbour across the face, else the top-grid cell; one descent for all
+    int code = 0, m = 0, oct = 0;
+    bool got = false;
     if ((t[0] >> (sh + 1)) == fi && (t[1] >> (sh + 1)) == fj && (t[2] >> (sh + 1)) == fk) {
         int child = ((t[0] >> sh) & 1) | (((t[1] >> sh) & 1) << 1) | (((t[2] >> sh) & 1) << 2);
-        int code = __ldg(G.son + 8 * w.oct + child);
-        ++son_loads;
-        descend(G, code, l, w.oct, t[0], t[1], t[2], w, son_loads);
-        return true;
-    }
-    if (l >= 2) {
+        code = __ldg(G.son + 8 * w.oct + child);
+        m = l;
+        oct = w.oct;
+        got = true;
+    } else if (l >= 2) {
         const bool up = is_pos(axis == 0 ? k[0] : (axis == 1 ? k[1] : k[2]));
         int face = 2 * axis + (up ? 1 : 0);
         int4 a = __ldg(G.nbr + 2 * w.oct);
@@ -460,14 +463,26 @@ __device__ __forceinline__ bool next_leaf(const Geo& G, const double p[3], const
             int d = (l - 1) - nl;
             int s2 = L - nl;
             if ((t[0] >> s2) == (f[0] >> d) && (t[1] >> s2) == (f[1] >> d) && (t[2] >> s2) == (f[2] >> d)) {
-                int code = __ldg(G.son + nc);
-                ++son_loads;
-                descend(G, code, nl, nc >> 3, t[0], t[1], t[2], w, son_loads);
-                return true;
+                code = __ldg(G.son + nc);
+                m = nl;
+                oct = nc >> 3;
+                got = true;
             }
         }
     }
-    return locate(G, t[0], t[1], t[2], w, son_loads);
+    if (!got) {
+        const int S = G.top_level;
+        const int s = L - S;
+        long long idx = (((long long)(t[2] >> s) << S) + (t[1] >> s)) << S;
+        idx += (t[0] >> s);
+        int4 e = __ldg(G.top + idx);
+        code = e.x;
+        m = e.y;
+        oct = e.z;
+    }
+    ++son_loads;
+    descend(G, code, m, oct, t[0], t[1], t[2], w, son_loads);
+    return true;
 }
 
 // distance along k from p to the exit face of leaf w (FP64, exactly the
