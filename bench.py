@@ -70,9 +70,10 @@ def parse():
     ap.add_argument("--galaxy-cap", type=int, default=64, help="scatterings per packet in the galaxy section")
     ap.add_argument("--galaxy-thin", type=float, default=1e-8,
                     help="density scale of the lower-column copy of the galaxy used for peeling and its adjoint")
-    ap.add_argument("--section", default="all", choices=["all", "main", "batch", "galaxy"],
+    ap.add_argument("--section", default="all", choices=["all", "main", "batch", "galaxy", "configs"],
                     help="all (default): the headline line with the batch and galaxy sections; "
-                         "batch / galaxy: that section alone, printed as its own JSON line")
+                         "batch / galaxy: that section alone, printed as its own JSON line; configs: GPU and "
+                         "oracle rates of the other configurations (not part of the default run)")
     ap.add_argument("--max-scatt", type=int, default=0,
                     help="cap scatterings per packet (profiling runs only; 0 = the full workload)")
     return ap.parse_args()
@@ -227,6 +228,71 @@ def run_batch(args):
                         "v_max U[0,300] km/s, (2^d)^3 grids d in 2..5, packets log-U[1e3,1e5] x %g" % args.batch_scale}
 
 
+# ------------------------------------------------------------------ per-config rates
+def _oracle_rate(wl, seconds, threads):
+    """Oracle on the first packets of a workload, doubling the sample until
+    about `seconds` of work: (scatterings/s, packets/s, packets, seconds)."""
+    import oracle
+    o = oracle.Oracle(wl)
+    n = max(threads, 2)
+    while True:
+        n = min(n, wl.packets.n)
+        t0 = time.perf_counter()
+        out, _ = o.run(lo=0, hi=n, threads=threads, chunk=1)
+        dt = time.perf_counter() - t0
+        if dt >= seconds / 3 or n == wl.packets.n:
+            return int(out["nscatt"].sum()) / dt, n / dt, n, dt
+        n *= 2
+
+
+def run_configs(args):
+    """GPU and oracle rates per configuration, at equal work per packet: the
+    oracle on a bounded sample, one thread and all host threads."""
+    import torch
+    import paper_2001_11252_gb300 as rg
+    import synth
+    dev = torch.device("cuda:0")
+    threads = os.cpu_count() or 1
+    cfgs = [
+        ("C1 slab tau0=1e4, T=1e4 K, 2000 packets", lambda n: synth.slab(tau0=1e4, n_packets=n), 2000),
+        ("C1-thick slab tau0=1e6, T=10 K, 2000 packets", lambda n: synth.slab(tau0=1e6, T=10.0, n_packets=n), 2000),
+        ("C3 expanding sphere N_HI=1e20, v_max 200 km/s, tau_dust 0.5, peeling 3 x 100^2 x 200",
+         lambda n: synth.expanding_sphere(n_packets=n), 1 << 12),
+        ("deuterium sphere N_HI=2e19, D/H 3e-5", lambda n: synth.deuterium_sphere(n_packets=n), 1 << 18),
+        ("Fe II UV1 sphere tau0=1e4 (fluorescence)", lambda n: synth.feII_sphere(n_packets=n), 1 << 20),
+    ]
+    out = []
+    for name, fn, n in cfgs:
+        wl = fn(n)
+        ctx = rg.Context(0)
+        ctx.setup(wl)
+        pk = wl.packets
+        t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(dev, dt)
+        args_d = (t(pk.pos, torch.float64), t(pk.dir, torch.float64), t(pk.nu, torch.float64),
+                  t(pk.ids.view(np.int64), torch.int64))
+        m = min(n, 1024)
+        ctx.propagate(*[a[:m] for a in args_d], stats=False)
+        ctx.zero_tallies()
+        stream = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = ctx.propagate(*args_d, stats=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+        ctx.close()
+        sc = st["nscatt_line"] + st["nscatt_dust"]
+        o1 = _oracle_rate(fn(64), args.cpu_seconds / 6, 1)
+        on = _oracle_rate(fn(max(64, 8 * threads)), args.cpu_seconds / 6, threads)
+        out.append({"config": name, "packets": n, "gpu_s": sec, "gpu_scatt_per_s": sc / sec, "gpu_packets_per_s": n / sec,
+                    "mean_scatterings": sc / n, "peel_rays": st["npeel_rays"],
+                    "oracle_1_thread_scatt_per_s": o1[0], "oracle_threads": threads,
+                    "oracle_all_threads_scatt_per_s": on[0], "oracle_sample_packets": [o1[2], on[2]],
+                    "gpu_over_oracle_all_threads": (sc / sec) / on[0]})
+    return out
+
+
 # ------------------------------------------------------------------ galaxy section
 def run_galaxy(args, peaks):
     """Synthetic galaxy (~1e7 leaves, levels 6-12, three lines, dust,
@@ -331,7 +397,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.section in ("batch", "galaxy"):
+    if args.section in ("batch", "galaxy", "configs"):
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         peaks = {}
@@ -339,7 +405,8 @@ def main():
             peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         except Exception:
             pass
-        res = run_batch(args) if args.section == "batch" else run_galaxy(args, peaks)
+        res = (run_batch(args) if args.section == "batch" else
+               run_galaxy(args, peaks) if args.section == "galaxy" else run_configs(args))
         print(json.dumps({"section": args.section, args.section: res}), flush=True)
         return
     import torch
