@@ -62,6 +62,8 @@ def parse():
                     help="models in the batched-vs-plain comparison (0 = skip it)")
     ap.add_argument("--batch-scale", type=float, default=0.01,
                     help="packets per batch model: log-uniform [1e3, 1e5] times this")
+    ap.add_argument("--batch-plain", type=int, default=1,
+                    help="also time one launch per model (1) or only the persistent launch (0)")
     ap.add_argument("--batch-cap", type=int, default=20000,
                     help="scatterings per packet cap in the batch comparison")
     ap.add_argument("--galaxy", type=int, default=1, help="run the synthetic-galaxy section (1) or not (0)")
@@ -215,14 +217,18 @@ def run_batch(args):
     t0 = time.perf_counter()
     stb = ctx.propagate_batch(rg.BATCH_PERSISTENT)
     tb = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    stp = ctx.propagate_batch(rg.BATCH_PER_MODEL)
-    tp = time.perf_counter() - t0
+    tp = float("nan")
+    if args.batch_plain:
+        t0 = time.perf_counter()
+        ctx.propagate_batch(rg.BATCH_PER_MODEL)
+        tp = time.perf_counter() - t0
     sc = stb["nscatt_line"] + stb["nscatt_dust"]
     ctx.close()
+    plain = tp == tp   # timed
     return {"models": len(models), "packets": stb["packets"], "scatterings": sc, "capped": stb["capped"],
-            "cap_per_packet": args.batch_cap, "persistent_s": tb, "per_model_s": tp,
-            "persistent_scatt_per_s": sc / tb, "per_model_scatt_per_s": sc / tp, "speedup": tp / tb,
+            "cap_per_packet": args.batch_cap, "persistent_s": tb, "per_model_s": tp if plain else None,
+            "persistent_scatt_per_s": sc / tb, "per_model_scatt_per_s": sc / tp if plain else None,
+            "speedup": tp / tb if plain else None,
             "autotuned": {"block": tune["best"][0], "blocks_per_sm": tune["best"][1]},
             "workload": "512 homogeneous slab/sphere models: tau0 log-U[1e2,1e7], T log-U[1e2,1e5] K, "
                         "v_max U[0,300] km/s, (2^d)^3 grids d in 2..5, packets log-U[1e3,1e5] x %g" % args.batch_scale}
