@@ -243,3 +243,21 @@ def test_peeling_flux_equals_escape():
         ps = 4 * math.pi * tal["pspec"][d] / n
         xs = np.arange(esc.size)
         assert abs((ps * xs).sum() / ps.sum() - (esc * xs).sum() / esc.sum()) < 2.0
+
+
+def test_expanding_sphere_redshift():
+    """Outflow (Sect. 3.4.2, expanding sphere): photons escape mostly on the
+    red side of the line; in an infalling sphere (v -> -v) on the blue side,
+    by the same amount (the two media are mirror images in frequency)."""
+    res = {}
+    for sign in (1.0, -1.0):
+        wl = synth.expanding_sphere(N_HI=1e18, v_max_kms=200.0 * sign, tau_dust=0.0, n_packets=400, npix=4, nchan=8)
+        wl.physics.recoil = 0
+        out, _ = oracle.Oracle(wl).run(threads=8)
+        h = wl.lines[0]
+        x = (out["nu"] - synth.nu_of(h.lambda_A)) / synth.doppler_width(h, 1e4)
+        res[sign] = x
+    m_out, m_in = res[1.0].mean(), res[-1.0].mean()
+    se = math.sqrt(res[1.0].var() / 400 + res[-1.0].var() / 400)
+    assert m_out < -5 * res[1.0].std() / 20 and m_in > 5 * res[-1.0].std() / 20
+    assert abs(m_out + m_in) < 4 * se
