@@ -263,7 +263,7 @@ def run_configs(args):
         ("C1 slab tau0=1e4, T=1e4 K, 2000 packets", lambda n: synth.slab(tau0=1e4, n_packets=n), 2000),
         ("C1-thick slab tau0=1e6, T=10 K, 2000 packets", lambda n: synth.slab(tau0=1e6, T=10.0, n_packets=n), 2000),
         ("C3 expanding sphere N_HI=1e20, v_max 200 km/s, tau_dust 0.5, peeling 3 x 100^2 x 200",
-         lambda n: synth.expanding_sphere(n_packets=n), 1 << 12),
+         lambda n: synth.expanding_sphere(n_packets=n), 1 << 17),
         ("deuterium sphere N_HI=2e19, D/H 3e-5", lambda n: synth.deuterium_sphere(n_packets=n), 1 << 18),
         ("Fe II UV1 sphere tau0=1e4 (fluorescence)", lambda n: synth.feII_sphere(n_packets=n), 1 << 20),
     ]
