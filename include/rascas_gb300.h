@@ -61,7 +61,7 @@ enum { RASCAS_HOST = 0, RASCAS_DEVICE = 1 };
 enum { RASCAS_PK_ACTIVE = 0, RASCAS_PK_ESCAPED = 1, RASCAS_PK_ABSORBED = 2,
        RASCAS_PK_CAPPED = 3, RASCAS_PK_ERROR = 4 };
 
-enum { RASCAS_DOMAIN_SPHERE = 0, RASCAS_DOMAIN_SLAB = 1, RASCAS_DOMAIN_CUBE = 2 };
+enum { RASCAS_DOMAIN_SPHERE = 0, RASCAS_DOMAIN_SLAB = 1, RASCAS_DOMAIN_CUBE = 2, RASCAS_DOMAIN_SHELL = 3 };
 
 enum { RASCAS_TALLY_SPECTRUM = 0,   /* [nbin] escape spectrum, 1 per escaped packet */
        RASCAS_TALLY_PEEL_SPECTRA = 1, /* [ndir][nbin] peeled flux per sr */
@@ -90,13 +90,18 @@ typedef struct {
     double box_cm;
 } rascas_octree;
 
-/* Domain of the computational volume (Sect. 4): a sphere (centre, radius),
- * a slab |z - centre_z| <= size, periodic in x and y (Sect. 4, footnote on
- * slabs), or a cube (centre, half side).  Packets escape at its border. */
+/* Domain of the computational volume (Sect. 4 names spheres, shells, cubes
+ * and slabs): a sphere (centre, radius = size), a shell (centre, outer radius
+ * = size, inner radius = inner: the volume between the two spheres), a slab
+ * |z - centre_z| <= size, periodic in x and y (Sect. 4, footnote on slabs),
+ * or a cube (centre, half side = size).  Packets escape at its border; a
+ * point outside the domain is at distance 0 from it.  `inner` is read for
+ * shells only (0 <= inner < size). */
 typedef struct {
     int32_t kind;
     double centre[3];
     double size;
+    double inner;
 } rascas_domain;
 
 /* One absorption line (Sect. 3.1.1, Table 1): rest frequency nu0 (Hz),

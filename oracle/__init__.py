@@ -64,7 +64,7 @@ class Cfg(C.Structure):
         ("son", C.c_void_p), ("n_HI", C.c_void_p), ("vx", C.c_void_p), ("vy", C.c_void_p),
         ("vz", C.c_void_p), ("T", C.c_void_p), ("n_dust", C.c_void_p), ("n_metal", C.c_void_p),
         ("noct", C.c_int64), ("nleaf", C.c_int64), ("box_cm", C.c_double),
-        ("dom_kind", C.c_int64), ("dom_c", C.c_double * 3), ("dom_size", C.c_double),
+        ("dom_kind", C.c_int64), ("dom_c", C.c_double * 3), ("dom_size", C.c_double), ("dom_inner", C.c_double),
         ("nline", C.c_int64),
         ("line_nu", C.c_double * MAXLINE), ("line_A", C.c_double * MAXLINE),
         ("line_f", C.c_double * MAXLINE), ("line_m", C.c_double * MAXLINE),
@@ -179,6 +179,7 @@ class Oracle:
         cf.dom_kind = d.kind
         cf.dom_c[:] = list(d.centre)
         cf.dom_size = d.size
+        cf.dom_inner = getattr(d, "inner", 0.0)
         assert len(wl.lines) <= MAXLINE
         cf.nline = len(wl.lines)
         for i, ln in enumerate(wl.lines):

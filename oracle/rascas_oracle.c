@@ -56,7 +56,7 @@ static const double OPI = 3.14159265358979323846;
 #define ORA_MAXDIR 8
 
 enum { ORA_ACTIVE = 0, ORA_ESCAPED = 1, ORA_ABSORBED = 2, ORA_CAPPED = 3, ORA_ERROR = 4 };
-enum { ORA_DOM_SPHERE = 0, ORA_DOM_SLAB = 1, ORA_DOM_CUBE = 2 };
+enum { ORA_DOM_SPHERE = 0, ORA_DOM_SLAB = 1, ORA_DOM_CUBE = 2, ORA_DOM_SHELL = 3 };
 
 typedef struct {
     /* mesh (Sect. 4.3): son per cell, physical fields per leaf */
@@ -68,6 +68,7 @@ typedef struct {
     int64_t dom_kind;
     double dom_c[3];
     double dom_size;
+    double dom_inner;   /* shell inner radius */
     /* lines (Sect. 3.1.1, Table 1) */
     int64_t nline;
     double line_nu[ORA_MAXLINE], line_A[ORA_MAXLINE], line_f[ORA_MAXLINE], line_m[ORA_MAXLINE];
@@ -440,14 +441,27 @@ static double border_distance(const ora_cfg *cf, const double p[3], const double
 {
     const double *c = cf->dom_c;
     double R = cf->dom_size;
-    if (cf->dom_kind == ORA_DOM_SPHERE) {
+    if (cf->dom_kind == ORA_DOM_SPHERE || cf->dom_kind == ORA_DOM_SHELL) {
         double d0 = p[0] - c[0], d1 = p[1] - c[1], d2 = p[2] - c[2];
         double b = d0 * k[0] + d1 * k[1] + d2 * k[2];
-        double cc = d0 * d0 + d1 * d1 + d2 * d2 - R * R;
+        double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+        double cc = r2 - R * R;
         double disc = b * b - cc;
         if (disc < 0.0) disc = 0.0;
         double sq = sqrt(disc);
         double t = b > 0.0 ? -cc / (b + sq) : sq - b;
+        if (cf->dom_kind == ORA_DOM_SHELL) {
+            /* a shell ends at the outer sphere and at the inner one: the first
+             * root of |p + t k - c| = inner when the ray moves inwards and
+             * meets it; a point inside the inner sphere is outside the domain */
+            double ci = r2 - cf->dom_inner * cf->dom_inner;
+            if (ci <= 0.0) return 0.0;
+            double di = b * b - ci;
+            if (b < 0.0 && di >= 0.0) {
+                double ti = ci / (-b + sqrt(di));
+                if (ti < t) t = ti;
+            }
+        }
         return t < 0.0 ? 0.0 : t;
     }
     double best = INFINITY;

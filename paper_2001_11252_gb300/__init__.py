@@ -13,5 +13,5 @@ from ._native import (  # noqa: F401
     Context, Stats, Event, RascasError, lib, library_path,
     TALLY_SPECTRUM, TALLY_PEEL_SPECTRA, TALLY_PEEL_IMAGES, TALLY_PEEL_CUBES,
     PK_ACTIVE, PK_ESCAPED, PK_ABSORBED, PK_CAPPED, PK_ERROR,
-    DOMAIN_SPHERE, DOMAIN_SLAB, DOMAIN_CUBE, BATCH_PERSISTENT, BATCH_PER_MODEL,
+    DOMAIN_SPHERE, DOMAIN_SLAB, DOMAIN_CUBE, DOMAIN_SHELL, BATCH_PERSISTENT, BATCH_PER_MODEL,
 )

@@ -16,7 +16,7 @@ from . import build as _build
 
 HOST, DEVICE = 0, 1
 PK_ACTIVE, PK_ESCAPED, PK_ABSORBED, PK_CAPPED, PK_ERROR = 0, 1, 2, 3, 4
-DOMAIN_SPHERE, DOMAIN_SLAB, DOMAIN_CUBE = 0, 1, 2
+DOMAIN_SPHERE, DOMAIN_SLAB, DOMAIN_CUBE, DOMAIN_SHELL = 0, 1, 2, 3
 TALLY_SPECTRUM, TALLY_PEEL_SPECTRA, TALLY_PEEL_IMAGES, TALLY_PEEL_CUBES = 0, 1, 2, 3
 MAX_LINES, MAX_CHAN, MAX_DIRS = 4, 4, 8
 C_CGS = 2.99792458e10
@@ -31,7 +31,7 @@ class Octree(C.Structure):
 
 
 class Domain(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("centre", C.c_double * 3), ("size", C.c_double)]
+    _fields_ = [("kind", C.c_int32), ("centre", C.c_double * 3), ("size", C.c_double), ("inner", C.c_double)]
 
 
 class Line(C.Structure):
@@ -226,11 +226,12 @@ class Context:
         t.box_cm = float(box_cm)
         self._ck(self._L.rascas_load_octree(self._h, C.byref(t), mem), "load_octree")
 
-    def set_domain(self, kind, centre, size):
+    def set_domain(self, kind, centre, size, inner=0.0):
         d = Domain()
         d.kind = int(kind)
         d.centre[:] = [float(v) for v in centre]
         d.size = float(size)
+        d.inner = float(inner)
         self._ck(self._L.rascas_set_domain(self._h, C.byref(d)), "set_domain")
 
     def set_lines(self, lines, dust=None):
@@ -289,7 +290,7 @@ class Context:
         m = wl.medium
         self.load_octree(m.tree.son, m.n_HI, m.vx, m.vy, m.vz, m.T, m.n_dust,
                          m.n_metal if any(l.density == 1 for l in wl.lines) else None, m.box_cm)
-        self.set_domain(wl.domain.kind, wl.domain.centre, wl.domain.size)
+        self.set_domain(wl.domain.kind, wl.domain.centre, wl.domain.size, getattr(wl.domain, "inner", 0.0))
         self.set_lines(wl.lines, wl.dust)
         ph = wl.physics
         self.set_physics(ph.recoil, ph.isotropic, ph.keep_direction, ph.x_gauss, ph.max_scatt, ph.max_steps,
@@ -446,6 +447,7 @@ class Context:
             M.domain.kind = wl.domain.kind
             M.domain.centre[:] = [float(v) for v in wl.domain.centre]
             M.domain.size = float(wl.domain.size)
+            M.domain.inner = float(getattr(wl.domain, "inner", 0.0))
             M.nu_lo, M.nu_hi = float(wl.detector.nu_lo), float(wl.detector.nu_hi)
             M.packets = PacketsIn(*[x.ctypes.data for x in b])
             M.npackets = int(pk.n)

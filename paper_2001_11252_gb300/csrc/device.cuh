@@ -510,17 +510,27 @@ __device__ __forceinline__ double face_distance(const double p[3], const double 
 // the oracle)
 __device__ __forceinline__ double border_distance(const Geo& G, const double p[3],
                                                   const double k[3], const double inv[3]) {
-    if (G.dom_kind == 0) {
+    if (G.dom_kind == 0 || G.dom_kind == 3) {
         double d0 = __dsub_rn(p[0], G.dom_c[0]);
         double d1 = __dsub_rn(p[1], G.dom_c[1]);
         double d2 = __dsub_rn(p[2], G.dom_c[2]);
         double b = __dadd_rn(__dadd_rn(__dmul_rn(d0, k[0]), __dmul_rn(d1, k[1])), __dmul_rn(d2, k[2]));
-        double cc = __dsub_rn(__dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2)),
-                              __dmul_rn(G.dom_R, G.dom_R));
+        double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
+        double cc = __dsub_rn(r2, __dmul_rn(G.dom_R, G.dom_R));
         double disc = __dsub_rn(__dmul_rn(b, b), cc);
         if (disc < 0.0) disc = 0.0;
         double sq = __dsqrt_rn(disc);
         double t = b > 0.0 ? __ddiv_rn(-cc, __dadd_rn(b, sq)) : __dsub_rn(sq, b);
+        if (G.dom_kind == 3) {
+            // shell: also the entry into the inner sphere, when the ray meets it
+            double ci = __dsub_rn(r2, __dmul_rn(G.dom_Rin, G.dom_Rin));
+            if (ci <= 0.0) return 0.0;   // inside the hole: outside the domain
+            double di = __dsub_rn(__dmul_rn(b, b), ci);
+            if (b < 0.0 && di >= 0.0) {
+                double ti = __ddiv_rn(ci, __dadd_rn(-b, __dsqrt_rn(di)));
+                if (ti < t) t = ti;
+            }
+        }
         return t < 0.0 ? 0.0 : t;
     }
     double best = __longlong_as_double(0x7ff0000000000000ULL);

@@ -133,13 +133,16 @@ void mesh_flags(HostMesh& M, const rascas_domain* dom) {
             const double* c = dom->centre;
             double R = dom->size;
             const double m = 1e-9 * (R > 0 ? R : 1.0);
-            if (dom->kind == RASCAS_DOMAIN_SPHERE) {
-                double d2 = 0.0;
+            if (dom->kind == RASCAS_DOMAIN_SPHERE || dom->kind == RASCAS_DOMAIN_SHELL) {
+                double d2 = 0.0, n2 = 0.0;
                 for (int ax = 0; ax < 3; ++ax) {
                     double far = std::fmax(std::fabs(lo[ax] - c[ax]), std::fabs(hi[ax] - c[ax]));
+                    double near = c[ax] < lo[ax] ? lo[ax] - c[ax] : (c[ax] > hi[ax] ? c[ax] - hi[ax] : 0.0);
                     d2 += far * far;
+                    n2 += near * near;
                 }
                 interior = std::sqrt(d2) < R - m;
+                if (dom->kind == RASCAS_DOMAIN_SHELL) interior = interior && std::sqrt(n2) > dom->inner + m;
             } else {
                 interior = true;
                 for (int ax = 0; ax < 3; ++ax) {
@@ -377,13 +380,16 @@ int rascas_load_octree(rascas_ctx* ctx, const rascas_octree* t, int mem) {
 
 int rascas_set_domain(rascas_ctx* ctx, const rascas_domain* d) {
     if (!ctx || !d) return RASCAS_E_ARG;
-    if (d->kind < 0 || d->kind > 2 || !(d->size > 0.0)) return fail(ctx, RASCAS_E_ARG, "domain: bad kind or size");
+    if (d->kind < 0 || d->kind > 3 || !(d->size > 0.0) ||
+        (d->kind == RASCAS_DOMAIN_SHELL && !(d->inner >= 0.0 && d->inner < d->size)))
+        return fail(ctx, RASCAS_E_ARG, "domain: bad kind or size");
     ctx->dom = *d;
     ctx->has_domain = true;
     Params& P = ctx->P;
     P.g.dom_kind = d->kind;
     for (int ax = 0; ax < 3; ++ax) P.g.dom_c[ax] = d->centre[ax];
     P.g.dom_R = d->size;
+    P.g.dom_Rin = d->kind == RASCAS_DOMAIN_SHELL ? d->inner : 0.0;
     if (ctx->has_mesh) {
         CK(cudaSetDevice(ctx->device));
         mesh_flags(ctx->mesh, &ctx->dom);
@@ -950,7 +956,8 @@ int rascas_load_batch(rascas_ctx* ctx, const rascas_model* models, int32_t nmode
     std::vector<double> cost(nmodels, 0.0);
     for (int m = 0; m < nmodels; ++m) {
         const rascas_model& md = models[m];
-        if (md.domain.kind < 0 || md.domain.kind > 2 || !(md.domain.size > 0.0) || !(md.nu_hi > md.nu_lo) ||
+        if (md.domain.kind < 0 || md.domain.kind > 3 || !(md.domain.size > 0.0) || !(md.nu_hi > md.nu_lo) ||
+            (md.domain.kind == RASCAS_DOMAIN_SHELL && !(md.domain.inner >= 0.0 && md.domain.inner < md.domain.size)) ||
             md.npackets < 0 || (md.npackets > 0 && (!md.packets.pos || !md.packets.dir || !md.packets.nu ||
                                                    !md.packets.id)))
             return fail(ctx, RASCAS_E_ARG, "load_batch: model " + std::to_string(m) + ": bad domain, axis or packets");
@@ -1013,6 +1020,7 @@ int rascas_load_batch(rascas_ctx* ctx, const rascas_model* models, int32_t nmode
         G.dom_kind = md.domain.kind;
         for (int ax = 0; ax < 3; ++ax) G.dom_c[ax] = md.domain.centre[ax];
         G.dom_R = md.domain.size;
+        G.dom_Rin = md.domain.kind == RASCAS_DOMAIN_SHELL ? md.domain.inner : 0.0;
         G.nu_lo = md.nu_lo; G.nu_inv_range = 1.0 / (md.nu_hi - md.nu_lo); G.nbin = nbin;
         G.spec = (float*)B.d_spec.p + (size_t)m * nbin;
         orec += M.rec.size(); oson += M.son.size(); onbr += M.nbr.size(); otop += M.top.size();

@@ -60,9 +60,10 @@ struct Geo {
     int top_level, max_level, nleaf, noct;
     double box_cm;
     float box_cm_f;
-    int dom_kind;          // 0 sphere, 1 slab (periodic x, y), 2 cube
+    int dom_kind;          // 0 sphere, 1 slab (periodic x, y), 2 cube, 3 shell
     double dom_c[3];
-    double dom_R;
+    double dom_R;          // sphere / shell outer radius, slab half-thickness, cube half side
+    double dom_Rin;        // shell inner radius
     // escape spectrum: bin = floor((nu - nu_lo) * nu_inv_range * nbin)
     double nu_lo, nu_inv_range;
     int nbin;

@@ -303,9 +303,10 @@ def uniform_medium(tree, box_cm, n_HI, T, n_dust=0.0, n_metal=0.0):
 
 @dataclass
 class Domain:
-    kind: int            # 0 sphere, 1 slab (periodic x,y), 2 cube
+    kind: int            # 0 sphere, 1 slab (periodic x,y), 2 cube, 3 shell
     centre: tuple = (0.5, 0.5, 0.5)
-    size: float = 0.45   # sphere radius / slab half-thickness / cube half-size (box units)
+    size: float = 0.45   # sphere / shell outer radius, slab half-thickness, cube half-size (box units)
+    inner: float = 0.0   # shell inner radius
 
 
 @dataclass
@@ -443,6 +444,43 @@ def deuterium_sphere(N_HI=2e19, T=1e4, d_over_h=3.0e-5, n_packets=10000, base=3,
     pk = point_source(n_packets, (0.5, 0.5, 0.5), nu_of(h.lambda_A), seed ^ 0xA5A5)
     lo, hi, nb = x_axis(h, T, -xrange, xrange, 200)
     return Workload("deuterium_sphere", med, Domain(0, (0.5, 0.5, 0.5), R), lines, Dust(sigma=4.0e-22),
+                    Physics(recoil=0, isotropic=0, seed=seed), Detector(lo, hi, nb), pk)
+
+
+def shell(tau0=1e4, T=1e4, inner=0.25, outer=0.45, n_packets=2000, v_max_kms=0.0, base=3, max_level=5,
+          seed_offset=0):
+    """Shell domain (Sect. 4: spheres, shells, cubes and slabs): uniform H I
+    between radii `inner` and `outer` (box units) about the box centre, line
+    centre optical depth tau0 across the shell (outer - inner), radial velocity
+    v_max r / outer, no dust; packets uniform in the shell volume, isotropic,
+    at line centre in the gas frame; packets escape through either sphere."""
+    tree = sphere_octree(base, max_level, radius=outer)
+    L = 1.0 * KPC_CM
+    line = lya()
+    n = density_for_tau0(line, T, tau0, (outer - inner) * L)
+    med = uniform_medium(tree, L, n, T)
+    if v_max_kms:
+        ctr = tree.leaf_centres() - 0.5
+        v = (v_max_kms * 1e5 / outer) * ctr
+        med.vx, med.vy, med.vz = (v[:, i].astype(np.float32) for i in range(3))
+    seed = RUN_SEED + 8 + seed_offset
+    rng = np.random.default_rng(seed ^ 0xA5A5)
+    r = (inner ** 3 + (outer ** 3 - inner ** 3) * rng.random(n_packets)) ** (1.0 / 3.0)
+    u = rng.normal(size=(n_packets, 3))
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    pos = 0.5 + r[:, None] * u
+    mu = 2.0 * rng.random(n_packets) - 1.0
+    phi = 2.0 * math.pi * rng.random(n_packets)
+    st = np.sqrt(1.0 - mu * mu)
+    d = np.stack([st * np.cos(phi), st * np.sin(phi), mu], 1)
+    vel = np.zeros((n_packets, 3))
+    if v_max_kms:
+        vel = (v_max_kms * 1e5 / outer) * (pos - 0.5)
+    beta = (d * vel).sum(1) / C_CGS
+    nu = nu_of(line.lambda_A) * (1.0 + beta)
+    pk = Packets(pos, d, nu, np.arange(n_packets, dtype=np.uint64))
+    lo, hi, nb = x_axis(line, T, -40.0, 40.0, 200)
+    return Workload("shell", med, Domain(3, (0.5, 0.5, 0.5), outer, inner), [line], Dust(sigma=4.0e-22),
                     Physics(recoil=0, isotropic=0, seed=seed), Detector(lo, hi, nb), pk)
 
 
