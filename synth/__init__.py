@@ -103,6 +103,16 @@ def feII_2374():
                 density=1, phase=1, channels=[(2.59e8, 2396.35)])
 
 
+def mgII_2796():
+    """Mg II 2796.35 A (A=2.60e8, f=0.608), resonant only."""
+    return Line("MgII_2796", 2796.35, 2.60e8, 0.608, 24.305 * AMU_CGS, density=1, phase=1)
+
+
+def mgII_2803():
+    """Mg II 2803.53 A (A=2.57e8, f=0.303), resonant only."""
+    return Line("MgII_2803", 2803.53, 2.57e8, 0.303, 24.305 * AMU_CGS, density=1, phase=1)
+
+
 def nu_of(lambda_A):
     return C_CGS / (lambda_A * 1e-8)
 
@@ -482,6 +492,32 @@ def shell(tau0=1e4, T=1e4, inner=0.25, outer=0.45, n_packets=2000, v_max_kms=0.0
     lo, hi, nb = x_axis(line, T, -40.0, 40.0, 200)
     return Workload("shell", med, Domain(3, (0.5, 0.5, 0.5), outer, inner), [line], Dust(sigma=4.0e-22),
                     Physics(recoil=0, isotropic=0, seed=seed), Detector(lo, hi, nb), pk)
+
+
+def mgII_wind(N_MgII=1e15, T=1e4, v_max_kms=200.0, n_packets=4000, base=3, max_level=5, seed_offset=0):
+    """Mg II doublet in a wind (Table 1; the doublet of Sect. 1): centre-to-edge
+    Mg II column N_MgII, a static core of radius R/10 and beyond it a radial
+    velocity rising linearly to v_max at R, no dust; packets at the centre, 2/3
+    at the 2796 and 1/3 at the 2803 line centre (the ratio of their oscillator
+    strengths), isotropic; escape spectrum over 2785-2815 A."""
+    tree = sphere_octree(base, max_level)
+    L = 1.0 * KPC_CM
+    R = 0.45
+    med = uniform_medium(tree, L, 0.0, T, n_metal=N_MgII / (R * L))
+    ctr = tree.leaf_centres() - 0.5
+    r = np.linalg.norm(ctr, axis=1)
+    rc = 0.1 * R
+    scale = np.where(r > rc, (r - rc) / (R - rc) / np.maximum(r, 1e-30), 0.0)
+    v = (v_max_kms * 1e5) * ctr * scale[:, None]
+    med.vx, med.vy, med.vz = (v[:, i].astype(np.float32) for i in range(3))
+    seed = RUN_SEED + 9 + seed_offset
+    l96, l03 = mgII_2796(), mgII_2803()
+    pk = point_source(n_packets, (0.5, 0.5, 0.5), nu_of(l96.lambda_A), seed ^ 0xA5A5)
+    rng = np.random.default_rng(seed)
+    red = rng.random(n_packets) < 1.0 / 3.0
+    pk.nu = np.where(red, nu_of(l03.lambda_A), nu_of(l96.lambda_A))
+    return Workload("mgII", med, Domain(0, (0.5, 0.5, 0.5), R), [l96, l03], Dust(sigma=4.0e-22),
+                    Physics(recoil=0, isotropic=0, seed=seed), Detector(nu_of(2815.0), nu_of(2785.0), 600), pk)
 
 
 PEEL_DIRS_3 = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0],
