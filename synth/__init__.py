@@ -399,20 +399,23 @@ def x_axis(line: Line, T, xlo, xhi, nbin):
     return nu0 + xlo * dnu, nu0 + xhi * dnu, nbin
 
 
-def slab(tau0=1e4, T=1e4, n_packets=2000, level=4, recoil=0, isotropic=1, seed_offset=0):
+def slab(tau0=1e4, T=1e4, n_packets=2000, level=4, recoil=0, isotropic=1, seed_offset=0, tau_dust=0.0,
+         albedo=0.32):
     """Static homogeneous H I slab (Sect. 3.4.2): (2^level)^3 grid, slab
     domain |z-1/2| <= 1/2 with periodic x,y, half-thickness line-centre
-    optical depth tau0, T, no dust, zero velocity; packets at the mid-plane
-    at x_in = 0, isotropic."""
+    optical depth tau0, T, zero velocity, half-thickness dust optical depth
+    tau_dust (albedo, g = 0.73); packets at the mid-plane at x_in = 0,
+    isotropic."""
     tree = uniform_octree(level)
     L = 1.0 * KPC_CM
     line = lya()
-    n = density_for_tau0(line, T, tau0, 0.5 * L)
-    med = uniform_medium(tree, L, n, T)
+    n = density_for_tau0(line, T, tau0, 0.5 * L) if tau0 > 0 else 0.0
+    dust = Dust(sigma=4.0e-22, albedo=albedo)
+    med = uniform_medium(tree, L, n, T, n_dust=tau_dust / (dust.sigma * 0.5 * L))
     seed = RUN_SEED + 0 + seed_offset
     pk = point_source(n_packets, (0.5, 0.5, 0.5), nu_of(line.lambda_A), seed ^ 0xA5A5)
     lo, hi, nb = x_axis(line, T, -60.0, 60.0, 200)
-    return Workload("slab", med, Domain(1, (0.5, 0.5, 0.5), 0.5), [line], Dust(),
+    return Workload("slab", med, Domain(1, (0.5, 0.5, 0.5), 0.5), [line], dust,
                     Physics(recoil=recoil, isotropic=isotropic, seed=seed), Detector(lo, hi, nb), pk)
 
 

@@ -261,3 +261,22 @@ def test_expanding_sphere_redshift():
     se = math.sqrt(res[1.0].var() / 400 + res[-1.0].var() / 400)
     assert m_out < -5 * res[1.0].std() / 20 and m_in > 5 * res[-1.0].std() / 20
     assert abs(m_out + m_in) < 4 * se
+
+
+def test_dusty_slab_resonant_trapping():
+    """Lya through an absorbing slab (Sect. 3.4.2, the escape fraction of a
+    dusty slab): resonant scattering lengthens the paths, so a line photon is
+    absorbed far more often than a continuum photon crossing the same dust;
+    without dust every packet escapes."""
+    n = 800
+    f = {}
+    for name, tau0, td in (("lya", 1e4, 0.1), ("continuum", 0.0, 0.1), ("no dust", 1e4, 0.0)):
+        wl = synth.slab(tau0=tau0, T=100.0, tau_dust=td, albedo=0.0, n_packets=n)
+        out, _ = oracle.Oracle(wl).run(threads=8)
+        f[name] = (out["status"] == oracle.ESCAPED).mean()
+    assert f["no dust"] == 1.0
+    # continuum from the mid-plane, isotropic: escape probability E2(tau_d)
+    from scipy.special import expn
+    se = math.sqrt(0.25 / n)
+    assert abs(f["continuum"] - expn(2, 0.1)) < 4 * se, f
+    assert f["lya"] < f["continuum"] - 6 * se, f
