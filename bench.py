@@ -38,8 +38,8 @@ WORKLOAD = ("static H I + dust sphere: 8^3 root refined to 64^3-equivalent octre
 # smsp__inst_executed.sum / scatterings of one ncu capture (65536 packets capped
 # at 1e4 scatterings each, profiles/k_propagate_sphere_tau1e6.md), and the
 # active lanes per warp instruction of the same capture
-INST_PER_SCATT = 34047718982 / 640157743
-LANES_PER_INST = 18.91
+INST_PER_SCATT = 34034899977 / 640157743
+LANES_PER_INST = 18.92
 # DRAM bytes per leaf visit of k_ray_tau on the synthetic galaxy
 # (dram__bytes_read.sum + dram__bytes_write.sum of one capture of 2^18 rays,
 # 59 732 805 leaf visits, profiles/k_ray_tau_galaxy.md)
