@@ -43,7 +43,7 @@ LANES_PER_INST = 18.92
 # DRAM bytes per leaf visit of k_ray_tau on the synthetic galaxy
 # (dram__bytes_read.sum + dram__bytes_write.sum of one capture of 2^18 rays,
 # 59 732 805 leaf visits, profiles/k_ray_tau_galaxy.md)
-RAY_DRAM_BYTES_PER_VISIT = (3.987451e9 + 16.796928e6) / 59732805
+RAY_DRAM_BYTES_PER_VISIT = (4.107982e9 + 49.11232e6) / 59732805
 ISSUE_PEAK_NOTE = "152 SMs x 4 schedulers x 1 warp-instruction/clock x SM clock"
 
 

@@ -768,9 +768,11 @@ __device__ __forceinline__ void ray_load(const RayInit* __restrict__ in, long lo
 
 // Persistent walk: each lane walks one ray leaf by leaf and takes the next ray
 // from the queue head as soon as its ray is done, so the lanes of a warp stay
-// busy whatever the spread of ray lengths.
+// busy whatever the spread of ray lengths. Eight blocks per SM (64 registers,
+// a few spilled values) hide more of the dependent leaf-record loads than the
+// five that the unconstrained register count allows.
 template <int NL>
-__global__ void __launch_bounds__(128) k_ray_tau(const Params* __restrict__ G, long long n,
+__global__ void __launch_bounds__(128, 8) k_ray_tau(const Params* __restrict__ G, long long n,
                                                  const RayInit* __restrict__ init, double* tau, int32_t* cells,
                                                  double* lens, int cap, int32_t* ncell) {
     const Params& P = *G;
