@@ -15,6 +15,8 @@ count up to floating-point summation order of whole-chunk tallies).
 Parity status of each function (pins live in tests/test_oracle_*.py):
   ora_philox4x32_10 .... pinned (published known-answer vectors)
   ora_voigt ............ pinned (quadrature of the H(a,x) integral, limits)
+  ora_faddeeva ......... pinned (scipy wofz, quadrature of H's integral, limits,
+                         normalisation, derivatives against differences)
   ora_u0/u_par sampler . pinned (chi-square against the normalised density)
   ora_mu_sample ........ pinned (CDF inversion identities, chi-square, <mu>=g)
   ora_onb .............. pinned (orthonormality)
@@ -79,6 +81,7 @@ class Cfg(C.Structure):
         ("nu_lo", C.c_double), ("nu_hi", C.c_double),
         ("nbin", C.c_int64), ("ndir", C.c_int64), ("npix", C.c_int64), ("cube", C.c_int64),
         ("dirs", (C.c_double * 3) * MAXDIR), ("fov", C.c_double), ("img_c", C.c_double * 3),
+        ("voigt", C.c_int64),
     ]
 
 
@@ -115,6 +118,10 @@ def lib():
             L.ora_word.argtypes = [u64, u64, u64]
             L.ora_voigt.restype = C.c_double
             L.ora_voigt.argtypes = [C.c_double, C.c_double]
+            L.ora_faddeeva.restype = None
+            L.ora_faddeeva.argtypes = [C.c_double, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            L.ora_faddeeva_derivs.restype = None
+            L.ora_faddeeva_derivs.argtypes = [C.c_double, C.c_double] + [C.POINTER(C.c_double)] * 3
             L.ora_u0.restype = C.c_double
             L.ora_u0.argtypes = [C.c_double, C.c_double]
             L.ora_mu_sample.restype = C.c_double
@@ -199,6 +206,7 @@ class Oracle:
         cf.recoil, cf.isotropic, cf.keep_dir = ph.recoil, ph.isotropic, ph.keep_direction
         cf.max_scatt, cf.max_steps = ph.max_scatt, ph.max_steps
         cf.x_gauss, cf.tau_stop, cf.seed = ph.x_gauss, ph.tau_stop, ph.seed
+        cf.voigt = getattr(ph, "voigt", 0)
         det = wl.detector
         cf.nu_lo, cf.nu_hi, cf.nbin = det.nu_lo, det.nu_hi, det.nbin
         dirs = np.asarray(det.dirs, dtype=np.float64).reshape(-1, 3)
@@ -382,8 +390,25 @@ def word(seed, pid, n):
     return lib().ora_word(seed, pid, n)
 
 
-def voigt(a, x):
+def voigt(a, x, method=0):
+    """H(a, x): method 0 the Tasitsiomi (2006) form, 1 the Faddeeva function."""
+    if method == 1:
+        return faddeeva(a, x).real
     return lib().ora_voigt(float(a), float(x))
+
+
+def faddeeva(a, x):
+    """w(x + ia) by the trapezoidal rule with its pole residue (Re w = H)."""
+    re, im = C.c_double(), C.c_double()
+    lib().ora_faddeeva(float(a), float(x), C.byref(re), C.byref(im))
+    return complex(re.value, im.value)
+
+
+def faddeeva_derivs(a, x):
+    """(H, dH/da, dH/dx) of the Faddeeva H."""
+    v = [C.c_double() for _ in range(3)]
+    lib().ora_faddeeva_derivs(float(a), float(x), *[C.byref(t) for t in v])
+    return tuple(t.value for t in v)
 
 
 def u0(x, a):

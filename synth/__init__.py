@@ -336,6 +336,7 @@ class Physics:
     max_steps: int = 0         # 0: no cap
     tau_stop: float = 50.0     # peeling rays stop once tau exceeds this (contribution < e^-tau_stop)
     seed: int = 0
+    voigt: int = 0             # H(a,x): 0 Tasitsiomi (2006), 1 the Faddeeva function (accurate option)
 
 
 @dataclass
