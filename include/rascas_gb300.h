@@ -62,6 +62,7 @@ enum { RASCAS_PK_ACTIVE = 0, RASCAS_PK_ESCAPED = 1, RASCAS_PK_ABSORBED = 2,
        RASCAS_PK_CAPPED = 3, RASCAS_PK_ERROR = 4 };
 
 enum { RASCAS_DOMAIN_SPHERE = 0, RASCAS_DOMAIN_SLAB = 1, RASCAS_DOMAIN_CUBE = 2, RASCAS_DOMAIN_SHELL = 3 };
+enum { RASCAS_VOIGT_TASITSIOMI = 0, RASCAS_VOIGT_FADDEEVA = 1 };
 
 enum { RASCAS_TALLY_SPECTRUM = 0,   /* [nbin] escape spectrum, 1 per escaped packet */
        RASCAS_TALLY_PEEL_SPECTRA = 1, /* [ndir][nbin] peeled flux per sr */
@@ -204,6 +205,18 @@ int rascas_load_octree(rascas_ctx *ctx, const rascas_octree *tree, int mem);
 int rascas_set_domain(rascas_ctx *ctx, const rascas_domain *dom);
 int rascas_set_lines(rascas_ctx *ctx, const rascas_line *lines, int32_t nline, const rascas_dust *dust);
 int rascas_set_physics(rascas_ctx *ctx, const rascas_physics *phys);
+/* How every later call evaluates the Hjerting-Voigt function H(a, x) of the
+ * line opacities (Sect. 3.3.2 weighs several approximations against an
+ * accurate evaluation):
+ *   RASCAS_VOIGT_TASITSIOMI (default): Tasitsiomi (2006) eqs. 7-8, the
+ *     paper's fast form, ~1 % from H for Lya at 1e4 K and worse at larger a;
+ *   RASCAS_VOIGT_FADDEEVA: H = Re w(x + ia) of the Faddeeva function, by the
+ *     trapezoidal rule on w's integral with its pole residue in closed form,
+ *     within ~5e-7 relative in FP32 for 0 <= a <= 1 at every x.
+ * Applies to rascas_propagate, _ray_tau, _trace, _propagate_batch, the
+ * peeling tallies, rascas_peel_adjoint and rascas_eval_voigt.  The context
+ * keeps the method; RASCAS_E_ARG for any other value. */
+int rascas_set_voigt(rascas_ctx *ctx, int method);
 /* Also zeroes the tallies (their shapes follow the detector). */
 int rascas_set_detector(rascas_ctx *ctx, const rascas_detector *det);
 int rascas_zero_tallies(rascas_ctx *ctx);
@@ -248,7 +261,8 @@ int rascas_trace(rascas_ctx *ctx, const rascas_packets_in *in, int64_t n, int32_
 
 /* ---- device-function probes (parity of the building blocks) ------------ */
 
-/* H(a, x) of the hot path (Tasitsiomi 2006 form, Sect. 3.3.2) at a[i], x[i]. */
+/* H(a, x) at a[i], x[i] by the context's method (rascas_set_voigt; default
+ * the Tasitsiomi 2006 form of the hot path, Sect. 3.3.2). */
 int rascas_eval_voigt(rascas_ctx *ctx, int64_t n, const float *a, const double *x, float *H, int mem);
 /* One u_par draw (Sect. 3.3.3) per i for frequency x[i], Voigt parameter a[i],
  * on the stream of packet id[i] starting at draw 0; ndraw[i] = words used. */

@@ -17,6 +17,7 @@ from . import build as _build
 HOST, DEVICE = 0, 1
 PK_ACTIVE, PK_ESCAPED, PK_ABSORBED, PK_CAPPED, PK_ERROR = 0, 1, 2, 3, 4
 DOMAIN_SPHERE, DOMAIN_SLAB, DOMAIN_CUBE, DOMAIN_SHELL = 0, 1, 2, 3
+VOIGT_TASITSIOMI, VOIGT_FADDEEVA = 0, 1
 TALLY_SPECTRUM, TALLY_PEEL_SPECTRA, TALLY_PEEL_IMAGES, TALLY_PEEL_CUBES = 0, 1, 2, 3
 MAX_LINES, MAX_CHAN, MAX_DIRS = 4, 4, 8
 C_CGS = 2.99792458e10
@@ -127,6 +128,7 @@ def lib():
             "rascas_ray_tau": [vp, i64, vp, vp, vp, vp, vp, vp, i32, vp, C.c_int],
             "rascas_trace": [vp, C.POINTER(PacketsIn), i64, i32, vp, vp, C.c_int],
             "rascas_eval_voigt": [vp, i64, vp, vp, vp, C.c_int],
+            "rascas_set_voigt": [vp, C.c_int],
             "rascas_sample_upar": [vp, i64, vp, vp, vp, vp, vp, C.c_int],
             "rascas_update_fields": [vp, vp, vp, vp, vp, vp, vp, vp, C.c_int],
             "rascas_peel_adjoint": [vp, C.POINTER(PacketsIn), i64, vp, vp, vp, vp, C.c_int],
@@ -256,6 +258,10 @@ class Context:
         self.nline = len(lines)
         self._ck(self._L.rascas_set_lines(self._h, arr, len(lines), C.byref(d)), "set_lines")
 
+    def set_voigt(self, method):
+        """H(a,x) method of every later call: VOIGT_TASITSIOMI or VOIGT_FADDEEVA."""
+        self._ck(self._L.rascas_set_voigt(self._h, int(method)), "set_voigt")
+
     def set_physics(self, recoil=1, isotropic=0, keep_dir=0, x_gauss=8.0, max_scatt=0, max_steps=0,
                     tau_stop=50.0, seed=0, fail_on_cap=0):
         p = Physics()
@@ -295,6 +301,7 @@ class Context:
         ph = wl.physics
         self.set_physics(ph.recoil, ph.isotropic, ph.keep_direction, ph.x_gauss, ph.max_scatt, ph.max_steps,
                          ph.tau_stop, ph.seed)
+        self.set_voigt(getattr(ph, "voigt", VOIGT_TASITSIOMI))
         d = wl.detector
         self.set_detector(d.nu_lo, d.nu_hi, d.nbin, d.dirs, d.npix, d.fov, d.centre, d.cube)
 

@@ -449,6 +449,32 @@ int rascas_set_lines(rascas_ctx* ctx, const rascas_line* lines, int32_t nline, c
     return RASCAS_OK;
 }
 
+// the walk kernels built for the H(a,x) method of the parameters
+static cudaError_t walk_propagate(const rg::Params& P, const rg::PacketsIn& in, const rg::PacketsOut& out,
+                                  const rg::TraceOut& tr, int grid, int block, cudaStream_t st) {
+    return P.voigt == RASCAS_VOIGT_FADDEEVA ? rg::launch_propagate_fad(P, in, out, tr, grid, block, st)
+                                            : rg::launch_propagate(P, in, out, tr, grid, block, st);
+}
+static cudaError_t walk_peel(const rg::Params& P, int sms, cudaStream_t st) {
+    return P.voigt == RASCAS_VOIGT_FADDEEVA ? rg::launch_peel_fad(P, sms, st) : rg::launch_peel(P, sms, st);
+}
+static cudaError_t walk_ray_tau(const rg::Params& P, long long n, const double* pos, const double* dir,
+                                const double* nu, double* tau, int32_t* cells, double* lens, int cap,
+                                int32_t* ncell, rg::RayInit* init, int sms, cudaStream_t st) {
+    return P.voigt == RASCAS_VOIGT_FADDEEVA
+               ? rg::launch_ray_tau_fad(P, n, pos, dir, nu, tau, cells, lens, cap, ncell, init, sms, st)
+               : rg::launch_ray_tau(P, n, pos, dir, nu, tau, cells, lens, cap, ncell, init, sms, st);
+}
+
+int rascas_set_voigt(rascas_ctx* ctx, int method) {
+    if (!ctx) return RASCAS_E_ARG;
+    if (method != RASCAS_VOIGT_TASITSIOMI && method != RASCAS_VOIGT_FADDEEVA)
+        return fail(ctx, RASCAS_E_ARG, "voigt: unknown method");
+    ctx->P.voigt = method;
+    ++ctx->version;
+    return RASCAS_OK;
+}
+
 int rascas_set_physics(rascas_ctx* ctx, const rascas_physics* ph) {
     if (!ctx || !ph) return RASCAS_E_ARG;
     if (!(ph->x_gauss > 0.0) || ph->max_scatt < 0 || ph->max_steps < 0 || !(ph->tau_stop > 0.0))
@@ -664,8 +690,8 @@ int run_propagate(rascas_ctx* ctx, const rascas_packets_in* in, int64_t n, const
         CK(cudaMemcpyAsync(ctx->d_params.p, &P, sizeof(Params), cudaMemcpyHostToDevice, st));
         for (long long round = 0;; ++round) {
             CK(cudaMemsetAsync(ctl, 0, 4 * sizeof(unsigned long long), st));
-            CK(rg::launch_propagate(P, din, dout, tr, grid, block, st));
-            CK(rg::launch_peel(P, ctx->sms, st));
+            CK(walk_propagate(P, din, dout, tr, grid, block, st));
+            CK(walk_peel(P, ctx->sms, st));
             unsigned int parked = 0;
             CK(cudaMemcpyAsync(&parked, P.suspended, sizeof(parked), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
@@ -676,7 +702,7 @@ int run_propagate(rascas_ctx* ctx, const rascas_packets_in* in, int64_t n, const
         CK(cudaMemcpyAsync(ctx->d_params.p, &P, sizeof(Params), cudaMemcpyHostToDevice, st));
         if (n > 0) {
             int grid = persistent_grid(ctx, false);
-            CK(rg::launch_propagate(P, din, dout, tr, grid, rg::propagate_block_size(), st));
+            CK(walk_propagate(P, din, dout, tr, grid, rg::propagate_block_size(), st));
         }
     }
     if (stats) CK(cudaEventRecord(e1, st));
@@ -795,7 +821,7 @@ int rascas_ray_tau(rascas_ctx* ctx, int64_t n, const double* pos, const double* 
     CK(cudaMemcpyAsync(ctx->d_params.p, &ctx->P, sizeof(Params), cudaMemcpyHostToDevice, st));
     CK(ctx->ray_init.ensure(N * sizeof(rg::RayInit)));
     CK(cudaMemsetAsync(ctx->P.head, 0, sizeof(unsigned long long), st));
-    CK(rg::launch_ray_tau(ctx->P, (long long)n, dpos, ddir, dnu, dtau, dcells, dlens, cap,
+    CK(walk_ray_tau(ctx->P, (long long)n, dpos, ddir, dnu, dtau, dcells, dlens, cap,
                           (mem == RASCAS_HOST || ncell) ? dncell : nullptr, (rg::RayInit*)ctx->ray_init.p, ctx->sms,
                           st));
     if (mem == RASCAS_HOST) {
@@ -823,12 +849,12 @@ int rascas_eval_voigt(rascas_ctx* ctx, int64_t n, const float* a, const double* 
         float* dH = da + N;
         CK(cudaMemcpyAsync(dx, x, N * 8, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(da, a, N * 4, cudaMemcpyHostToDevice, st));
-        CK(rg::launch_eval_voigt((long long)n, da, dx, dH, st));
+        CK(rg::launch_eval_voigt((long long)n, da, dx, dH, ctx->P.voigt, st));
         CK(cudaMemcpyAsync(H, dH, N * 4, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         return RASCAS_OK;
     }
-    CK(rg::launch_eval_voigt((long long)n, a, x, H, st));
+    CK(rg::launch_eval_voigt((long long)n, a, x, H, ctx->P.voigt, st));
     return RASCAS_OK;
 }
 
@@ -912,7 +938,7 @@ int rascas_propagate_noalloc(rascas_ctx* ctx, const rascas_packets_in* in, int64
         CK(cudaMemcpyAsync(dir, in->dir, 3 * N * 8, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(nu, in->nu, N * 8, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(id, in->id, N * 8, cudaMemcpyHostToDevice, st));
-        CK(rg::launch_propagate(P, din, dout, tr, persistent_grid(ctx, false), rg::propagate_block_size(), st));
+        CK(walk_propagate(P, din, dout, tr, persistent_grid(ctx, false), rg::propagate_block_size(), st));
         if (out) {
             if (out->status) CK(cudaMemcpyAsync(out->status, ost, N * 4, cudaMemcpyDeviceToHost, st));
             if (out->nscatt) CK(cudaMemcpyAsync(out->nscatt, ons, N * 8, cudaMemcpyDeviceToHost, st));
@@ -1089,7 +1115,7 @@ int rascas_propagate_batch(rascas_ctx* ctx, int32_t mode, rascas_run_stats* stat
             CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             cudaError_t e1c = cudaMemsetAsync(ctx->d_counters.p, 0, cnt_bytes, st);
             cudaError_t e2c = cudaMemsetAsync(B.d_spec.p, 0, spec_bytes, st);
-            cudaError_t e3c = rg::launch_propagate(P, in, out, tr, grid, block, st);
+            cudaError_t e3c = walk_propagate(P, in, out, tr, grid, block, st);
             cudaError_t ec = cudaStreamEndCapture(st, &g);
             if (e1c != cudaSuccess || e2c != cudaSuccess || e3c != cudaSuccess || ec != cudaSuccess)
                 return cuda_fail(ctx, ec != cudaSuccess ? ec : (e3c != cudaSuccess ? e3c : e1c), "batch graph capture");
@@ -1117,7 +1143,7 @@ int rascas_propagate_batch(rascas_ctx* ctx, int32_t mode, rascas_run_stats* stat
             long long blocks = (n + block - 1) / block;
             int gk = (int)(blocks < grid ? blocks : grid);
             CK(cudaMemsetAsync(P.head, 0, sizeof(unsigned long long), st));
-            CK(rg::launch_propagate(Pk, ink, out, tr, gk, block, st));
+            CK(walk_propagate(Pk, ink, out, tr, gk, block, st));
         }
     }
     CK(cudaEventRecord(e1, st));

@@ -126,6 +126,7 @@ struct Params {
     unsigned int* suspended;          // warps suspended this round
     double dir_inv[kMaxDirs][3];      // 1 / dirs (0 where a component is 0)
     float dir_kp[kMaxDirs][3][2];     // dirs as FP32 pairs
+    int voigt;                        // H(a,x) method of the walk kernels (host side: picks the build)
     // run scratch
     unsigned long long* counters;  // [CNT_N]
     unsigned long long* head;      // work-queue head
@@ -161,9 +162,13 @@ struct TraceOut {
     int max_events;
 };
 
-// launchers (kernels.cu)
+// launchers (kernels.cu).  The three that run the walk exist twice: the plain
+// names launch kernels that evaluate H(a,x) by Tasitsiomi's form, the _fad
+// names kernels that evaluate the Faddeeva function (Params::voigt selects).
 cudaError_t launch_propagate(const Params& P, const PacketsIn& in, const PacketsOut& out,
                              const TraceOut& tr, int grid, int block, cudaStream_t st);
+cudaError_t launch_propagate_fad(const Params& P, const PacketsIn& in, const PacketsOut& out,
+                                 const TraceOut& tr, int grid, int block, cudaStream_t st);
 // start state of one ray of rascas_ray_tau, written by a set-up pass
 struct RayInit {
     double p[3], k[3], inv[3];
@@ -178,15 +183,19 @@ static_assert(sizeof(RayInit) % 16 == 0, "RayInit keeps 16-byte alignment");
 // deferred peeling: walk and tally the records of one round (reads the
 // record count from P.peel_count; P.peel_head must be zero on entry)
 cudaError_t launch_peel(const Params& P, int sms, cudaStream_t st);
+cudaError_t launch_peel_fad(const Params& P, int sms, cudaStream_t st);
 // bytes of one suspended packet state for nline lines
 size_t packet_save_bytes(int nline);
 
 cudaError_t launch_ray_tau(const Params& P, long long n, const double* pos, const double* dir,
                            const double* nu, double* tau, int32_t* cells, double* lens, int cap, int32_t* ncell,
                            RayInit* init, int sms, cudaStream_t st);
+cudaError_t launch_ray_tau_fad(const Params& P, long long n, const double* pos, const double* dir,
+                               const double* nu, double* tau, int32_t* cells, double* lens, int cap, int32_t* ncell,
+                               RayInit* init, int sms, cudaStream_t st);
 cudaError_t launch_pack_fields(long long n, const float* nh, const float* vx, const float* vy, const float* vz,
                                const float* T, const float* nd, const float* nm, float4* rec, cudaStream_t st);
-cudaError_t launch_eval_voigt(long long n, const float* a, const double* x, float* H, cudaStream_t st);
+cudaError_t launch_eval_voigt(long long n, const float* a, const double* x, float* H, int method, cudaStream_t st);
 cudaError_t launch_sample_upar(const Params& P, long long n, const double* x, const float* a,
                                const uint64_t* id, float* u, int32_t* ndraw, cudaStream_t st);
 cudaError_t noalloc_scratch(int device, void** ptr, size_t* bytes);

@@ -19,7 +19,20 @@
 #include "device.cuh"
 #include "internal.h"
 
+// This file is compiled twice: the kernels of each build evaluate H(a,x) by
+// one method (device.cuh, kFaddeeva), live in their own inline namespace (so
+// the two builds' kernels never share a symbol) and are launched through
+// launchers whose names carry the method (internal.h).
+#if RG_FADDEEVA
+#define RG_KVAR voigt_faddeeva
+#define RG_SFX(name) name##_fad
+#else
+#define RG_KVAR voigt_tasitsiomi
+#define RG_SFX(name) name
+#endif
+
 namespace rg {
+inline namespace RG_KVAR {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr double kInf = __builtin_huge_val();
@@ -177,7 +190,8 @@ __device__ __forceinline__ bool ray_grad_step(const Params& P, Ray<NL>& r, float
         const float a = L.a_pref * rs;
         const float x = xh[i];
         float H, Ha, Hx;
-        voigt_derivs(a, x, H, Ha, Hx);
+        if constexpr (kFaddeeva) faddeeva_derivs(a, x, H, Ha, Hx);
+        else voigt_derivs(a, x, H, Ha, Hx);
         const float s0 = L.sig_pref * rs;
         const float nX = (L.dens == 1 ? r1.z : r0.x) * L.abund;
         if (L.dens != 1) dk[0] += L.abund * s0 * H;
@@ -956,6 +970,7 @@ __global__ void __launch_bounds__(128) k_peel(const Params* __restrict__ G) {
     flush(P, nl, CNT_NBOR_LOADS);
 }
 
+#if !RG_FADDEEVA
 __global__ void k_pack_fields(long long n, const float* nh, const float* vx, const float* vy, const float* vz,
                               const float* T, const float* nd, const float* nm, float4* rec) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -965,16 +980,16 @@ __global__ void k_pack_fields(long long n, const float* nh, const float* vx, con
     rec[2 * i + 1] = make_float4(T[i], nd[i], nm ? nm[i] : 0.0f, flags);
 }
 
-cudaError_t launch_pack_fields(long long n, const float* nh, const float* vx, const float* vy, const float* vz,
-                               const float* T, const float* nd, const float* nm, float4* rec, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    k_pack_fields<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, nh, vx, vy, vz, T, nd, nm, rec);
-    return cudaGetLastError();
-}
-
-__global__ void k_eval_voigt(long long n, const float* a, const double* x, float* H) {
+// H(a, x) by either method (method 1: the Faddeeva function)
+__global__ void k_eval_voigt(long long n, const float* a, const double* x, float* H, int method) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) H[i] = voigt_h(a[i], x[i]);
+    if (i >= n) return;
+    if (method == 1) {
+        const float xh = (float)x[i];
+        H[i] = faddeeva_h(a[i], xh, (float)(x[i] - (double)xh));
+    } else {
+        H[i] = voigt_h(a[i], x[i]);
+    }
 }
 
 __global__ void k_sample_upar(Params P, long long n, const double* x, const float* a, const uint64_t* id,
@@ -991,41 +1006,22 @@ __global__ void k_sample_upar(Params P, long long n, const double* x, const floa
     nd[i] = err ? -1 : (int32_t)rng.n;
 }
 
+#endif  // !RG_FADDEEVA
+
+}  // inline namespace RG_KVAR
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-int propagate_block_size() { return 128; }
-
 // draw rings, the u0 coefficient cache of each line, the event counters
-size_t propagate_smem(int nline, int block) {
+static size_t smem_bytes(int nline, int block) {
     return (size_t)(kRing + nline * 6) * block * sizeof(float) + (size_t)block * sizeof(Tallies);
-}
-
-template <int NL, bool PEEL, bool BATCH>
-static int occ(int block) {
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate<NL, PEEL, BATCH, false>, block,
-                                                  propagate_smem(NL, block));
-    return nb;
-}
-
-int propagate_blocks_per_sm(int block, bool peel) {
-    return peel ? occ<1, true, false>(block) : occ<1, false, false>(block);
-}
-
-int propagate_batch_blocks_per_sm(int nline, int block) {
-    switch (nline) {
-        case 1: return occ<1, false, true>(block);
-        case 2: return occ<2, false, true>(block);
-        case 3: return occ<3, false, true>(block);
-        default: return occ<4, false, true>(block);
-    }
 }
 
 template <int NL>
 static cudaError_t launch_nl(const Params& P, const PacketsIn& in, const PacketsOut& out, const TraceOut& tr,
                              int grid, int block, cudaStream_t st) {
-    size_t smem = propagate_smem(NL, block);
+    size_t smem = smem_bytes(NL, block);
     // per-event traces are recorded by single-model runs without peeling only
     if (tr.nev && (P.nmodels > 0 || P.ndir > 0)) return cudaErrorInvalidValue;
     if (P.nmodels > 0) k_propagate<NL, false, true, false><<<grid, block, smem, st>>>(P, in, out, tr);
@@ -1035,7 +1031,7 @@ static cudaError_t launch_nl(const Params& P, const PacketsIn& in, const Packets
     return cudaGetLastError();
 }
 
-cudaError_t launch_propagate(const Params& P, const PacketsIn& in, const PacketsOut& out, const TraceOut& tr,
+cudaError_t RG_SFX(launch_propagate)(const Params& P, const PacketsIn& in, const PacketsOut& out, const TraceOut& tr,
                              int grid, int block, cudaStream_t st) {
     switch (P.nline) {
         case 1: return launch_nl<1>(P, in, out, tr, grid, block, st);
@@ -1060,7 +1056,7 @@ static int peel_occ() {
     return nb > 0 ? nb : 1;
 }
 
-cudaError_t launch_peel(const Params& P, int sms, cudaStream_t st) {
+cudaError_t RG_SFX(launch_peel)(const Params& P, int sms, cudaStream_t st) {
     const Params* G = P.self;
     switch (P.nline) {
         case 1: k_peel<1><<<sms * peel_occ<1>(), 128, 0, st>>>(G); break;
@@ -1072,17 +1068,8 @@ cudaError_t launch_peel(const Params& P, int sms, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-size_t packet_save_bytes(int nline) {
-    switch (nline) {
-        case 1: return sizeof(Packet<1>);
-        case 2: return sizeof(Packet<2>);
-        case 3: return sizeof(Packet<3>);
-        default: return sizeof(Packet<4>);
-    }
-}
-
 // the queue head P.head must be zero on entry
-cudaError_t launch_ray_tau(const Params& P, long long n, const double* pos, const double* dir, const double* nu,
+cudaError_t RG_SFX(launch_ray_tau)(const Params& P, long long n, const double* pos, const double* dir, const double* nu,
                            double* tau, int32_t* cells, double* lens, int cap, int32_t* ncell, RayInit* init,
                            int sms, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
@@ -1109,9 +1096,51 @@ cudaError_t launch_ray_tau(const Params& P, long long n, const double* pos, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_eval_voigt(long long n, const float* a, const double* x, float* H, cudaStream_t st) {
+#if !RG_FADDEEVA
+int propagate_block_size() { return 128; }
+
+size_t propagate_smem(int nline, int block) { return smem_bytes(nline, block); }
+
+template <int NL, bool PEEL, bool BATCH>
+static int occ(int block) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_propagate<NL, PEEL, BATCH, false>, block,
+                                                  smem_bytes(NL, block));
+    return nb;
+}
+
+int propagate_blocks_per_sm(int block, bool peel) {
+    return peel ? occ<1, true, false>(block) : occ<1, false, false>(block);
+}
+
+int propagate_batch_blocks_per_sm(int nline, int block) {
+    switch (nline) {
+        case 1: return occ<1, false, true>(block);
+        case 2: return occ<2, false, true>(block);
+        case 3: return occ<3, false, true>(block);
+        default: return occ<4, false, true>(block);
+    }
+}
+
+size_t packet_save_bytes(int nline) {
+    switch (nline) {
+        case 1: return sizeof(Packet<1>);
+        case 2: return sizeof(Packet<2>);
+        case 3: return sizeof(Packet<3>);
+        default: return sizeof(Packet<4>);
+    }
+}
+
+cudaError_t launch_pack_fields(long long n, const float* nh, const float* vx, const float* vy, const float* vz,
+                               const float* T, const float* nd, const float* nm, float4* rec, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    k_eval_voigt<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, a, x, H);
+    k_pack_fields<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, nh, vx, vy, vz, T, nd, nm, rec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval_voigt(long long n, const float* a, const double* x, float* H, int method, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_eval_voigt<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, a, x, H, method);
     return cudaGetLastError();
 }
 
@@ -1121,5 +1150,7 @@ cudaError_t launch_sample_upar(const Params& P, long long n, const double* x, co
     k_sample_upar<<<(unsigned)((n + 127) / 128), 128, kRing * 128 * sizeof(uint32_t), st>>>(P, n, x, a, id, u, nd);
     return cudaGetLastError();
 }
+
+#endif  // !RG_FADDEEVA
 
 }  // namespace rg

@@ -13,9 +13,10 @@ pytestmark = pytest.mark.gpu
 FIELDS = ["n_HI", "vx", "vy", "vz", "T", "n_dust"]
 
 
-def _workload(n=300):
+def _workload(n=300, voigt=0):
     wl = synth.expanding_sphere(N_HI=3e17, tau_dust=0.3, n_packets=n, npix=8, nchan=24, base=3, max_level=4)
     wl.physics.tau_stop = float("inf")
+    wl.physics.voigt = voigt
     return wl
 
 
@@ -33,15 +34,17 @@ def _state_from(o, rec, pid):
     return st
 
 
-def test_gpu_adjoint_matches_oracle():
+@pytest.mark.parametrize("voigt", [0, 1])
+def test_gpu_adjoint_matches_oracle(voigt):
     """The GPU adjoint replays the GPU's own scattering record; the oracle
     rebuilds that record step by step from the GPU trace (each event replayed
     from the GPU's state, as in the per-step parity tests) and differentiates
-    it in FP64.  Whole histories are not compared: FP32 velocity sampling
+    it in FP64 (voigt 1: both sides with the Faddeeva H and its derivatives).
+    Whole histories are not compared: FP32 velocity sampling
     makes the continuous state drift by ~1e-5 Doppler widths over thousands of
     scatterings while the discrete history stays the same."""
     import paper_2001_11252_gb300 as rg
-    wl = _workload(200)
+    wl = _workload(200, voigt)
     ctx = rg.Context(0)
     ctx.setup(wl)
     o = oracle.Oracle(wl)

@@ -1,0 +1,131 @@
+"""The accurate H(a,x) option (the Faddeeva function; Sect. 3.3.2 weighs the
+fast approximations against it) on the GPU, through the C ABI, against the
+FP64 oracle's own Faddeeva evaluation (pinned in test_oracle_faddeeva.py).
+
+Tolerances: H within 2e-6 relative (the FP32 evaluation carries ~5e-7: a sum
+of positive node terms and two bounded correction terms, each a few FP32
+roundings); walks bit-exact; tau within 2e-6; whole runs coupled as in
+test_gpu_parity.py."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import context, gpu_run, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+FAD = 1
+
+
+def _fad(wl):
+    wl.physics.voigt = FAD
+    return wl
+
+
+def test_faddeeva_eval_matches_oracle():
+    wl = synth.slab(n_packets=1)
+    ctx = context(_fad(wl))
+    rng = np.random.default_rng(5)
+    n = 6000
+    a = (10 ** rng.uniform(-6, 0, n)).astype(np.float32)
+    x = np.concatenate([rng.uniform(-9, 9, n // 2), rng.uniform(-3, 3, n // 4),
+                        np.sign(rng.uniform(-1, 1, n // 4)) * 10 ** rng.uniform(0, 5, n // 4)])
+    x[:12] = [0.0, 0.25, -0.25, 0.5, 3.25, 7.99, 8.0, 8.01, 5.5, -11.0, 1e3, 1e5]
+    a[:12] = [4.717e-4, 1e-6, 0.3, 1e-3, 1e-6, 1e-2, 1e-2, 1e-2, 1.0, 0.1, 1e-4, 4.717e-4]
+    H = ctx.eval_voigt(a, x).astype(np.float64)
+    ref = np.array([oracle.faddeeva(float(ai), float(xi)).real for ai, xi in zip(a, x)])
+    rel = np.abs(H / ref - 1)
+    print("Faddeeva H: max rel %.3g at a=%g x=%g" % (rel.max(), a[rel.argmax()], x[rel.argmax()]))
+    assert rel.max() < 2e-6, (rel.max(), x[rel.argmax()], a[rel.argmax()])
+    # the default method is Tasitsiomi's form, ~1 % away
+    ctx.set_voigt(0)
+    Ht = ctx.eval_voigt(a[:12], x[:12]).astype(np.float64)
+    assert np.max(np.abs(Ht / ref[:12] - 1)) > 1e-3
+
+
+@pytest.mark.parametrize("which", ["sphere", "galaxy"])
+def test_faddeeva_ray_walk(which):
+    """Same leaves and path lengths as the oracle, tau within 2e-6."""
+    if which == "sphere":
+        wl = synth.sphere(tau0=1e4, T=100.0, tau_dust=0.5, n_packets=1, base=3, max_level=6)
+    else:
+        wl = synth.galaxy(n_leaf=150_000, grid_level=6, base_level=4, max_level=10, n_packets=10, npix=8, nchan=8)
+    ctx = context(_fad(wl))
+    o = oracle.Oracle(wl)
+    rng = np.random.default_rng(12)
+    n = 300
+    pos = rng.uniform(0.1, 0.9, (n, 3))
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    nu0 = synth.nu_of(wl.lines[0].lambda_A)
+    dnu = synth.doppler_width(wl.lines[0], 1e4)
+    nu = nu0 + rng.uniform(-10, 10, n) * dnu
+    cap = 4096
+    tau, cells, lens, ncell = ctx.ray_tau(pos, d, nu, cap=cap)
+    worst = 0.0
+    for i in range(n):
+        t_o, c_o, l_o, n_o = o.ray_tau(pos[i], d[i], nu[i], cap=cap)
+        assert ncell[i] == n_o
+        m = min(n_o, cap)
+        assert np.array_equal(cells[i, :m], c_o[:m]), i
+        assert np.array_equal(lens[i, :m], l_o[:m]), i
+        worst = max(worst, abs(tau[i] - t_o) / (abs(t_o) + 1e-300))
+    print(which, "Faddeeva tau: max rel %.3g" % worst)
+    assert worst < 2e-6
+
+
+def test_faddeeva_mean_free_path_gpu():
+    """Line-centre mean free path R / (tau0 exp(a^2) erfc(a)) at T = 1 K."""
+    from scipy.special import erfcx
+    n, tau0, T = 1 << 16, 10.0, 1.0
+    wl = synth.sphere(tau0=tau0, T=T, n_packets=n, base=3, max_level=3)
+    wl.physics.max_scatt = 1
+    ctx = context(_fad(wl))
+    g, st = gpu_run(ctx, wl.packets, device=True)
+    first = g["path"][g["status"] == oracle.CAPPED]
+    ln = wl.lines[0]
+    a = ln.A_ul / (4 * math.pi * synth.doppler_width(ln, T))
+    lam = wl.domain.size / (tau0 * erfcx(a))
+    assert first.size > 0.999 * n
+    assert abs(first.mean() / lam - 1) < 4 / math.sqrt(first.size)
+
+
+def test_faddeeva_replay_per_step():
+    """GPU events replayed by the oracle (both with the Faddeeva H) land on
+    the same leaf with the same draw count and status."""
+    from test_gpu_parity import _replay
+    wl = _fad(synth.sphere(tau0=1e4, T=100.0, tau_dust=1.0, n_packets=64))
+    st = _replay(wl, 64, 200)
+    print("Faddeeva replay", st)
+    assert st["steps"] > 1000
+    assert st["mismatch"] <= 0.002 * st["steps"] + 2
+    assert st["pos"] < 1e-6
+    assert st["x"] < 3e-5
+
+
+@pytest.mark.parametrize("which", ["lya_100K", "feII"])
+def test_faddeeva_run_matches_oracle(which):
+    """Coupled whole runs: Lya through a 100 K sphere (a ~ 4.7e-3) and the
+    Fe II UV1 fluorescent sphere."""
+    if which == "feII":
+        n = 2000
+        wl = synth.feII_sphere(tau0=1e4, n_packets=n)
+    else:
+        n = 300
+        wl = synth.sphere(tau0=1e4, T=100.0, tau_dust=0.5, n_packets=n)
+    ctx = context(_fad(wl))
+    g, st = gpu_run(ctx, wl.packets)
+    r, _ = oracle_run(wl)
+    same = (g["nscatt"] == r["nscatt"]).mean()
+    mg, mr = g["nscatt"].mean(), r["nscatt"].mean()
+    print("%s Faddeeva: identical %.4f <N> %.2f vs %.2f" % (which, same, mg, mr))
+    assert st["errors"] == 0
+    assert same > 0.9
+    assert abs(mg / mr - 1) < 0.01 or same > 0.98
+    both = g["nscatt"] == r["nscatt"]
+    ln = wl.lines[0]
+    dnu = synth.doppler_width(ln, float(wl.medium.T[0]))
+    assert np.median(np.abs(g["nu"][both] - r["nu"][both]) / dnu) < 1e-4
