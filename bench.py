@@ -76,14 +76,28 @@ def parse():
                     help="all (default): the headline line with the batch and galaxy sections; "
                          "batch / galaxy: that section alone, printed as its own JSON line; configs: GPU and "
                          "oracle rates of the other configurations (not part of the default run)")
+    ap.add_argument("--voigt", default="tasitsiomi", choices=["tasitsiomi", "faddeeva"],
+                    help="H(a,x) evaluation: Tasitsiomi's form (default, the paper's hot-path choice) or the "
+                         "accurate Faddeeva function")
     ap.add_argument("--max-scatt", type=int, default=0,
                     help="cap scatterings per packet (profiling runs only; 0 = the full workload)")
     return ap.parse_args()
 
 
+# H(a,x) method of every run (0: Tasitsiomi's form, the default and the
+# headline; 1: the Faddeeva function), set from --voigt
+VOIGT = 0
+
+
+def _with_voigt(wl):
+    wl.physics.voigt = VOIGT
+    return wl
+
+
 def workload(n):
     import synth
     wl = synth.sphere(tau0=1e6, T=1e4, tau_dust=1.0, n_packets=n, recoil=0, isotropic=0)
+    wl.physics.voigt = VOIGT
     return wl
 
 
@@ -192,7 +206,8 @@ def run_reference(args):
             "packets_per_s": pk, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(r[3] for r in rates) / len(rates), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "oracle on %d packets per step" % int(np.mean([r[2] for r in rates]))},
+            "config": {"workload": WORKLOAD, "voigt": args.voigt,
+                       "sample": "oracle on %d packets per step" % int(np.mean([r[2] for r in rates]))},
             "cpu_baseline": {"value": sc, "unit": "scatterings/s", "cores": threads, "kind": "oracle",
                              "sample": "%d packets of the workload per step, %d threads" % (int(np.mean([r[2] for r in rates])), threads)},
             "e2e": {"value": sc, "unit": "scatterings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -211,6 +226,7 @@ def run_batch(args):
     ctx.set_lines(w0.lines, w0.dust)
     ph = w0.physics
     ctx.set_physics(ph.recoil, ph.isotropic, 0, ph.x_gauss, args.batch_cap, 0, ph.tau_stop, ph.seed)
+    ctx.set_voigt(VOIGT)
     ctx.load_batch(models, nbin=200)
     tune = ctx.autotune_batch(max_scatt=max(1, args.batch_cap // 20))
     ctx.propagate_batch(rg.BATCH_PERSISTENT)           # warm-up (graph capture)
@@ -268,7 +284,8 @@ def run_configs(args):
         ("Fe II UV1 sphere tau0=1e4 (fluorescence)", lambda n: synth.feII_sphere(n_packets=n), 1 << 20),
     ]
     out = []
-    for name, fn, n in cfgs:
+    for name, fn0, n in cfgs:
+        fn = (lambda f: (lambda k: _with_voigt(f(k))))(fn0)
         wl = fn(n)
         ctx = rg.Context(0)
         ctx.setup(wl)
@@ -311,6 +328,7 @@ def run_galaxy(args, peaks):
     import synth
     t0 = time.perf_counter()
     wl = synth.galaxy(n_packets=max(args.galaxy_rays, args.galaxy_packets))
+    wl.physics.voigt = VOIGT
     gen_s = time.perf_counter() - t0
     dev = torch.device("cuda:0")
     ctx = rg.Context(0)
@@ -400,7 +418,9 @@ def run_galaxy(args, peaks):
 
 # ------------------------------------------------------------------ our arm
 def main():
+    global VOIGT
     args = parse()
+    VOIGT = 1 if args.voigt == "faddeeva" else 0
     if args.impl == "reference":
         return run_reference(args)
     if args.section in ("batch", "galaxy", "configs"):
@@ -531,7 +551,7 @@ def main():
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "packets_per_step": P, "per_rank": True,
+            "config": {"workload": WORKLOAD, "voigt": args.voigt, "packets_per_step": P, "per_rank": True,
                        "l2": "256 MB buffer written between timed steps (L2 flush)",
                        "mean_scatterings_per_packet": scatt / max(1, pk_done)},
             "roofline": roof,
