@@ -876,20 +876,6 @@ __device__ __forceinline__ double to_gas(double nu_ext, double b) {
 }
 __device__ __forceinline__ double to_ext(double nu_gas, double b) { return __fma_rn(nu_gas, b, nu_gas); }
 
-// total opacity at gas-frame frequency nu (cm^-1), per line in kl[]
-template <int NL>
-__device__ __forceinline__ float opacity(const Params& P, const CellCache<NL>& cc, double nu,
-                                         float kl[NL]) {
-    float tot = cc.kap_d;
-#pragma unroll
-    for (int i = 0; i < NL; ++i) {
-        double x = (nu - P.line[i].nu0) * cc.invdnu[i];
-        kl[i] = cc.kap0[i] * voigt_sel(cc.a[i], x);
-        tot += kl[i];
-    }
-    return tot;
-}
-
 // ---------------------------------------------------------------------------
 // Opacity along a ray at fixed external frequency and direction (the peeling
 // integral and its adjoint, Sect. 3.1 opacities in each leaf's frame), with no

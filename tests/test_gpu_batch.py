@@ -11,22 +11,27 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-def _batch_ctx(models, cap):
+def _batch_ctx(models, cap, voigt=0):
     import paper_2001_11252_gb300 as rg
     ctx = rg.Context(0)
     w0 = models[0]
     ctx.set_lines(w0.lines, w0.dust)
     ph = w0.physics
     ctx.set_physics(ph.recoil, ph.isotropic, ph.keep_direction, ph.x_gauss, cap, 0, ph.tau_stop, ph.seed)
+    ctx.set_voigt(voigt)
     ctx.load_batch(models, nbin=200)
     return ctx
 
 
-def test_batch_equals_per_model_and_single_runs():
+@pytest.mark.parametrize("voigt", [0, 1])
+def test_batch_equals_per_model_and_single_runs(voigt):
+    """voigt 1: the same with the Faddeeva H (the second kernel build)."""
     import paper_2001_11252_gb300 as rg
     models = synth.batch_models(40, packet_scale=0.004)
+    for w in models:
+        w.physics.voigt = voigt
     cap = 20000
-    ctx = _batch_ctx(models, cap)
+    ctx = _batch_ctx(models, cap, voigt)
     st_b = ctx.propagate_batch(rg.BATCH_PERSISTENT)
     sp_b = ctx.get_batch_spectra()
     st_p = ctx.propagate_batch(rg.BATCH_PER_MODEL)
