@@ -87,6 +87,45 @@ def test_ray_tau_closed_form_sphere():
         assert n == 1 + np.abs(i1 - i0).sum()
 
 
+def test_walk_on_graded_tree_matches_brute_force():
+    """The neighbour-search walk (Sect. 4.3: same father, then the neighbour
+    across the face, then the root) on a graded octree: the midpoint of every
+    segment lies in the leaf the walk reports (by a scan of all leaves),
+    consecutive segments join end to end, and the summed path equals the
+    analytic distance to the sphere border."""
+    wl = synth.sphere(n_packets=1, base=2, max_level=6)
+    o = oracle.Oracle(wl)
+    tree = wl.medium.tree
+    nu0 = synth.nu_of(wl.lines[0].lambda_A)
+    c = np.array(wl.domain.centre)
+    R = wl.domain.size
+    rng = np.random.default_rng(17)
+    nseg = 0
+    for i in range(90):
+        r = R * rng.random() ** (1 / 3) * 0.99
+        v = rng.normal(size=3)
+        p = c + v / np.linalg.norm(v) * r
+        if i < 20:
+            p = np.round(p * 64) / 64          # start on faces, edges and corners
+        k = rng.normal(size=3)
+        if i % 10 == 0:
+            k[i % 3] = 0.0                      # rays inside a face plane
+        k /= np.linalg.norm(k)
+        tau, cells, lens, n = o.ray_tau(p, k, nu0, cap=100000)
+        assert n == len(cells) > 0
+        b = float(np.dot(p - c, k))
+        t_border = -b + math.sqrt(b * b - (float(np.dot(p - c, p - c)) - R * R))
+        assert abs(lens.sum() - t_border) <= 1e-12 * max(t_border, 1.0)
+        s = np.concatenate([[0.0], np.cumsum(lens)])
+        for j in range(n):
+            if lens[j] < 1e-9:
+                continue                        # a zero-length step through an edge or corner
+            mid = p + 0.5 * (s[j] + s[j + 1]) * k
+            assert _brute_leaf(tree, mid, k) == cells[j], (i, j)
+            nseg += 1
+    assert nseg > 500
+
+
 def test_ray_tau_periodic_slab():
     """Slab (periodic x,y, Sect. 4): a grazing ray from the mid-plane wraps
     many times; its path to the border is (1/2)/|k_z| and tau = tau0/|k_z|."""
