@@ -212,7 +212,10 @@ int rascas_set_physics(rascas_ctx *ctx, const rascas_physics *phys);
  *     paper's fast form, ~1 % from H for Lya at 1e4 K and worse at larger a;
  *   RASCAS_VOIGT_FADDEEVA: H = Re w(x + ia) of the Faddeeva function, by the
  *     trapezoidal rule on w's integral with its pole residue in closed form,
- *     within ~5e-7 relative in FP32 for 0 <= a <= 1 at every x.
+ *     within ~5e-7 relative in FP32 for 0 <= a <= 1 at every x (4e-6 at
+ *     a = 2).  The rule's remainder grows like exp(4 pi a - pi^2 / h^2) with
+ *     its step h = 1/2, so the evaluation is not valid for a > 2; a line of
+ *     Table 1 reaches a = 2 only below ~0.01 K.
  * Applies to rascas_propagate, _ray_tau, _trace, _propagate_batch, the
  * peeling tallies, rascas_peel_adjoint and rascas_eval_voigt.  The context
  * keeps the method; RASCAS_E_ARG for any other value. */

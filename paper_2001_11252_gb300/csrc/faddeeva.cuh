@@ -60,7 +60,9 @@ RG_HD float sinpi_f(float x) {
 // E(u) = (e^u - 1)/u and B(v) = 1/(1 - e^{-v}) - 1/v, both regular at 0 (Taylor
 // and Bernoulli-number series there), so FP32 keeps ~5e-7 relative accuracy
 // in H and K for 0 <= a <= 1 for |x| <= 8 (nodes |n| <= 11; weights below
-// e^-30 are left out).  Beyond |x| = 8 the asymptotic series of w is cheaper
+// e^-30 are left out).  The remainder grows like e^{2 pi a/h - pi^2/h^2}: 4e-6
+// at a = 2, and the rule is not valid beyond (a line of Table 1 reaches a = 2
+// only below ~0.01 K).  Beyond |x| = 8 the asymptotic series of w is cheaper
 // and as accurate (fad_far).
 // ---------------------------------------------------------------------------
 // (h/pi) e^{-n^2 h^2} for h = 1/2, at compile time: e^{-1/4} by its Taylor

@@ -58,3 +58,13 @@ def test_faddeeva_fp32_against_wofz(tmp_path):
     # beyond |x| = 8 the series derivative itself is accurate to FP32
     assert np.max(np.abs(v[far, 2] / Ha[far] - 1)) < 1e-5
     assert np.max(np.abs(v[far, 3] / Hx[far] - 1)) < 1e-5
+
+
+def test_faddeeva_fp32_domain_edge(tmp_path):
+    """At a = 2, the edge of the stated domain, H is still within 1e-5."""
+    from scipy.special import wofz
+    x = np.concatenate([np.linspace(-12, 12, 2001), [20.0, 1e3]])
+    a = np.full(x.size, 2.0)
+    v = _run(tmp_path, a, x)
+    xs = x.astype(np.float32).astype(np.float64)
+    assert np.max(np.abs(v[:, 0] / wofz(xs + 2j).real - 1)) < 1e-5
