@@ -14,4 +14,5 @@ from ._native import (  # noqa: F401
     TALLY_SPECTRUM, TALLY_PEEL_SPECTRA, TALLY_PEEL_IMAGES, TALLY_PEEL_CUBES,
     PK_ACTIVE, PK_ESCAPED, PK_ABSORBED, PK_CAPPED, PK_ERROR,
     DOMAIN_SPHERE, DOMAIN_SLAB, DOMAIN_CUBE, DOMAIN_SHELL, BATCH_PERSISTENT, BATCH_PER_MODEL,
+    VOIGT_TASITSIOMI, VOIGT_FADDEEVA,
 )

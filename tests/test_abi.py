@@ -44,3 +44,12 @@ def test_binding_fails_loudly_without_gpu():
     import paper_2001_11252_gb300 as rg
     with pytest.raises(Exception):
         rg.Context(0)
+
+
+def test_binding_constants_match_header():
+    """The enum values the binding passes through the ABI are the header's."""
+    import paper_2001_11252_gb300 as rg
+    src = open(HEADER).read()
+    enums = dict((k, int(v)) for k, v in re.findall(r"\b(RASCAS_[A-Z_0-9]+)\s*=\s*(-?\d+)", src))
+    for name in ["DOMAIN_SPHERE", "DOMAIN_SLAB", "DOMAIN_CUBE", "DOMAIN_SHELL", "VOIGT_TASITSIOMI", "VOIGT_FADDEEVA"]:
+        assert getattr(rg, name) == enums["RASCAS_" + name], name
