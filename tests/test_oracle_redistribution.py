@@ -68,3 +68,32 @@ def test_single_scattering_redistribution(x_in, kind):
     # the test has teeth: leaving out the perpendicular velocity is rejected
     wrong = _reference(x_in, a, kind, 200000, np.random.default_rng(4), perp=False)
     assert ks_2samp(got, wrong).pvalue < 1e-6
+
+
+def test_recoil_denominator():
+    """Eq. nuout_nuin: with the same draws (same packet stream) a scattering
+    with recoil differs from one without only by the denominator
+    1 + (1 - mu) h nu_in / (m c^2), mu = k_out . k_in."""
+    res = {}
+    for rec in (0, 1):
+        wl = synth.slab(tau0=1e9, T=1e4, n_packets=1, isotropic=0, recoil=rec)
+        o = oracle.Oracle(wl)
+        h = wl.lines[0]
+        nu0, dnu = synth.nu_of(h.lambda_A), synth.doppler_width(h, 1e4)
+        k_in = np.array([0.6, 0.0, 0.8])
+        out = []
+        for pid in range(400):
+            nu_in = nu0 + (pid % 9 - 4) * 0.7 * dnu
+            s = o.new_state(np.array([0.5, 0.5, 0.5]), k_in, nu_in, pid + 77)
+            o.event(s)
+            out.append((s.nscatt, s.nu, np.dot(np.array(s.k), k_in), nu_in))
+        res[rec] = out
+    m = synth.lya().mass_g
+    checked = 0
+    for (n0, nu_a, mu_a, nu_in), (n1, nu_b, mu_b, _) in zip(res[0], res[1]):
+        assert n0 == n1 == 1
+        assert mu_a == mu_b                      # same draws, same direction
+        expect = nu_a / (1.0 + (1.0 - mu_a) * synth.H_CGS * nu_in / (m * synth.C_CGS ** 2))
+        assert abs(nu_b / expect - 1) < 1e-14
+        checked += 1
+    assert checked == 400
