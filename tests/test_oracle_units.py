@@ -174,3 +174,43 @@ def test_onb_orthonormal():
         b1, b2 = oracle.onb(n)
         M = np.stack([b1, b2, n])
         assert np.allclose(M @ M.T, np.eye(3), atol=1e-14)
+
+
+def test_opacity_frame_change():
+    """Sect. 3 frame change: a leaf moving with velocity v presents to a photon
+    of external frequency nu_ext along k the opacity of the gas at rest at
+    nu_gas = nu_ext / (1 + k.v/c); a velocity perpendicular to k changes
+    nothing; the Doppler offset moves by k.v / v_th widths."""
+    wl = synth.slab(tau0=1e3, T=1e4, n_packets=1)
+    o = oracle.Oracle(wl)
+    ln = wl.lines[0]
+    nu0, dnu = synth.nu_of(ln.lambda_A), synth.doppler_width(ln, 1e4)
+    nleaf = wl.medium.tree.nleaf
+    leaf = 7
+    v = np.float32(1.0e7)                     # 100 km/s
+    rng = np.random.default_rng(4)
+    for _ in range(40):
+        k = rng.normal(size=3)
+        k /= np.linalg.norm(k)
+        x = rng.uniform(-8, 8)
+        nu_gas = nu0 + x * dnu
+        o.set_field("vx", np.zeros(nleaf))
+        kap_rest = o.opacity(leaf, nu_gas, k)
+        o.set_field("vx", np.full(nleaf, v))
+        beta = k[0] * float(v) / synth.C_CGS
+        kap_moving = o.opacity(leaf, nu_gas * (1.0 + beta), k)
+        assert abs(kap_moving / kap_rest - 1) < 1e-9
+        # perpendicular motion: no shift
+        kp = np.array([0.0, k[1], k[2]])
+        kp /= np.linalg.norm(kp)
+        o.set_field("vx", np.zeros(nleaf))
+        kap_p0 = o.opacity(leaf, nu_gas, kp)
+        o.set_field("vx", np.full(nleaf, v))
+        assert o.opacity(leaf, nu_gas, kp) == kap_p0
+    # the line centre seen from a receding leaf sits k.v/c nu0 to the red
+    o.set_field("vx", np.full(nleaf, v))
+    k = np.array([-1.0, 0.0, 0.0])
+    shift = nu0 * (1.0 - float(v) / synth.C_CGS)
+    nus = shift + np.linspace(-0.05, 0.05, 201) * dnu
+    kaps = [o.opacity(leaf, f, k) for f in nus]
+    assert abs((nus[int(np.argmax(kaps))] - shift) / dnu) <= 0.0005 + 1e-12
