@@ -90,9 +90,8 @@ def test_ray_tau_closed_form_sphere():
 def test_walk_on_graded_tree_matches_brute_force():
     """The neighbour-search walk (Sect. 4.3: same father, then the neighbour
     across the face, then the root) on a graded octree: the midpoint of every
-    segment lies in the leaf the walk reports (by a scan of all leaves),
-    consecutive segments join end to end, and the summed path equals the
-    analytic distance to the sphere border."""
+    segment lies in the leaf the walk reports (by a scan of all leaves), and
+    the summed path equals the analytic distance to the sphere border."""
     wl = synth.sphere(n_packets=1, base=2, max_level=6)
     o = oracle.Oracle(wl)
     tree = wl.medium.tree
@@ -188,6 +187,24 @@ def test_pure_absorber(tau_d):
     esc = int((out["status"] == oracle.ESCAPED).sum())
     assert esc + int((out["status"] == oracle.ABSORBED).sum()) == n
     assert binomtest(esc, n, math.exp(-tau_d)).pvalue > 1e-3
+
+
+@pytest.mark.parametrize("tau_d", [5.0, 20.0])
+def test_interaction_choice_dust_vs_line(tau_d):
+    """Sect. 3.2: the first interaction is with dust with probability
+    tau_d / (tau_d + tau_HI) at the packet's frequency.  Slab with
+    half-thickness tau0 = 10 in H I at line centre (Tasitsiomi's H(a,0) = 1)
+    and tau_d in dust of albedo 0, packets emitted at x = 0, one interaction
+    each: dust interactions are the absorptions."""
+    from scipy.stats import binomtest
+    n = 20000
+    wl = synth.slab(tau0=10.0, T=1e4, n_packets=n, tau_dust=tau_d, albedo=0.0)
+    wl.physics.max_scatt = 1
+    out, _ = oracle.Oracle(wl).run(threads=THREADS)
+    absorbed = int((out["status"] == oracle.ABSORBED).sum())
+    capped = int((out["status"] == oracle.CAPPED).sum())
+    assert absorbed + capped >= n - 2          # escaping before any interaction: e^-(10 + tau_d)
+    assert binomtest(absorbed, absorbed + capped, tau_d / (tau_d + 10.0)).pvalue > 1e-3
 
 
 @pytest.mark.parametrize("tau0", [10.0, 1e3])
