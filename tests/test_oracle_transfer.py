@@ -151,6 +151,17 @@ def test_conservation_no_dust():
     assert np.all(out["nscatt"] > 0)
 
 
+def test_escape_spectrum_is_the_histogram_of_escapes():
+    """Sect. 4.4 tallies: the escape spectrum is the histogram of the escaped
+    packets' external frequencies on the detector axis, bin for bin."""
+    wl = synth.slab(tau0=1e3, T=1e4, n_packets=800)
+    out, tal = oracle.Oracle(wl).run(threads=THREADS)
+    det = wl.detector
+    esc = out["status"] == oracle.ESCAPED
+    h, _ = np.histogram(out["nu"][esc], bins=np.linspace(det.nu_lo, det.nu_hi, det.nbin + 1))
+    assert np.array_equal(tal["spec"], h)
+
+
 def test_slab_symmetry():
     """Static slab without recoil: escape through +z and -z equally likely,
     spectrum symmetric in x (Sect. 3.4.2)."""
