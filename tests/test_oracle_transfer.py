@@ -312,6 +312,47 @@ def test_peeling_flux_equals_escape():
         assert abs((ps * xs).sum() / ps.sum() - (esc * xs).sum() / esc.sum()) < 2.0
 
 
+def test_peeled_images_of_a_transparent_sphere():
+    """Peeling at emission (Sect. 5.1) through an empty medium: each packet
+    adds 1/(4 pi) (isotropic emission, e^-0 = 1) to the pixel where its
+    birth point projects on the image plane of each direction (axes e_u, e_v
+    orthonormal to the direction) and to the channel of its frequency."""
+    n = 600
+    wl = synth.sphere(tau0=0.0, T=1e4, n_packets=n, base=3, max_level=4)
+    wl.detector.dirs = synth.PEEL_DIRS_3.copy()
+    wl.detector.npix, wl.detector.fov = 16, 1.0
+    rng = np.random.default_rng(23)
+    c = np.array(wl.domain.centre)
+    r = wl.domain.size * rng.random(n) ** (1 / 3) * 0.999
+    v = rng.normal(size=(n, 3))
+    pos = c + v / np.linalg.norm(v, axis=1)[:, None] * r[:, None]
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    nu = synth.nu_of(wl.lines[0].lambda_A) + rng.uniform(-20, 20, n) * synth.doppler_width(wl.lines[0], 1e4)
+    pk = synth.Packets(pos, d, nu, np.arange(n, dtype=np.uint64) + 5)
+    wl.physics.tau_stop = math.inf
+    out, tal = oracle.Oracle(wl).run(packets=pk, threads=THREADS)
+    assert np.all(out["status"] == oracle.ESCAPED) and np.all(out["nscatt"] == 0)
+    det = wl.detector
+    npix = det.npix
+    img = np.zeros((3, npix, npix))
+    spec = np.zeros((3, det.nbin))
+    for di, ko in enumerate(det.dirs):
+        ko = ko / np.linalg.norm(ko)
+        eu, ev = oracle.onb(ko)
+        assert abs(np.dot(eu, ko)) < 1e-15 and abs(np.dot(ev, ko)) < 1e-15
+        rel = pos - np.array(det.centre)
+        iu = np.floor((rel @ eu / det.fov + 0.5) * npix).astype(int)
+        iv = np.floor((rel @ ev / det.fov + 0.5) * npix).astype(int)
+        ok = (iu >= 0) & (iu < npix) & (iv >= 0) & (iv < npix)
+        np.add.at(img[di], (iv[ok], iu[ok]), 1.0 / (4 * math.pi))
+        ch = np.floor((nu - det.nu_lo) / (det.nu_hi - det.nu_lo) * det.nbin).astype(int)
+        okc = (ch >= 0) & (ch < det.nbin)
+        np.add.at(spec[di], ch[okc], 1.0 / (4 * math.pi))
+    assert np.allclose(tal["pimg"].reshape(3, npix, npix), img, rtol=1e-12, atol=1e-15)
+    assert np.allclose(tal["pspec"].reshape(3, -1), spec, rtol=1e-12, atol=1e-15)
+
+
 def test_expanding_sphere_redshift():
     """Outflow (Sect. 3.4.2, expanding sphere): photons escape mostly on the
     red side of the line; in an infalling sphere (v -> -v) on the blue side,
