@@ -91,8 +91,7 @@ RG_HD void fad_node(float a, float a2, float xh, float xl, int m, float& H, floa
 }
 
 template <int... I>
-RG_HD void fad_nodes(float a, float xh, float xl, int m, float& H, float& K,
-                                          std::integer_sequence<int, I...>) {
+RG_HD void fad_nodes(float a, float xh, float xl, int m, float& H, float& K, std::integer_sequence<int, I...>) {
     const float a2 = a * a;
     (fad_node<I - 11>(a, a2, xh, xl, m, H, K), ...);
 }
