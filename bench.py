@@ -89,6 +89,22 @@ def parse():
 VOIGT = 0
 
 
+def host_cpu():
+    """The host CPU the oracle ran on: model name where the kernel reports
+    one, machine type, logical CPUs."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu": model or platform.machine(), "machine": platform.machine(), "nproc": os.cpu_count()}
+
+
 def _with_voigt(wl):
     wl.physics.voigt = VOIGT
     return wl
@@ -209,7 +225,8 @@ def run_reference(args):
             "config": {"workload": WORKLOAD, "voigt": args.voigt,
                        "sample": "oracle on %d packets per step" % int(np.mean([r[2] for r in rates]))},
             "cpu_baseline": {"value": sc, "unit": "scatterings/s", "cores": threads, "kind": "oracle",
-                             "sample": "%d packets of the workload per step, %d threads" % (int(np.mean([r[2] for r in rates])), threads)},
+                             "sample": "%d packets of the workload per step, %d threads" % (int(np.mean([r[2] for r in rates])), threads),
+                             "host": host_cpu()},
             "e2e": {"value": sc, "unit": "scatterings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -572,7 +589,7 @@ def main():
         sc, pr, npk, secs = cpu_oracle_rate(workload, args.cpu_seconds, threads)
         line["cpu_baseline"] = {"value": sc, "unit": "scatterings/s", "cores": threads, "kind": "oracle",
                                 "sample": "%d packets of the workload (%.1f s on %d threads), %.3g packets/s"
-                                          % (npk, secs, threads, pr)}
+                                          % (npk, secs, threads, pr), "host": host_cpu()}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

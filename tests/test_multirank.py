@@ -79,3 +79,10 @@ def test_two_gloo_ranks():
     assert np.array_equal(res[0][5], np.asarray(tal["spec"], np.float64))
     assert np.array_equal(res[0][6], [float((out["status"] == s).sum()) for s in (1, 2, 3)])
     assert np.array_equal(res[0][5], res[1][5])
+
+
+def test_host_cpu_record():
+    """The CPU baseline names the host it ran on."""
+    import bench
+    h = bench.host_cpu()
+    assert set(h) == {"cpu", "machine", "nproc"} and h["cpu"] and h["nproc"] >= 1
