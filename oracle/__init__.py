@@ -23,7 +23,15 @@ Parity status of each function (pins live in tests/test_oracle_*.py):
   walk / ray_tau ....... pinned (brute-force leaf lookup, closed-form tau)
   ora_run / ora_event .. pinned (MFP, conservation, symmetry, pure absorber,
                          error budget, Neufeld / Dijkstra spectra, Harrington)
-  peeling .............. pinned (4 pi * peeled flux = escape fraction, symmetry)
+  peeling .............. pinned (4 pi * peeled flux = escape fraction, symmetry,
+                         empty medium); no cut-off (rays walked until exp(-tau)
+                         underflows in FP64, which changes no tally)
+  line_props ........... pinned (a at T = 10, 1e2, 1e4 K as printed in Sect. 3.4.2;
+                         sigma integrated over frequency = pi e^2 f / (m_e c))
+  core-skipping u_perp . pinned (radius law of the truncated 2-D Gaussian,
+                         x_crit = 0 identical to the plain draw, slab spectra)
+  ray_columns .......... pinned (closed-form chords of a uniform sphere, same
+                         leaves as ray_tau)
 """
 from __future__ import annotations
 
@@ -77,11 +85,12 @@ class Cfg(C.Structure):
         ("dust_sigma", C.c_double), ("dust_albedo", C.c_double), ("dust_g", C.c_double),
         ("recoil", C.c_int64), ("isotropic", C.c_int64), ("keep_dir", C.c_int64),
         ("max_scatt", C.c_int64), ("max_steps", C.c_int64),
-        ("x_gauss", C.c_double), ("tau_stop", C.c_double), ("seed", C.c_uint64),
+        ("x_gauss", C.c_double), ("seed", C.c_uint64),
         ("nu_lo", C.c_double), ("nu_hi", C.c_double),
         ("nbin", C.c_int64), ("ndir", C.c_int64), ("npix", C.c_int64), ("cube", C.c_int64),
         ("dirs", (C.c_double * 3) * MAXDIR), ("fov", C.c_double), ("img_c", C.c_double * 3),
         ("voigt", C.c_int64),
+        ("core_skip", C.c_double), ("core_skip_f", C.c_double),
     ]
 
 
@@ -149,6 +158,12 @@ def lib():
                                              C.c_void_p]
             L.ora_voigt_derivs.argtypes = [C.c_double, C.c_double, dp, dp, dp]
             L.ora_emission.argtypes = [C.POINTER(Cfg), C.POINTER(State), C.POINTER(Tally)]
+            L.ora_line_props.argtypes = [C.POINTER(Cfg), i64, i64, C.c_double, dp]
+            L.ora_sample_uperp_n.argtypes = [C.POINTER(Cfg), u64, C.c_double, C.c_double, i64, dp]
+            L.ora_core_skip_xcrit.restype = C.c_double
+            L.ora_core_skip_xcrit.argtypes = [C.POINTER(Cfg), i64, i64, i64]
+            L.ora_ray_columns.restype = i64
+            L.ora_ray_columns.argtypes = [C.POINTER(Cfg), dp, dp, dp]
             for f in ("ora_sizeof_cfg", "ora_sizeof_state", "ora_sizeof_tally", "ora_sizeof_event"):
                 getattr(L, f).restype = i64
             assert L.ora_sizeof_cfg() == C.sizeof(Cfg)
@@ -205,8 +220,10 @@ class Oracle:
         ph = wl.physics
         cf.recoil, cf.isotropic, cf.keep_dir = ph.recoil, ph.isotropic, ph.keep_direction
         cf.max_scatt, cf.max_steps = ph.max_scatt, ph.max_steps
-        cf.x_gauss, cf.tau_stop, cf.seed = ph.x_gauss, ph.tau_stop, ph.seed
+        cf.x_gauss, cf.seed = ph.x_gauss, ph.seed
         cf.voigt = getattr(ph, "voigt", 0)
+        cf.core_skip = getattr(ph, "core_skip", 0.0)
+        cf.core_skip_f = getattr(ph, "core_skip_f", 0.0)
         det = wl.detector
         cf.nu_lo, cf.nu_hi, cf.nbin = det.nu_lo, det.nu_hi, det.nbin
         dirs = np.asarray(det.dirs, dtype=np.float64).reshape(-1, 3)
@@ -344,6 +361,32 @@ class Oracle:
                                 _dp(lens) if cap else None, cap, C.byref(nc))
         n = min(nc.value, cap)
         return tau, cells[:n], lens[:n], nc.value
+
+    def line_props(self, il, leaf, nu_gas):
+        """(v_th, Delta nu_D, a, x, sigma) of line il in a leaf at gas-frame
+        frequency nu_gas (Sect. 3.1.1)."""
+        out = np.zeros(5)
+        lib().ora_line_props(C.byref(self.cfg), int(il), int(leaf), float(nu_gas), _dp(out))
+        return tuple(float(v) for v in out)
+
+    def uperp_samples(self, x_in, x_crit, n, pid=0):
+        """n perpendicular-velocity pairs [n, 2] drawn at x_in with the
+        core-skipping threshold x_crit (0 = the plain draw)."""
+        out = np.zeros(2 * n)
+        lib().ora_sample_uperp_n(C.byref(self.cfg), int(pid), float(x_in), float(x_crit), n, _dp(out))
+        return out.reshape(n, 2)
+
+    def core_skip_xcrit(self, il, leaf, level):
+        return lib().ora_core_skip_xcrit(C.byref(self.cfg), int(il), int(leaf), int(level))
+
+    def ray_columns(self, p, k):
+        """(N_HI, N_dust, N_metal) from p along k to the domain border and the
+        number of leaves crossed."""
+        p = np.ascontiguousarray(p, dtype=np.float64)
+        k = np.ascontiguousarray(k, dtype=np.float64)
+        cols = np.zeros(3)
+        n = lib().ora_ray_columns(C.byref(self.cfg), _dp(p), _dp(k), _dp(cols))
+        return cols, n
 
     def upar_samples(self, x, a, n, pid=0):
         out = np.zeros(n)

@@ -80,7 +80,7 @@ typedef struct {
     double dust_sigma, dust_albedo, dust_g;
     /* physics switches */
     int64_t recoil, isotropic, keep_dir, max_scatt, max_steps;
-    double x_gauss, tau_stop;
+    double x_gauss;
     uint64_t seed;
     /* detector: frequency axis (external frame), peeling directions, image */
     double nu_lo, nu_hi;
@@ -89,6 +89,11 @@ typedef struct {
     double fov, img_c[3];
     /* H(a,x) evaluation: 0 Tasitsiomi (2006), 1 the Faddeeva function */
     int64_t voigt;
+    /* core-skipping (Sect. 3.2.1): critical frequency x_crit of the
+     * truncated perpendicular-velocity draw; core_skip_f > 0 sets
+     * x_crit = core_skip_f (a tau_cell)^(1/3) per scattering, else
+     * x_crit = core_skip (0 = off) */
+    double core_skip, core_skip_f;
 } ora_cfg;
 
 typedef struct {
@@ -260,6 +265,18 @@ static void line_props(const ora_cfg *cf, int il, int64_t leaf, double nu_gas, o
     lp->a = cf->line_A[il] / (4.0 * OPI * lp->dnu);
     lp->x = (nu_gas - cf->line_nu[il]) / lp->dnu;
     lp->sigma = sqrt(OPI) * OE * OE * cf->line_f[il] / (OME * OC * lp->dnu) * voigt_of(cf, lp->a, lp->x);
+}
+
+/* exported for the pins: v_th, Delta nu_D, a, x, sigma of line il in a leaf */
+ORA_API void ora_line_props(const ora_cfg *cf, int64_t il, int64_t leaf, double nu_gas, double out[5])
+{
+    ora_lineprop lp;
+    line_props(cf, (int)il, leaf, nu_gas, &lp);
+    out[0] = lp.vth;
+    out[1] = lp.dnu;
+    out[2] = lp.a;
+    out[3] = lp.x;
+    out[4] = lp.sigma;
 }
 
 static double beta_of(const ora_cfg *cf, int64_t leaf, const double k[3])
@@ -613,6 +630,44 @@ ORA_API double ora_ray_tau(const ora_cfg *cf, const double p[3], const double k[
     return ray_tau(cf, p, k, nu_ext, leaf, level, ijk, tau_stop, cells, lens, cap, ncell);
 }
 
+/* Column densities from p along k to the domain border (the ray integral of
+ * Sect. 3.1 without the line profile: the quantity behind escape fractions of
+ * ionising photons and sight-line columns, Sects. 5 and 6):
+ *   cols[0] = sum n_HI l L, cols[1] = sum n_dust l L, cols[2] = sum n_metal l L
+ * over the leaves of the walk of Sect. 4.3 (cm^-2; n_dust in its own units
+ * times cm).  Returns the number of leaves crossed; 0 outside the box. */
+ORA_API int64_t ora_ray_columns(const ora_cfg *cf, const double p_in[3], const double k[3], double cols[3])
+{
+    double p[3] = {p_in[0], p_in[1], p_in[2]};
+    wrap_periodic(cf, p, k);
+    int64_t level, ijk[3];
+    int64_t leaf = descend(cf, p, k, &level, ijk);
+    cols[0] = cols[1] = cols[2] = 0.0;
+    if (leaf < 0) return 0;
+    double inv[3];
+    inverse_dir(k, inv);
+    int64_t n = 0;
+    for (long guard = 0; guard < 100000000L; ++guard) {
+        ora_state tmp;
+        memcpy(tmp.p, p, sizeof p);
+        memcpy(tmp.k, k, sizeof tmp.k);
+        tmp.level = level;
+        memcpy(tmp.ijk, ijk, sizeof ijk);
+        int axis;
+        double tf = face_distance(&tmp, inv, &axis);
+        double tb = border_distance(cf, p, k, inv);
+        double l = tb <= tf ? tb : tf;
+        double lc = l * cf->box_cm;
+        cols[0] += (double)cf->n_HI[leaf] * lc;
+        cols[1] += (double)cf->n_dust[leaf] * lc;
+        cols[2] += (cf->n_metal ? (double)cf->n_metal[leaf] : 0.0) * lc;
+        ++n;
+        if (tb <= tf) break;
+        if (cross_face(cf, p, k, axis, tf, &leaf, &level, ijk)) break;
+    }
+    return n;
+}
+
 /* detector bins of a peeling event: channel (or -1) and pixel (or -1) */
 static void peel_bins(const ora_cfg *cf, const double p[3], int d, double nu_o_ext, int64_t *ch, int64_t *px)
 {
@@ -633,12 +688,19 @@ static void peel_bins(const ora_cfg *cf, const double p[3], int d, double nu_o_e
     }
 }
 
+/* The oracle applies no peeling cut-off of its own (Sect. 5.1 peeling sums
+ * w exp(-tau) over every event): a ray is walked until exp(-tau) underflows
+ * to zero in double precision.  Beyond tau = 746, exp(-tau) is 0 in IEEE
+ * binary64 (the smallest subnormal is exp(-744.4)), so stopping there leaves
+ * every tally and every gradient bit-identical to walking on to the border. */
+#define ORA_TAU_UNDERFLOW 746.0
+
 /* add the contribution w exp(-tau) of one event to spectra, images, cubes */
 static void peel_deposit(const ora_cfg *cf, ora_tally *ty, const ora_peel_event *e)
 {
     int d = (int)e->dir;
-    double tau = ray_tau(cf, e->p, cf->dirs[d], e->nu, e->leaf, e->level, e->ijk, cf->tau_stop, 0, 0, 0, 0);
-    if (tau > cf->tau_stop) return;
+    double tau = ray_tau(cf, e->p, cf->dirs[d], e->nu, e->leaf, e->level, e->ijk, ORA_TAU_UNDERFLOW, 0, 0, 0, 0);
+    if (tau > ORA_TAU_UNDERFLOW) return;
     double f = e->w * exp(-tau);
     int64_t ch, px;
     peel_bins(cf, e->p, d, e->nu, &ch, &px);
@@ -769,8 +831,8 @@ ORA_API void ora_adjoint_events(const ora_cfg *cf, const ora_peel_event *ev, int
     for (int64_t i = 0; i < n; ++i) {
         const ora_peel_event *e = ev + i;
         int d = (int)e->dir;
-        double tau = ray_tau(cf, e->p, cf->dirs[d], e->nu, e->leaf, e->level, e->ijk, cf->tau_stop, 0, 0, 0, 0);
-        if (tau > cf->tau_stop) continue;
+        double tau = ray_tau(cf, e->p, cf->dirs[d], e->nu, e->leaf, e->level, e->ijk, ORA_TAU_UNDERFLOW, 0, 0, 0, 0);
+        if (tau > ORA_TAU_UNDERFLOW) continue;
         int64_t ch, px;
         peel_bins(cf, e->p, d, e->nu, &ch, &px);
         double G = 0.0;
@@ -828,6 +890,59 @@ static void scatter_dust(const ora_cfg *cf, ora_state *s, ora_tally *ty, double 
     ty->nscatt_dust++;
 }
 
+/* Perpendicular velocity components (u_perp1, u_perp2) of the scatterer
+ * (Sect. 3.2.1: each from the unbiased Gaussian exp(-u^2)/sqrt(pi)), drawn
+ * as a pair in polar form from two words.  Core-skipping (Sect. 3.2.1, after
+ * Ahn et al. 2002; the truncated draw of Dijkstra et al. 2006): when
+ * |x_in| < x_crit the pair comes from the same 2-D Gaussian restricted to
+ * |u_perp| >= x_crit, whose radius has P(|u_perp| > r) = exp(x_crit^2 - r^2),
+ * so r = sqrt(x_crit^2 - ln r1).  x_crit = 0 is the plain draw. */
+static void sample_uperp(const ora_cfg *cf, ora_state *s, double x_in, double x_crit, double *u1, double *u2)
+{
+    double r1 = u23(cf, s), r2 = u23(cf, s);
+    double xc2 = fabs(x_in) < x_crit ? x_crit * x_crit : 0.0;
+    double rho = sqrt(xc2 - log(r1));
+    *u1 = rho * cos(2.0 * OPI * r2);
+    *u2 = rho * sin(2.0 * OPI * r2);
+}
+
+/* exported for the pins: n pairs from one packet stream, starting at draw 0 */
+ORA_API void ora_sample_uperp_n(const ora_cfg *cf, uint64_t pid, double x_in, double x_crit, int64_t n, double *out)
+{
+    ora_state s;
+    memset(&s, 0, sizeof s);
+    s.pid = pid;
+    for (int64_t i = 0; i < n; ++i) sample_uperp(cf, &s, x_in, x_crit, out + 2 * i, out + 2 * i + 1);
+}
+
+/* Critical frequency of core-skipping for a scattering on line il in the
+ * packet's leaf.  The paper uses the scheme of Smith et al. (2015) without
+ * printing it; the reading taken here scales x_crit with (a tau_cell)^(1/3),
+ * the frequency scale at which a thick medium lets photons out (the slab
+ * spectrum of Sect. 3.4.2 peaks near 1.07 (a tau0)^(1/3)), with tau_cell the
+ * line-centre optical depth across the leaf (H -> 1) and a user factor. */
+static double core_skip_xcrit(const ora_cfg *cf, int il, const ora_state *s, const ora_lineprop *lp)
+{
+    if (cf->core_skip_f > 0.0) {
+        double sigma0 = sqrt(OPI) * OE * OE * cf->line_f[il] / (OME * OC * lp->dnu);
+        double tau_cell = line_density(cf, il, s->leaf) * sigma0 * ldexp(1.0, -(int)s->level) * cf->box_cm;
+        return cf->core_skip_f * cbrt(lp->a * tau_cell);
+    }
+    return cf->core_skip;
+}
+
+/* exported for the pins: x_crit of line il in leaf `leaf` at level `level` */
+ORA_API double ora_core_skip_xcrit(const ora_cfg *cf, int64_t il, int64_t leaf, int64_t level)
+{
+    ora_state s;
+    memset(&s, 0, sizeof s);
+    s.leaf = leaf;
+    s.level = level;
+    ora_lineprop lp;
+    line_props(cf, (int)il, leaf, cf->line_nu[il], &lp);
+    return core_skip_xcrit(cf, (int)il, &s, &lp);
+}
+
 static int scatter_line(const ora_cfg *cf, ora_state *s, ora_tally *ty, int il, double nu_gas)
 {
     int64_t leaf = s->leaf;
@@ -852,9 +967,8 @@ static int scatter_line(const ora_cfg *cf, ora_state *s, ora_tally *ty, int il, 
     int err = 0;
     double upar = sample_upar(cf, s, lp.x, lp.a, &err);
     if (err) return 1;
-    double r1 = u23(cf, s), r2 = u23(cf, s);
-    double rho = sqrt(-log(r1));
-    double up1 = rho * cos(2.0 * OPI * r2), up2 = rho * sin(2.0 * OPI * r2);
+    double up1, up2;
+    sample_uperp(cf, s, lp.x, core_skip_xcrit(cf, il, s, &lp), &up1, &up2);
     double kin[3] = {s->k[0], s->k[1], s->k[2]};
     double e1[3], e2[3];
     onb(kin, e1, e2);

@@ -337,6 +337,8 @@ class Physics:
     tau_stop: float = 50.0     # peeling rays stop once tau exceeds this (contribution < e^-tau_stop)
     seed: int = 0
     voigt: int = 0             # H(a,x): 0 Tasitsiomi (2006), 1 the Faddeeva function (accurate option)
+    core_skip: float = 0.0     # core-skipping critical frequency x_crit (0 = off)
+    core_skip_f: float = 0.0   # > 0: x_crit = core_skip_f * (a tau_cell)^(1/3) per scattering instead
 
 
 @dataclass
