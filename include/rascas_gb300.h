@@ -130,13 +130,28 @@ typedef struct {
  * default 8), per-packet caps on scatterings and walk steps (0 = none),
  * tau_stop: peeling rays stop once tau > tau_stop (their contribution is
  * below exp(-tau_stop)), run seed of the Philox4x32-10 streams, fail_on_cap:
- * make rascas_propagate return RASCAS_E_CAPPED when a packet was capped. */
+ * make rascas_propagate return RASCAS_E_CAPPED when a packet was capped.
+ * Core-skipping (Sect. 3.2.1, the acceleration the paper uses for its galaxy
+ * image, Sect. 5.1): a scattering whose frequency lies in the core,
+ * |x_in| < x_crit in the scatterer's Doppler units, draws the scatterer's
+ * perpendicular velocity from the Maxwellian restricted to |u_perp| >= x_crit
+ * (Ahn et al. 2002; Dijkstra et al. 2006), which moves the photon to the wing
+ * at once.  x_crit = core_skip (>= 0; 0 = off), or, when core_skip_f > 0,
+ * x_crit = core_skip_f (a tau_cell)^(1/3) per scattering, tau_cell being the
+ * line-centre optical depth of the scattering line across the packet's leaf
+ * (the paper follows Smith et al. 2015, whose rule it does not print; this
+ * form follows the (a tau)^(1/3) frequency scale at which thick media let
+ * photons out).  It biases the redistribution: spectra of dust-free media
+ * stay the same for x_crit well inside their peaks; with dust it
+ * underestimates the extinction (Sect. 3.2.1).  RASCAS_E_ARG for negative
+ * values. */
 typedef struct {
     int32_t recoil, isotropic, keep_dir, fail_on_cap;
     double x_gauss;
     int64_t max_scatt, max_steps;
     double tau_stop;
     uint64_t seed;
+    double core_skip, core_skip_f;
 } rascas_physics;
 
 /* Detector: frequency axis [nu_lo, nu_hi) in nbin bins (external frame),
@@ -195,16 +210,44 @@ const char *rascas_last_error(const rascas_ctx *ctx);
 int rascas_set_stream(rascas_ctx *ctx, void *stream);
 
 /* ---- problem set-up (the paper's problem statement: mesh + fields,
- *      lines, domain, sources, peeling directions) ----------------------- */
+ *      lines, domain, sources, peeling directions) -----------------------
+ * Set-up calls copy their arguments into the context (the caller keeps its
+ * structs) and return RASCAS_E_ARG for out-of-range values without changing
+ * the context.  They may be called in any order before the first run and
+ * again between runs; rascas_propagate and the calls after it need the
+ * octree, domain, lines and physics (RASCAS_E_STATE otherwise). */
 
 /* Copy an octree and its leaf fields to the device (mem: where the arrays
  * live).  Validates the tree (RASCAS_E_ARG on malformed input), derives the
  * father and neighbour links of Sect. 4.3 and the leaf levels, and packs the
  * fields into 32-byte leaf records. */
 int rascas_load_octree(rascas_ctx *ctx, const rascas_octree *tree, int mem);
+/* The computational domain of Sect. 4 (sphere, shell, slab periodic in x and
+ * y, cube) inside the unit box.  Leaves that cannot reach its border are
+ * flagged so that the walk skips the border distance there (re-derived when
+ * the octree or the domain changes). */
 int rascas_set_domain(rascas_ctx *ctx, const rascas_domain *dom);
+/* The absorbers of Sect. 3.1: nline (1..RASCAS_MAX_LINES) lines of Table 1
+ * with their decay channels (Sect. 3.2.3), and dust (Sects. 3.1.2, 3.2.2;
+ * dust may be NULL = none).  Line i's opacity is its density times
+ * sigma0 H(a, x) with sigma0 = sqrt(pi) e^2 f_lu / (m_e c Delta nu_D) and
+ * a = A_ul / (4 pi Delta nu_D), Delta nu_D = nu0 v_th / c,
+ * v_th = sqrt(2 k_B T / mass_g) (Sect. 3.1.1). */
 int rascas_set_lines(rascas_ctx *ctx, const rascas_line *lines, int32_t nline, const rascas_dust *dust);
+/* The switches, caps and random-stream seed of rascas_physics above
+ * (Sects. 3.2, 3.3, 4.5). */
 int rascas_set_physics(rascas_ctx *ctx, const rascas_physics *phys);
+/* Bounded device work.  The persistent kernels of rascas_propagate, _trace,
+ * _propagate_noalloc and _propagate_batch, and the peeling kernel, give up
+ * once a thread has run max_iterations loop iterations (one walk step per
+ * iteration; 0 = no limit, at most 2^32 - 1) or a launch has run
+ * time_limit_s seconds of the GPU's global timer (0 = no limit; checked
+ * every 256 iterations).  The call then returns RASCAS_E_TIMEOUT; packets in
+ * flight are left unfinished (status RASCAS_PK_ACTIVE where statuses are
+ * returned), packets never started keep their output slots untouched, and
+ * tallies hold what was accumulated.  The context stays usable.  Default:
+ * no limits.  Not in the paper: a guard of this implementation. */
+int rascas_set_limits(rascas_ctx *ctx, int64_t max_iterations, double time_limit_s);
 /* How every later call evaluates the Hjerting-Voigt function H(a, x) of the
  * line opacities (Sect. 3.3.2 weighs several approximations against an
  * accurate evaluation):
@@ -220,8 +263,12 @@ int rascas_set_physics(rascas_ctx *ctx, const rascas_physics *phys);
  * peeling tallies, rascas_peel_adjoint and rascas_eval_voigt.  The context
  * keeps the method; RASCAS_E_ARG for any other value. */
 int rascas_set_voigt(rascas_ctx *ctx, int method);
-/* Also zeroes the tallies (their shapes follow the detector). */
+/* The mock observations of Sect. 5.1 (peeling-off towards fixed observer
+ * directions into spectra, images and spectral cubes) and the frequency axis
+ * of the angle-integrated escape spectrum (Sect. 4.4 outputs).  Allocates the
+ * tallies and zeroes them (their shapes follow the detector). */
 int rascas_set_detector(rascas_ctx *ctx, const rascas_detector *det);
+/* Zero every tally of the detector (asynchronous, on the context's stream). */
 int rascas_zero_tallies(rascas_ctx *ctx);
 /* Capacity, in 64-byte records, of the device buffer of peeling rays (one per
  * emission or scattering and observer direction, Sect. 3.1 peeling) that the
@@ -244,7 +291,11 @@ int rascas_set_peel_capacity(rascas_ctx *ctx, int64_t records);
 int rascas_propagate(rascas_ctx *ctx, const rascas_packets_in *in, int64_t n,
                      const rascas_packets_out *out, int mem, rascas_run_stats *stats);
 
-/* Copy a tally (kind = RASCAS_TALLY_*) into dst (count floats, mem). */
+/* Copy a tally (kind = RASCAS_TALLY_*) into dst (count floats, mem): the
+ * escape spectrum (one per escaped packet, Sect. 4.4) or the peeled spectra,
+ * images and cubes (sums of w exp(-tau) per bin, Sect. 5.1).  count must be
+ * the tally's size (RASCAS_E_ARG otherwise); RASCAS_E_STATE when the
+ * detector does not accumulate that kind.  Host copies synchronise. */
 int rascas_get_tally(rascas_ctx *ctx, int kind, float *dst, size_t count, int mem);
 
 /* Optical depth from pos[3i] along dir[3i] to the domain border at external
@@ -255,6 +306,20 @@ int rascas_get_tally(rascas_ctx *ctx, int kind, float *dst, size_t count, int me
 int rascas_ray_tau(rascas_ctx *ctx, int64_t n, const double *pos, const double *dir,
                    const double *nu, double *tau, int32_t *cells, double *lens,
                    int32_t cap, int32_t *ncell, int mem);
+
+/* Column densities along rays, the ray-tracing use of the walk (the paper's
+ * escape fractions of ionising photons from optical depths integrated along
+ * many rays, and column densities along arbitrary sight lines: Sect. 5
+ * introduction, Sect. 6).  For ray i from pos[3i] along dir[3i] to the domain
+ * border (the leaves of the walk of Sect. 4.3, the same as rascas_ray_tau's):
+ *   cols[3i] = sum n_HI l L, cols[3i+1] = sum n_dust l L,
+ *   cols[3i+2] = sum n_metal l L        (cm^-2; n_dust in its own units x cm)
+ *   tau[i] = sigma_HI cols[3i] + sigma_dust cols[3i+1]
+ * (a continuum optical depth, e.g. sigma_HI = 6.3e-18 cm^2 at 13.6 eV) and
+ * ncell[i] = leaves crossed.  tau and ncell may be NULL; pointers follow mem.
+ * Rays starting outside the box get zeros.  Needs the octree and domain. */
+int rascas_ray_columns(rascas_ctx *ctx, int64_t n, const double *pos, const double *dir, double sigma_HI,
+                       double sigma_dust, double *cols, double *tau, int32_t *ncell, int mem);
 
 /* Run packets like rascas_propagate (same streams, no tallies) and record up
  * to max_events events per packet into events[n][max_events]; nevents[n]
@@ -271,6 +336,16 @@ int rascas_eval_voigt(rascas_ctx *ctx, int64_t n, const float *a, const double *
  * on the stream of packet id[i] starting at draw 0; ndraw[i] = words used. */
 int rascas_sample_upar(rascas_ctx *ctx, int64_t n, const double *x, const float *a,
                        const uint64_t *id, float *u, int32_t *ndraw, int mem);
+
+/* Issue rates of the device's arithmetic pipes, measured by timing long
+ * chains of one instruction kind over a full grid (the denominators of the
+ * instruction-issue roofline of the scattering loop, which is bound by
+ * arithmetic, not by HBM): rates[0] FP32 FMA, rates[1] FP64 FMA, rates[2]
+ * special-function (MUFU EX2), rates[3] 32-bit integer multiply-add, each in
+ * warp-instructions per second for the whole device.  Runs on the legacy
+ * default stream for about a tenth of a second; synchronises.  Not in the
+ * paper: a measurement aid. */
+int rascas_probe_issue_rates(rascas_ctx *ctx, double *rates);
 
 /* ---- adjoint (gradients of the peeled tallies) --------------------------- */
 
@@ -314,9 +389,12 @@ typedef struct {
 enum { RASCAS_BATCH_PERSISTENT = 0,   /* one persistent launch over all models (CUDA graph) */
        RASCAS_BATCH_PER_MODEL = 1 };  /* one launch per model, in sequence (the plain way) */
 
-/* Launch shape tried by the autotuner and its time for the capped batch. */
+/* Launch shape tried by the autotuner and its time for the capped batch:
+ * threads per block, resident blocks per SM, and the refill granularity
+ * (consecutive packets a lane reserves per grab from the work queue, the
+ * analogue of the paper's bundles of N_bundle packets, Sects. 4.4, 4.6). */
 typedef struct {
-    int32_t block, blocks_per_sm;
+    int32_t block, blocks_per_sm, refill;
     double ms;
 } rascas_tune;
 
@@ -329,12 +407,24 @@ int rascas_load_batch(rascas_ctx *ctx, const rascas_model *models, int32_t nmode
  * mode = RASCAS_BATCH_*.  Synchronises; stats (may be NULL) cover the batch,
  * kernel_ms the device time of the whole call. */
 int rascas_propagate_batch(rascas_ctx *ctx, int32_t mode, rascas_run_stats *stats);
+/* rascas_propagate_batch that also returns per-packet results: out's arrays
+ * (any may be NULL, not all) hold every packet of the batch, models in the
+ * order given to rascas_load_batch, each model's packets in its own order
+ * ([sum of npackets] entries; pos and dir x3).  The persistent launch is made
+ * directly (not from the captured graph).  Synchronises. */
+int rascas_propagate_batch_packets(rascas_ctx *ctx, int32_t mode, const rascas_packets_out *out, int mem,
+                                   rascas_run_stats *stats);
 /* Escape spectra [nmodels][nbin] in the order the models were given. */
 int rascas_get_batch_spectra(rascas_ctx *ctx, float *dst, size_t count, int mem);
-/* Time the persistent batch launch for block sizes {64, 128} and every
- * resident-block count per SM, with each packet capped at max_scatt
- * scatterings, and keep the fastest shape for later rascas_propagate_batch
- * calls.  tried (may be NULL) receives up to max_tried timings. */
+/* Time the persistent batch launch, each packet capped at max_scatt
+ * scatterings: block sizes {64, 128} x every resident-block count per SM with
+ * one packet per queue grab, then refill granularities {2, 4, 8, 16} at the
+ * fastest shape; keep the fastest for later rascas_propagate_batch calls.
+ * tried (may be NULL) receives up to max_tried timings. */
+/* Set the batch launch shape by hand (shape->ms is ignored): block = 32, 64,
+ * 96 or 128 threads, blocks_per_sm >= 0 (0 = as many as fit), refill >= 1
+ * (at most 4096).  Results do not depend on the shape. */
+int rascas_set_batch_launch(rascas_ctx *ctx, const rascas_tune *shape);
 int rascas_autotune_batch(rascas_ctx *ctx, int64_t max_scatt, rascas_tune *best, rascas_tune *tried,
                           int32_t max_tried, int32_t *ntried);
 
@@ -351,19 +441,20 @@ int rascas_autotune_batch(rascas_ctx *ctx, int64_t max_scatt, rascas_tune *best,
  * device scratch (work-queue head, counters, a parameter copy and the staging
  * of up to RASCAS_NOALLOC_MAX_PACKETS packets, 8 MiB in all) is a static
  * device array that every GPU loading the library holds until the process
- * exits.  The context must already be set up (octree, domain, lines,
- * physics).  No counterpart in the paper: this is an interface variant only.
+ * exits.  rascas_create looks up the array's device address, which loads the
+ * module holding it: the 8 MiB are taken then, so create the context before
+ * handing the free memory to another pool.  The context must already be set
+ * up (octree, domain, lines, physics).  No counterpart in the paper: this is
+ * an interface variant only.
  *
  * in/out are HOST arrays (as rascas_packets_in / rascas_packets_out); out and
  * stats may be NULL.  Results per packet are identical to rascas_propagate on
  * the same packets; tallies and peeling are not accumulated (per-packet
  * outputs only).  n > RASCAS_NOALLOC_MAX_PACKETS returns RASCAS_E_ARG.
- * The first call on a device looks up the array's device address (once per
- * device; make that first call before any stream capture).  Every call
- * reuses the same array and clears the parts that must start at zero; calls
- * that overlap on the GPU (several host threads, streams or contexts on one
- * device at once) race on it and must be serialised by the caller.  The call
- * synchronises the context's stream before returning. */
+ * Every call reuses the same array and clears the parts that must start at
+ * zero; calls that overlap on the GPU (several host threads, streams or
+ * contexts on one device at once) race on it and must be serialised by the
+ * caller.  The call synchronises the context's stream before returning. */
 int rascas_propagate_noalloc(rascas_ctx *ctx, const rascas_packets_in *in, int64_t n,
                              const rascas_packets_out *out, rascas_run_stats *stats);
 

@@ -48,7 +48,8 @@ class Dust(C.Structure):
 class Physics(C.Structure):
     _fields_ = [("recoil", C.c_int32), ("isotropic", C.c_int32), ("keep_dir", C.c_int32),
                 ("fail_on_cap", C.c_int32), ("x_gauss", C.c_double), ("max_scatt", C.c_int64),
-                ("max_steps", C.c_int64), ("tau_stop", C.c_double), ("seed", C.c_uint64)]
+                ("max_steps", C.c_int64), ("tau_stop", C.c_double), ("seed", C.c_uint64),
+                ("core_skip", C.c_double), ("core_skip_f", C.c_double)]
 
 
 class Detector(C.Structure):
@@ -88,7 +89,7 @@ class Model(C.Structure):
 
 
 class Tune(C.Structure):
-    _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("ms", C.c_double)]
+    _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("refill", C.c_int32), ("ms", C.c_double)]
 
 
 BATCH_PERSISTENT, BATCH_PER_MODEL = 0, 1
@@ -120,6 +121,9 @@ def lib():
             "rascas_set_domain": [vp, C.POINTER(Domain)],
             "rascas_set_lines": [vp, C.POINTER(Line), i32, C.POINTER(Dust)],
             "rascas_set_physics": [vp, C.POINTER(Physics)],
+            "rascas_set_limits": [vp, i64, C.c_double],
+            "rascas_ray_columns": [vp, i64, vp, vp, C.c_double, C.c_double, vp, vp, vp, C.c_int],
+            "rascas_propagate_batch_packets": [vp, i32, C.POINTER(PacketsOut), C.c_int, C.POINTER(Stats)],
             "rascas_set_detector": [vp, C.POINTER(Detector)],
             "rascas_zero_tallies": [vp],
             "rascas_set_peel_capacity": [vp, i64],
@@ -136,6 +140,8 @@ def lib():
             "rascas_propagate_batch": [vp, i32, C.POINTER(Stats)],
             "rascas_get_batch_spectra": [vp, vp, C.c_size_t, C.c_int],
             "rascas_autotune_batch": [vp, i64, C.POINTER(Tune), C.POINTER(Tune), i32, C.POINTER(i32)],
+            "rascas_set_batch_launch": [vp, C.POINTER(Tune)],
+            "rascas_probe_issue_rates": [vp, C.POINTER(C.c_double)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -263,14 +269,19 @@ class Context:
         self._ck(self._L.rascas_set_voigt(self._h, int(method)), "set_voigt")
 
     def set_physics(self, recoil=1, isotropic=0, keep_dir=0, x_gauss=8.0, max_scatt=0, max_steps=0,
-                    tau_stop=50.0, seed=0, fail_on_cap=0):
+                    tau_stop=50.0, seed=0, fail_on_cap=0, core_skip=0.0, core_skip_f=0.0):
         p = Physics()
         p.recoil, p.isotropic, p.keep_dir, p.fail_on_cap = int(recoil), int(isotropic), int(keep_dir), int(fail_on_cap)
         p.x_gauss = float(x_gauss)
         p.max_scatt, p.max_steps = int(max_scatt), int(max_steps)
         p.tau_stop = float(tau_stop) if math.isfinite(tau_stop) else 1e300
         p.seed = int(seed)
+        p.core_skip, p.core_skip_f = float(core_skip), float(core_skip_f)
         self._ck(self._L.rascas_set_physics(self._h, C.byref(p)), "set_physics")
+
+    def set_limits(self, max_iterations=0, time_limit_s=0.0):
+        """Bounded device work (rascas_set_limits): 0 = no limit."""
+        self._ck(self._L.rascas_set_limits(self._h, int(max_iterations), float(time_limit_s)), "set_limits")
 
     def set_detector(self, nu_lo, nu_hi, nbin, dirs=(), npix=0, fov=1.0, centre=(0.5, 0.5, 0.5), cube=0):
         d = Detector()
@@ -300,7 +311,7 @@ class Context:
         self.set_lines(wl.lines, wl.dust)
         ph = wl.physics
         self.set_physics(ph.recoil, ph.isotropic, ph.keep_direction, ph.x_gauss, ph.max_scatt, ph.max_steps,
-                         ph.tau_stop, ph.seed)
+                         ph.tau_stop, ph.seed, 0, getattr(ph, "core_skip", 0.0), getattr(ph, "core_skip_f", 0.0))
         self.set_voigt(getattr(ph, "voigt", VOIGT_TASITSIOMI))
         d = wl.detector
         self.set_detector(d.nu_lo, d.nu_hi, d.nbin, d.dirs, d.npix, d.fov, d.centre, d.cube)
@@ -361,6 +372,27 @@ class Context:
         self._ck(r, "ray_tau")
         return tau, cells, lens, ncell
 
+    def ray_columns(self, pos, dir, sigma_HI=0.0, sigma_dust=0.0):
+        """Column densities [n, 3] (N_HI, N_dust, N_metal) from pos along dir
+        to the domain border, the continuum optical depth sigma_HI N_HI +
+        sigma_dust N_dust [n] and the leaves crossed [n]."""
+        pos, dir = _c(pos, np.float64), _c(dir, np.float64)
+        mem = _mem(pos, dir)
+        n = int(pos.shape[0])
+        if mem == DEVICE:
+            import torch
+            dev = pos.device
+            cols = torch.empty((n, 3), dtype=torch.float64, device=dev)
+            tau = torch.empty(n, dtype=torch.float64, device=dev)
+            ncell = torch.empty(n, dtype=torch.int32, device=dev)
+        else:
+            cols, tau, ncell = np.zeros((n, 3)), np.zeros(n), np.zeros(n, np.int32)
+        self._stream_sync_torch(mem)
+        r = self._L.rascas_ray_columns(self._h, n, _ptr(pos), _ptr(dir), float(sigma_HI), float(sigma_dust),
+                                       _ptr(cols), _ptr(tau), _ptr(ncell), mem)
+        self._ck(r, "ray_columns")
+        return cols, tau, ncell
+
     def trace(self, pos, dir, nu, ids, max_events):
         """Events of each packet (host arrays only): structured array
         [n, max_events] (fields of rascas_event) and the counts [n]."""
@@ -401,6 +433,13 @@ class Context:
         self._ck(self._L.rascas_sample_upar(self._h, n, _ptr(x), _ptr(a), _ptr(ids), _ptr(u), _ptr(nd), mem),
                  "sample_upar")
         return u, nd
+
+    def probe_issue_rates(self):
+        """Measured issue rates (warp-instructions/s, whole device) of the FP32
+        FMA, FP64 FMA, MUFU and IMAD pipes."""
+        r = (C.c_double * 4)()
+        self._ck(self._L.rascas_probe_issue_rates(self._h, r), "probe_issue_rates")
+        return {"ffma": r[0], "dfma": r[1], "mufu": r[2], "imad": r[3]}
 
     # ------------------------------------------------------------ adjoint
     def update_fields(self, n_HI, vx, vy, vz, T, n_dust, n_metal=None):
@@ -459,6 +498,7 @@ class Context:
             M.packets = PacketsIn(*[x.ctypes.data for x in b])
             M.npackets = int(pk.n)
         self.batch_shape = (len(workloads), int(nbin))
+        self._batch_counts = [int(wl.packets.n) for wl in workloads]
         self._ck(self._L.rascas_load_batch(self._h, arr, len(workloads), int(nbin), HOST), "load_batch")
 
     def propagate_batch(self, mode=BATCH_PERSISTENT):
@@ -466,11 +506,28 @@ class Context:
         self._ck(self._L.rascas_propagate_batch(self._h, int(mode), C.byref(st)), "propagate_batch")
         return st.as_dict()
 
+    def propagate_batch_packets(self, mode=BATCH_PERSISTENT):
+        """propagate_batch with per-packet results (host arrays, models in
+        load order): (dict of status, nscatt, nu, pos, dir, path; stats)."""
+        n = sum(self._batch_counts)
+        out = {"status": np.zeros(n, np.int32), "nscatt": np.zeros(n, np.int64), "nu": np.zeros(n),
+               "pos": np.zeros((n, 3)), "dir": np.zeros((n, 3)), "path": np.zeros(n)}
+        pout = PacketsOut(*[_ptr(out[k]) for k in ("status", "nscatt", "nu", "pos", "dir", "path")])
+        st = Stats()
+        self._ck(self._L.rascas_propagate_batch_packets(self._h, int(mode), C.byref(pout), HOST, C.byref(st)),
+                 "propagate_batch_packets")
+        return out, st.as_dict()
+
     def get_batch_spectra(self):
         dst = np.zeros(self.batch_shape, dtype=np.float32)
         self._ck(self._L.rascas_get_batch_spectra(self._h, C.c_void_p(dst.ctypes.data), dst.size, HOST),
                  "get_batch_spectra")
         return dst
+
+    def set_batch_launch(self, block=128, blocks_per_sm=0, refill=1):
+        t = Tune()
+        t.block, t.blocks_per_sm, t.refill = int(block), int(blocks_per_sm), int(refill)
+        self._ck(self._L.rascas_set_batch_launch(self._h, C.byref(t)), "set_batch_launch")
 
     def autotune_batch(self, max_scatt=1000):
         best = Tune()
@@ -478,8 +535,9 @@ class Context:
         nt = C.c_int32()
         self._ck(self._L.rascas_autotune_batch(self._h, int(max_scatt), C.byref(best), tried, 64, C.byref(nt)),
                  "autotune_batch")
-        return {"best": (best.block, best.blocks_per_sm, best.ms),
-                "tried": [(tried[i].block, tried[i].blocks_per_sm, tried[i].ms) for i in range(nt.value)]}
+        return {"best": (best.block, best.blocks_per_sm, best.ms), "refill": best.refill,
+                "tried": [(tried[i].block, tried[i].blocks_per_sm, tried[i].ms, tried[i].refill)
+                          for i in range(nt.value)]}
 
     def _stream_sync_torch(self, mem):
         """Device calls run on torch's current stream."""

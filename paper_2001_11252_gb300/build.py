@@ -1,9 +1,9 @@
 """Build the CUDA library in-tree for GB300 (sm_103a).
 
-Four objects compiled in parallel -- the kernels twice with nvcc (H(a,x) by
+Five objects compiled in parallel -- the kernels twice with nvcc (H(a,x) by
 Tasitsiomi's form, and by the Faddeeva function with -DRG_FADDEEVA=1), the
-allocation-free entry point with nvcc, the C-ABI host code with g++ against the
-CUDA runtime -- linked into
+allocation-free entry point and the issue-rate probes with nvcc, the C-ABI host
+code with g++ against the CUDA runtime -- linked into
 ``paper_2001_11252_gb300/_build/librascas_gb300.so``.  No CMake.
 """
 from __future__ import annotations
@@ -54,16 +54,22 @@ def build(force=False, verbose=False, ptxas_v=False):
     f_obj = os.path.join(BUILD, "kernels_fad.o")
     h_obj = os.path.join(BUILD, "host.o")
     n_obj = os.path.join(BUILD, "noalloc.o")
+    p_obj = os.path.join(BUILD, "probe_rates.o")
     kcmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c",
             os.path.join(CSRC, "kernels.cu"), "-o", k_obj, *inc]
     fcmd = [c if c != k_obj else f_obj for c in kcmd] + ["-DRG_FADDEEVA=1"]
     if ptxas_v:
         kcmd.insert(1, "-Xptxas=-v")
         fcmd.insert(1, "-Xptxas=-v")
-    hcmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-c", os.path.join(CSRC, "host.cpp"), "-o", h_obj, *inc]
+    # no contraction into fused multiply-adds: the host's image-plane basis and
+    # line constants are evaluated exactly as written, on x86 and on Arm
+    hcmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-c", os.path.join(CSRC, "host.cpp"), "-o",
+            h_obj, *inc]
     ncmd = [nvcc, *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-c", os.path.join(CSRC, "noalloc.cu"),
             "-o", n_obj, *inc]
-    cmds = (kcmd, fcmd, hcmd, ncmd)
+    pcmd = [nvcc, *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-c", os.path.join(CSRC, "probe_rates.cu"),
+            "-o", p_obj, *inc]
+    cmds = (kcmd, fcmd, hcmd, ncmd, pcmd)
     procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT) for c in cmds]
     outs = [p.communicate()[0].decode() for p in procs]
     for p, o, c in zip(procs, outs, cmds):
@@ -72,7 +78,7 @@ def build(force=False, verbose=False, ptxas_v=False):
         if verbose and o.strip():
             print(o)
     tmp = LIB + ".tmp%d" % os.getpid()
-    lcmd = [nvcc, *ARCH, "-shared", "-o", tmp, k_obj, f_obj, h_obj, n_obj, "-lcudart"]
+    lcmd = [nvcc, *ARCH, "-shared", "-o", tmp, k_obj, f_obj, h_obj, n_obj, p_obj, "-lcudart"]
     r = subprocess.run(lcmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed: %s\n%s" % (" ".join(lcmd), r.stdout.decode()))

@@ -84,12 +84,18 @@ struct rascas_ctx {
         std::vector<long long> first;    // packet prefix sums in scheduled order
         DevBuf d_rec, d_son, d_nbr, d_top, d_geo, d_first, d_pos, d_dir, d_nu, d_id, d_spec;
         int block = 128, blocks_per_sm = 0;   // launch shape (autotuned)
+        int refill = 1;                       // packets a lane reserves per queue grab (autotuned)
         cudaGraphExec_t graph = nullptr;
         cudaStream_t graph_stream = nullptr;
         unsigned long long graph_key = 0;
     } batch;
     cudaStream_t own_stream = nullptr;    // for graph capture when the context's stream is the legacy one
     unsigned long long version = 1;       // bumped by every set-up call
+    // device address of the allocation-free entry point's static scratch,
+    // resolved when the context is created (the module load that backs it
+    // happens then, not inside rascas_propagate_noalloc)
+    void* noalloc_base = nullptr;
+    size_t noalloc_bytes = 0;
 };
 
 namespace {
@@ -303,7 +309,11 @@ int rascas_create(rascas_ctx** out, int device) {
         return RASCAS_E_CUDA;
     }
     cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
-    if (ctx->d_counters.ensure(sizeof(unsigned long long) * (rg::CNT_N + 1)) != cudaSuccess ||
+    if (rg::noalloc_scratch(&ctx->noalloc_base, &ctx->noalloc_bytes) != cudaSuccess) {
+        delete ctx;
+        return RASCAS_E_CUDA;
+    }
+    if (ctx->d_counters.ensure(sizeof(unsigned long long) * rg::kCounterWords) != cudaSuccess ||
         ctx->d_params.ensure(sizeof(Params)) != cudaSuccess) {
         ctx->d_counters.release();
         delete ctx;
@@ -312,9 +322,11 @@ int rascas_create(rascas_ctx** out, int device) {
     ctx->P.self = (const Params*)ctx->d_params.p;
     ctx->P.counters = (unsigned long long*)ctx->d_counters.p;
     ctx->P.head = ctx->P.counters + rg::CNT_N;
+    ctx->P.abort_flag = (unsigned int*)(ctx->P.counters + rg::CNT_N + 1);
     ctx->P.tau_stop = 50.0;
     ctx->P.x_gauss = 8.0f;
     ctx->P.recoil = 1;
+    ctx->P.refill = 1;
     *out = ctx;
     return RASCAS_OK;
 }
@@ -477,7 +489,8 @@ int rascas_set_voigt(rascas_ctx* ctx, int method) {
 
 int rascas_set_physics(rascas_ctx* ctx, const rascas_physics* ph) {
     if (!ctx || !ph) return RASCAS_E_ARG;
-    if (!(ph->x_gauss > 0.0) || ph->max_scatt < 0 || ph->max_steps < 0 || !(ph->tau_stop > 0.0))
+    if (!(ph->x_gauss > 0.0) || ph->max_scatt < 0 || ph->max_steps < 0 || !(ph->tau_stop > 0.0) ||
+        !(ph->core_skip >= 0.0) || !(ph->core_skip_f >= 0.0))
         return fail(ctx, RASCAS_E_ARG, "physics: bad values");
     ctx->phys = *ph;
     Params& P = ctx->P;
@@ -490,8 +503,24 @@ int rascas_set_physics(rascas_ctx* ctx, const rascas_physics* ph) {
     P.tau_stop = ph->tau_stop;
     P.key0 = (uint32_t)ph->seed;
     P.key1 = (uint32_t)(ph->seed >> 32);
+    P.core_skip = (float)ph->core_skip;
+    P.core_skip_f = (float)ph->core_skip_f;
+    P.core_skip_on = ph->core_skip > 0.0 || ph->core_skip_f > 0.0;
     ++ctx->version;
     ctx->has_phys = true;
+    return RASCAS_OK;
+}
+
+int rascas_set_limits(rascas_ctx* ctx, int64_t max_iterations, double time_limit_s) {
+    if (!ctx || max_iterations < 0 || max_iterations > 0xffffffffLL || !(time_limit_s >= 0.0) ||
+        !(time_limit_s < 1.8e10))
+        return fail(ctx, RASCAS_E_ARG, "set_limits: bad values");
+    Params& P = ctx->P;
+    P.max_iter = (unsigned int)max_iterations;
+    P.time_limit_ns = (unsigned long long)(time_limit_s * 1e9);
+    if (time_limit_s > 0.0 && P.time_limit_ns == 0ull) P.time_limit_ns = 1ull;
+    P.limits = P.max_iter != 0u || P.time_limit_ns != 0ull;
+    ++ctx->version;
     return RASCAS_OK;
 }
 
@@ -504,12 +533,12 @@ int rascas_set_detector(rascas_ctx* ctx, const rascas_detector* d) {
     ctx->det = *d;
     Params& P = ctx->P;
     P.g.nu_lo = d->nu_lo;
-    P.g.nu_inv_range = 1.0 / (d->nu_hi - d->nu_lo);
+    P.g.nu_range = d->nu_hi - d->nu_lo;
     P.g.nbin = d->nbin;
     P.ndir = d->ndir;
     P.npix = d->npix;
     P.cube = d->cube && d->npix > 0 && d->ndir > 0;
-    P.inv_fov = d->npix > 0 ? 1.0 / d->fov : 0.0;
+    P.fov = d->npix > 0 ? d->fov : 1.0;
     for (int ax = 0; ax < 3; ++ax) P.img_c[ax] = d->centre[ax];
     for (int i = 0; i < d->ndir; ++i) {
         double n2 = d->dirs[i][0] * d->dirs[i][0] + d->dirs[i][1] * d->dirs[i][1] + d->dirs[i][2] * d->dirs[i][2];
@@ -613,7 +642,7 @@ int run_propagate(rascas_ctx* ctx, const rascas_packets_in* in, int64_t n, const
         if (!ctx->has_det) {
             P.g.nbin = 1;
             P.g.nu_lo = 0.0;
-            P.g.nu_inv_range = 0.0;
+            P.g.nu_range = 1.0;
         }
     }
     rg::PacketsIn din{in->pos, in->dir, in->nu, in->id, (long long)n, 0};
@@ -659,7 +688,7 @@ int run_propagate(rascas_ctx* ctx, const rascas_packets_in* in, int64_t n, const
         tr.nev = nevents;
     }
     if (tr.nev) CK(cudaMemsetAsync(tr.nev, 0, N * 4, st));
-    CK(cudaMemsetAsync(ctx->d_counters.p, 0, sizeof(unsigned long long) * (rg::CNT_N + 1), st));
+    CK(cudaMemsetAsync(ctx->d_counters.p, 0, sizeof(unsigned long long) * rg::kCounterWords, st));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (stats) {
         CK(cudaEventCreate(&e0));
@@ -692,9 +721,11 @@ int run_propagate(rascas_ctx* ctx, const rascas_packets_in* in, int64_t n, const
             CK(cudaMemsetAsync(ctl, 0, 4 * sizeof(unsigned long long), st));
             CK(walk_propagate(P, din, dout, tr, grid, block, st));
             CK(walk_peel(P, ctx->sms, st));
-            unsigned int parked = 0;
+            unsigned int parked = 0, aborted = 0;
             CK(cudaMemcpyAsync(&parked, P.suspended, sizeof(parked), cudaMemcpyDeviceToHost, st));
+            if (P.limits) CK(cudaMemcpyAsync(&aborted, P.abort_flag, sizeof(aborted), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
+            if (aborted) break;
             if (parked == 0) break;
             if (round > (1LL << 30)) return fail(ctx, RASCAS_E_STATE, "propagate: peeling rounds do not end");
         }
@@ -720,8 +751,8 @@ int run_propagate(rascas_ctx* ctx, const rascas_packets_in* in, int64_t n, const
             CK(cudaMemcpyAsync(nevents, tr.nev, N * 4, cudaMemcpyDeviceToHost, st));
         }
     }
-    unsigned long long cnt[rg::CNT_N] = {};
-    if (stats || mem == RASCAS_HOST || ctx->phys.fail_on_cap) {
+    unsigned long long cnt[rg::kCounterWords] = {};
+    if (stats || mem == RASCAS_HOST || ctx->phys.fail_on_cap || P.limits) {
         CK(cudaMemcpyAsync(cnt, ctx->d_counters.p, sizeof(cnt), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
     }
@@ -746,6 +777,8 @@ int run_propagate(rascas_ctx* ctx, const rascas_packets_in* in, int64_t n, const
         stats->nbor_loads = (int64_t)cnt[rg::CNT_NBOR_LOADS];
         stats->kernel_ms = ms;
     }
+    if (P.limits && cnt[rg::CNT_N + 1] != 0)
+        return fail(ctx, RASCAS_E_TIMEOUT, "propagate: a device iteration or time limit was reached (rascas_set_limits)");
     if (ctx->phys.fail_on_cap && cnt[rg::CNT_CAPPED] > 0)
         return fail(ctx, RASCAS_E_CAPPED, "some packets reached a cap");
     return RASCAS_OK;
@@ -836,6 +869,54 @@ int rascas_ray_tau(rascas_ctx* ctx, int64_t n, const double* pos, const double* 
     return RASCAS_OK;
 }
 
+int rascas_ray_columns(rascas_ctx* ctx, int64_t n, const double* pos, const double* dir, double sigma_HI,
+                       double sigma_dust, double* cols, double* tau, int32_t* ncell, int mem) {
+    if (!ctx || n < 0 || !pos || !dir || !cols || !(sigma_HI >= 0.0) || !(sigma_dust >= 0.0) ||
+        (mem != RASCAS_HOST && mem != RASCAS_DEVICE))
+        return fail(ctx, RASCAS_E_ARG, "ray_columns: bad arguments");
+    if (!ctx->has_mesh) return fail(ctx, RASCAS_E_STATE, "no octree loaded");
+    if (!ctx->has_domain) return fail(ctx, RASCAS_E_STATE, "no domain set");
+    CK(cudaSetDevice(ctx->device));
+    if (n == 0) return RASCAS_OK;
+    cudaStream_t st = ctx->stream;
+    const size_t N = (size_t)n;
+    const double *dpos = pos, *ddir = dir;
+    double *dcols = cols, *dtau = tau;
+    int32_t* dncell = ncell;
+    if (mem == RASCAS_HOST) {
+        CK(ctx->stage_aux.ensure(N * (3 + 3 + 3 + 1) * 8 + N * 4 + 64));
+        double* a = (double*)ctx->stage_aux.p;
+        dpos = a; ddir = a + 3 * N; dcols = a + 6 * N; dtau = tau ? a + 9 * N : nullptr;
+        dncell = ncell ? (int32_t*)(a + 10 * N) : nullptr;
+        CK(cudaMemcpyAsync((void*)dpos, pos, 3 * N * 8, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync((void*)ddir, dir, 3 * N * 8, cudaMemcpyHostToDevice, st));
+    }
+    CK(cudaMemcpyAsync(ctx->d_params.p, &ctx->P, sizeof(Params), cudaMemcpyHostToDevice, st));
+    CK(ctx->ray_init.ensure(N * sizeof(rg::RayInit)));
+    CK(cudaMemsetAsync(ctx->P.head, 0, sizeof(unsigned long long), st));
+    CK(rg::launch_ray_columns(ctx->P, (long long)n, dpos, ddir, dcols, dtau, sigma_HI, sigma_dust, dncell,
+                              (rg::RayInit*)ctx->ray_init.p, ctx->sms, st));
+    if (mem == RASCAS_HOST) {
+        CK(cudaMemcpyAsync(cols, dcols, 3 * N * 8, cudaMemcpyDeviceToHost, st));
+        if (tau) CK(cudaMemcpyAsync(tau, dtau, N * 8, cudaMemcpyDeviceToHost, st));
+        if (ncell) CK(cudaMemcpyAsync(ncell, dncell, N * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return RASCAS_OK;
+}
+
+int rascas_probe_issue_rates(rascas_ctx* ctx, double* rates) {
+    if (!ctx || !rates) return fail(ctx, RASCAS_E_ARG, "probe_issue_rates: bad arguments");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    DevBuf scratch;
+    CK(scratch.ensure(4096));
+    cudaError_t e = rg::probe_issue_rates(ctx->sms, scratch.p, rates);
+    scratch.release();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "probe_issue_rates");
+    return RASCAS_OK;
+}
+
 int rascas_eval_voigt(rascas_ctx* ctx, int64_t n, const float* a, const double* x, float* H, int mem) {
     if (!ctx || n < 0 || !a || !x || !H) return fail(ctx, RASCAS_E_ARG, "eval_voigt: bad arguments");
     CK(cudaSetDevice(ctx->device));
@@ -897,15 +978,14 @@ int rascas_propagate_noalloc(rascas_ctx* ctx, const rascas_packets_in* in, int64
     int r = check_ready(ctx);
     if (r) return r;
     CK(cudaSetDevice(ctx->device));
-    char* base = nullptr;
-    size_t bytes = 0;
-    CK(rg::noalloc_scratch(ctx->device, (void**)&base, &bytes));
-    // layout: counters + queue head | parameter copy | packet staging
+    char* base = (char*)ctx->noalloc_base;
+    const size_t bytes = ctx->noalloc_bytes;
+    // layout: counters, queue head, abort flag | parameter copy | packet staging
     const size_t N = (size_t)n;
     auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
     size_t off = 0;
     unsigned long long* cnt_d = (unsigned long long*)(base + off);
-    off += al(sizeof(unsigned long long) * (rg::CNT_N + 1));
+    off += al(sizeof(unsigned long long) * rg::kCounterWords);
     Params* par_d = (Params*)(base + off);
     off += al(sizeof(Params));
     double* pos = (double*)(base + off); off += al(3 * N * 8);
@@ -924,9 +1004,10 @@ int rascas_propagate_noalloc(rascas_ctx* ctx, const rascas_packets_in* in, int64
     P.ndir = 0;
     P.counters = cnt_d;
     P.head = cnt_d + rg::CNT_N;
+    P.abort_flag = (unsigned int*)(cnt_d + rg::CNT_N + 1);
     P.self = par_d;
     cudaStream_t st = ctx->stream;
-    CK(cudaMemsetAsync(cnt_d, 0, sizeof(unsigned long long) * (rg::CNT_N + 1), st));
+    CK(cudaMemsetAsync(cnt_d, 0, sizeof(unsigned long long) * rg::kCounterWords, st));
     CK(cudaMemcpyAsync(par_d, &P, sizeof(Params), cudaMemcpyHostToDevice, st));
     rg::PacketsIn din{pos, dir, nu, id, (long long)n, 0};
     rg::PacketsOut dout{};
@@ -948,7 +1029,7 @@ int rascas_propagate_noalloc(rascas_ctx* ctx, const rascas_packets_in* in, int64
             if (out->path) CK(cudaMemcpyAsync(out->path, opath, N * 8, cudaMemcpyDeviceToHost, st));
         }
     }
-    unsigned long long cnt[rg::CNT_N] = {};
+    unsigned long long cnt[rg::kCounterWords] = {};
     CK(cudaMemcpyAsync(cnt, cnt_d, sizeof(cnt), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (stats) {
@@ -966,6 +1047,8 @@ int rascas_propagate_noalloc(rascas_ctx* ctx, const rascas_packets_in* in, int64
         stats->son_loads = (int64_t)cnt[rg::CNT_SON_LOADS];
         stats->nbor_loads = (int64_t)cnt[rg::CNT_NBOR_LOADS];
     }
+    if (P.limits && cnt[rg::CNT_N + 1] != 0)
+        return fail(ctx, RASCAS_E_TIMEOUT, "propagate_noalloc: a device iteration or time limit was reached");
     if (ctx->phys.fail_on_cap && cnt[rg::CNT_CAPPED] > 0)
         return fail(ctx, RASCAS_E_CAPPED, "some packets reached a cap");
     return RASCAS_OK;
@@ -1047,7 +1130,7 @@ int rascas_load_batch(rascas_ctx* ctx, const rascas_model* models, int32_t nmode
         for (int ax = 0; ax < 3; ++ax) G.dom_c[ax] = md.domain.centre[ax];
         G.dom_R = md.domain.size;
         G.dom_Rin = md.domain.kind == RASCAS_DOMAIN_SHELL ? md.domain.inner : 0.0;
-        G.nu_lo = md.nu_lo; G.nu_inv_range = 1.0 / (md.nu_hi - md.nu_lo); G.nbin = nbin;
+        G.nu_lo = md.nu_lo; G.nu_range = md.nu_hi - md.nu_lo; G.nbin = nbin;
         G.spec = (float*)B.d_spec.p + (size_t)m * nbin;
         orec += M.rec.size(); oson += M.son.size(); onbr += M.nbr.size(); otop += M.top.size();
         const size_t n = (size_t)md.npackets, o = (size_t)B.first[k];
@@ -1069,7 +1152,31 @@ int rascas_load_batch(rascas_ctx* ctx, const rascas_model* models, int32_t nmode
     return RASCAS_OK;
 }
 
-int rascas_propagate_batch(rascas_ctx* ctx, int32_t mode, rascas_run_stats* stats) {
+}  // extern "C"
+
+namespace {
+
+void fill_stats(rascas_run_stats* stats, const unsigned long long* cnt, double ms) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->packets = (int64_t)cnt[rg::CNT_PACKETS];
+    stats->escaped = (int64_t)cnt[rg::CNT_ESCAPED];
+    stats->absorbed = (int64_t)cnt[rg::CNT_ABSORBED];
+    stats->capped = (int64_t)cnt[rg::CNT_CAPPED];
+    stats->errors = (int64_t)cnt[rg::CNT_ERRORS];
+    stats->nscatt_line = (int64_t)cnt[rg::CNT_SCATT_LINE];
+    stats->nscatt_dust = (int64_t)cnt[rg::CNT_SCATT_DUST];
+    stats->ncross = (int64_t)cnt[rg::CNT_CROSS];
+    stats->upar_trials = (int64_t)cnt[rg::CNT_UPAR_TRIALS];
+    stats->leaf_loads = (int64_t)cnt[rg::CNT_LEAF_LOADS];
+    stats->son_loads = (int64_t)cnt[rg::CNT_SON_LOADS];
+    stats->nbor_loads = (int64_t)cnt[rg::CNT_NBOR_LOADS];
+    stats->kernel_ms = ms;
+}
+
+// the batch run; `out` (device buffers in scheduled order, or all null) gets
+// per-packet results, in which case the persistent launch is made directly
+// rather than from the captured graph
+int run_batch(rascas_ctx* ctx, int32_t mode, const rg::PacketsOut& out, rascas_run_stats* stats) {
     if (!ctx || (mode != RASCAS_BATCH_PERSISTENT && mode != RASCAS_BATCH_PER_MODEL))
         return fail(ctx, RASCAS_E_ARG, "propagate_batch: bad arguments");
     auto& B = ctx->batch;
@@ -1088,24 +1195,26 @@ int rascas_propagate_batch(rascas_ctx* ctx, int32_t mode, rascas_run_stats* stat
     P.models = (const rg::Geo*)B.d_geo.p;
     P.model_first = (const long long*)B.d_first.p;
     P.nmodels = B.nmodels;
+    P.refill = B.refill;
     rg::PacketsIn in{(const double*)B.d_pos.p, (const double*)B.d_dir.p, (const double*)B.d_nu.p,
                      (const uint64_t*)B.d_id.p, B.npackets, 0};
-    rg::PacketsOut out{};
     rg::TraceOut tr{nullptr, nullptr, 0};
+    const bool direct = out.status || out.nscatt || out.nu || out.pos || out.dir || out.path;
     const int block = B.block;
     int per_sm = B.blocks_per_sm > 0 ? B.blocks_per_sm : rg::propagate_batch_blocks_per_sm(P.nline, block);
     if (per_sm < 1) per_sm = 1;
     const int grid = ctx->sms * per_sm;
-    const size_t cnt_bytes = sizeof(unsigned long long) * (rg::CNT_N + 1);
+    const size_t cnt_bytes = sizeof(unsigned long long) * rg::kCounterWords;
     const size_t spec_bytes = sizeof(float) * (size_t)B.nmodels * B.nbin;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     CK(cudaEventRecord(e0, st));
-    if (mode == RASCAS_BATCH_PERSISTENT) {
+    if (mode == RASCAS_BATCH_PERSISTENT && !direct) {
         // one persistent launch over every model's packets, replayed from a
         // captured CUDA graph (re-captured when the set-up or shape changed)
-        unsigned long long key = ctx->version * 1000003ULL + (unsigned long long)(block * 64 + per_sm);
+        unsigned long long key = ctx->version * 1000003ULL +
+                                 (unsigned long long)((block * 64 + per_sm) * 4096 + B.refill);
         if (!B.graph || B.graph_key != key || B.graph_stream != st) {
             if (B.graph) {
                 cudaGraphExecDestroy(B.graph);
@@ -1126,6 +1235,10 @@ int rascas_propagate_batch(rascas_ctx* ctx, int32_t mode, rascas_run_stats* stat
             B.graph_stream = st;
         }
         CK(cudaGraphLaunch(B.graph, st));
+    } else if (mode == RASCAS_BATCH_PERSISTENT) {
+        CK(cudaMemsetAsync(ctx->d_counters.p, 0, cnt_bytes, st));
+        CK(cudaMemsetAsync(B.d_spec.p, 0, spec_bytes, st));
+        CK(walk_propagate(P, in, out, tr, grid, block, st));
     } else {
         // the plain alternative: one launch per model, in sequence
         CK(cudaMemsetAsync(ctx->d_counters.p, 0, cnt_bytes, st));
@@ -1140,37 +1253,78 @@ int rascas_propagate_batch(rascas_ctx* ctx, int32_t mode, rascas_run_stats* stat
             rg::PacketsIn ink = in;
             ink.first = B.first[k];
             ink.n = B.first[k + 1];
-            long long blocks = (n + block - 1) / block;
+            long long blocks = (n + (long long)block * Pk.refill - 1) / ((long long)block * Pk.refill);
             int gk = (int)(blocks < grid ? blocks : grid);
             CK(cudaMemsetAsync(P.head, 0, sizeof(unsigned long long), st));
             CK(walk_propagate(Pk, ink, out, tr, gk, block, st));
         }
     }
     CK(cudaEventRecord(e1, st));
-    unsigned long long cnt[rg::CNT_N] = {};
+    unsigned long long cnt[rg::kCounterWords] = {};
     CK(cudaMemcpyAsync(cnt, ctx->d_counters.p, sizeof(cnt), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (stats) {
-        std::memset(stats, 0, sizeof(*stats));
-        stats->packets = (int64_t)cnt[rg::CNT_PACKETS];
-        stats->escaped = (int64_t)cnt[rg::CNT_ESCAPED];
-        stats->absorbed = (int64_t)cnt[rg::CNT_ABSORBED];
-        stats->capped = (int64_t)cnt[rg::CNT_CAPPED];
-        stats->errors = (int64_t)cnt[rg::CNT_ERRORS];
-        stats->nscatt_line = (int64_t)cnt[rg::CNT_SCATT_LINE];
-        stats->nscatt_dust = (int64_t)cnt[rg::CNT_SCATT_DUST];
-        stats->ncross = (int64_t)cnt[rg::CNT_CROSS];
-        stats->upar_trials = (int64_t)cnt[rg::CNT_UPAR_TRIALS];
-        stats->leaf_loads = (int64_t)cnt[rg::CNT_LEAF_LOADS];
-        stats->son_loads = (int64_t)cnt[rg::CNT_SON_LOADS];
-        stats->nbor_loads = (int64_t)cnt[rg::CNT_NBOR_LOADS];
-        stats->kernel_ms = ms;
-    }
+    if (stats) fill_stats(stats, cnt, ms);
+    if (P.limits && cnt[rg::CNT_N + 1] != 0)
+        return fail(ctx, RASCAS_E_TIMEOUT, "propagate_batch: a device iteration or time limit was reached");
     return RASCAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rascas_propagate_batch(rascas_ctx* ctx, int32_t mode, rascas_run_stats* stats) {
+    return run_batch(ctx, mode, rg::PacketsOut{}, stats);
+}
+
+int rascas_propagate_batch_packets(rascas_ctx* ctx, int32_t mode, const rascas_packets_out* out, int mem,
+                                   rascas_run_stats* stats) {
+    if (!ctx || !out || (mem != RASCAS_HOST && mem != RASCAS_DEVICE))
+        return fail(ctx, RASCAS_E_ARG, "propagate_batch_packets: bad arguments");
+    auto& B = ctx->batch;
+    if (B.nmodels < 1) return fail(ctx, RASCAS_E_STATE, "propagate_batch_packets: no batch loaded");
+    CK(cudaSetDevice(ctx->device));
+    // results land in scheduled order on the device, then move per model to
+    // the caller's order (models as given to rascas_load_batch)
+    const size_t N = (size_t)(B.npackets > 0 ? B.npackets : 1);
+    CK(ctx->stage_out.ensure(N * (4 + 8 + 8 + 24 + 24 + 8) + 64));
+    char* o = (char*)ctx->stage_out.p;
+    double* onu = (double*)o;
+    double* opos = onu + N;
+    double* odir = opos + 3 * N;
+    double* opath = odir + 3 * N;
+    int64_t* ons = (int64_t*)(opath + N);
+    int32_t* ost = (int32_t*)(ons + N);
+    rg::PacketsOut dout{out->status ? ost : nullptr, out->nscatt ? ons : nullptr, out->nu ? onu : nullptr,
+                        out->pos ? opos : nullptr, out->dir ? odir : nullptr, out->path ? opath : nullptr};
+    if (!(dout.status || dout.nscatt || dout.nu || dout.pos || dout.dir || dout.path))
+        return fail(ctx, RASCAS_E_ARG, "propagate_batch_packets: no output array");
+    int r = run_batch(ctx, mode, dout, stats);
+    if (r != RASCAS_OK && r != RASCAS_E_TIMEOUT) return r;
+    cudaStream_t st = ctx->stream ? ctx->stream : ctx->own_stream;
+    const cudaMemcpyKind kind = mem == RASCAS_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    // caller offset of each model: prefix sums over the models in given order
+    std::vector<long long> off_given(B.nmodels + 1, 0);
+    std::vector<long long> count(B.nmodels, 0);
+    for (int k = 0; k < B.nmodels; ++k) count[B.order[k]] = B.first[k + 1] - B.first[k];
+    for (int m = 0; m < B.nmodels; ++m) off_given[m + 1] = off_given[m] + count[m];
+    for (int k = 0; k < B.nmodels; ++k) {
+        const size_t src = (size_t)B.first[k], n = (size_t)(B.first[k + 1] - B.first[k]);
+        const size_t dst = (size_t)off_given[B.order[k]];
+        if (n == 0) continue;
+        if (out->status) CK(cudaMemcpyAsync(out->status + dst, ost + src, n * 4, kind, st));
+        if (out->nscatt) CK(cudaMemcpyAsync(out->nscatt + dst, ons + src, n * 8, kind, st));
+        if (out->nu) CK(cudaMemcpyAsync(out->nu + dst, onu + src, n * 8, kind, st));
+        if (out->pos) CK(cudaMemcpyAsync(out->pos + 3 * dst, opos + 3 * src, 3 * n * 8, kind, st));
+        if (out->dir) CK(cudaMemcpyAsync(out->dir + 3 * dst, odir + 3 * src, 3 * n * 8, kind, st));
+        if (out->path) CK(cudaMemcpyAsync(out->path + dst, opath + src, n * 8, kind, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    return r;
 }
 
 int rascas_get_batch_spectra(rascas_ctx* ctx, float* dst, size_t count, int mem) {
@@ -1189,37 +1343,59 @@ int rascas_autotune_batch(rascas_ctx* ctx, int64_t max_scatt, rascas_tune* best,
     auto& B = ctx->batch;
     if (B.nmodels < 1) return fail(ctx, RASCAS_E_STATE, "autotune_batch: no batch loaded");
     const long long saved_scatt = ctx->P.max_scatt;
-    const int saved_block = B.block, saved_per_sm = B.blocks_per_sm;
+    const int saved_block = B.block, saved_per_sm = B.blocks_per_sm, saved_refill = B.refill;
     ctx->P.max_scatt = max_scatt;   // short runs of the same batch, each packet capped
     ++ctx->version;
-    rascas_tune bt{0, 0, 0.0};
+    rascas_tune bt{0, 0, 0, 0.0};
     int nt = 0;
     int rc = RASCAS_OK;
+    auto trial = [&](int block, int per_sm, int refill) {
+        B.block = block;
+        B.blocks_per_sm = per_sm;
+        B.refill = refill;
+        rascas_run_stats st;
+        rc = rascas_propagate_batch(ctx, RASCAS_BATCH_PERSISTENT, &st);
+        if (rc != RASCAS_OK) return;
+        rascas_tune t{block, per_sm, refill, st.kernel_ms};
+        if (tried && nt < max_tried) tried[nt] = t;
+        ++nt;
+        if (bt.ms == 0.0 || t.ms < bt.ms) bt = t;
+    };
+    // launch shape first (one packet per grab), then the refill granularity
+    // at the best shape
     for (int block : {64, 128}) {
         int occ = rg::propagate_batch_blocks_per_sm(ctx->P.nline, block);
-        for (int per_sm = 1; per_sm <= occ && rc == RASCAS_OK; ++per_sm) {
-            B.block = block;
-            B.blocks_per_sm = per_sm;
-            rascas_run_stats st;
-            rc = rascas_propagate_batch(ctx, RASCAS_BATCH_PERSISTENT, &st);
-            if (rc != RASCAS_OK) break;
-            rascas_tune t{block, per_sm, st.kernel_ms};
-            if (tried && nt < max_tried) tried[nt] = t;
-            ++nt;
-            if (bt.ms == 0.0 || t.ms < bt.ms) bt = t;
-        }
+        for (int per_sm = 1; per_sm <= occ && rc == RASCAS_OK; ++per_sm) trial(block, per_sm, 1);
+    }
+    const int sb = bt.block, sp = bt.blocks_per_sm;
+    for (int refill : {2, 4, 8, 16}) {
+        if (rc != RASCAS_OK) break;
+        trial(sb, sp, refill);
     }
     ctx->P.max_scatt = saved_scatt;
     ++ctx->version;
     if (rc != RASCAS_OK) {
         B.block = saved_block;
         B.blocks_per_sm = saved_per_sm;
+        B.refill = saved_refill;
         return rc;
     }
     B.block = bt.block;
     B.blocks_per_sm = bt.blocks_per_sm;
+    B.refill = bt.refill;
     if (best) *best = bt;
     if (ntried) *ntried = nt;
+    return RASCAS_OK;
+}
+
+int rascas_set_batch_launch(rascas_ctx* ctx, const rascas_tune* shape) {
+    if (!ctx || !shape || shape->block < 32 || shape->block > rg::propagate_block_size() || shape->block % 32 != 0 ||
+        shape->blocks_per_sm < 0 || shape->refill < 1 || shape->refill > 4096)
+        return fail(ctx, RASCAS_E_ARG, "set_batch_launch: block 32..128 in steps of 32, blocks_per_sm >= 0, refill 1..4096");
+    auto& B = ctx->batch;
+    B.block = shape->block;
+    B.blocks_per_sm = shape->blocks_per_sm;
+    B.refill = shape->refill;
     return RASCAS_OK;
 }
 

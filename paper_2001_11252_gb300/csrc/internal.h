@@ -64,8 +64,9 @@ struct Geo {
     double dom_c[3];
     double dom_R;          // sphere / shell outer radius, slab half-thickness, cube half side
     double dom_Rin;        // shell inner radius
-    // escape spectrum: bin = floor((nu - nu_lo) * nu_inv_range * nbin)
-    double nu_lo, nu_inv_range;
+    // escape spectrum: bin = floor((nu - nu_lo) / nu_range * nbin), the
+    // plain definition's operations in FP64 (exact ties bin as in the oracle)
+    double nu_lo, nu_range;
     int nbin;
     float* spec;
 };
@@ -103,7 +104,7 @@ struct Params {
     double dirs[kMaxDirs][3];
     double eu[kMaxDirs][3], ev[kMaxDirs][3];
     double img_c[3];
-    double inv_fov;
+    double fov;
     float* pspec;
     float* pimg;
     float* pcube;
@@ -127,10 +128,27 @@ struct Params {
     double dir_inv[kMaxDirs][3];      // 1 / dirs (0 where a component is 0)
     float dir_kp[kMaxDirs][3][2];     // dirs as FP32 pairs
     int voigt;                        // H(a,x) method of the walk kernels (host side: picks the build)
+    // core-skipping (Sect. 3.2.1): scatterings with |x_in| < x_crit draw the
+    // perpendicular velocity from the Gaussian restricted to |u_perp| >= x_crit;
+    // x_crit = core_skip, or core_skip_f (a tau_cell)^(1/3) when core_skip_f > 0
+    int core_skip_on;
+    float core_skip, core_skip_f;
+    // bounded device work of the persistent kernels: per-thread loop
+    // iterations and nanoseconds of %globaltimer per launch (0 = no limit);
+    // a kernel that reaches one raises *abort_flag, every warp then stops
+    int limits;
+    unsigned int max_iter;
+    unsigned long long time_limit_ns;
+    unsigned int* abort_flag;
+    // batch queue: consecutive packets a lane reserves per queue grab
+    int refill;
     // run scratch
     unsigned long long* counters;  // [CNT_N]
     unsigned long long* head;      // work-queue head
 };
+
+// words of the counter block: CNT_N counters, the work-queue head, the abort flag
+constexpr int kCounterWords = CNT_N + 2;
 
 struct PacketsIn {
     const double* pos;
@@ -193,12 +211,19 @@ cudaError_t launch_ray_tau(const Params& P, long long n, const double* pos, cons
 cudaError_t launch_ray_tau_fad(const Params& P, long long n, const double* pos, const double* dir,
                                const double* nu, double* tau, int32_t* cells, double* lens, int cap, int32_t* ncell,
                                RayInit* init, int sms, cudaStream_t st);
+// column densities along rays (default build only): cols[3i..3i+2] = N_HI,
+// N_dust, N_metal; tau[i] = sig_hi N_HI + sig_d N_dust (either may be null)
+cudaError_t launch_ray_columns(const Params& P, long long n, const double* pos, const double* dir, double* cols,
+                               double* tau, double sig_hi, double sig_d, int32_t* ncell, RayInit* init, int sms,
+                               cudaStream_t st);
 cudaError_t launch_pack_fields(long long n, const float* nh, const float* vx, const float* vy, const float* vz,
                                const float* T, const float* nd, const float* nm, float4* rec, cudaStream_t st);
 cudaError_t launch_eval_voigt(long long n, const float* a, const double* x, float* H, int method, cudaStream_t st);
 cudaError_t launch_sample_upar(const Params& P, long long n, const double* x, const float* a,
                                const uint64_t* id, float* u, int32_t* ndraw, cudaStream_t st);
-cudaError_t noalloc_scratch(int device, void** ptr, size_t* bytes);
+cudaError_t noalloc_scratch(void** ptr, size_t* bytes);
+// issue rates of the FP32 FMA, FP64 FMA, MUFU and IMAD pipes (probe_rates.cu)
+cudaError_t probe_issue_rates(int sms, void* scratch, double rates[4]);
 int propagate_block_size();
 size_t propagate_smem(int nline, int block);
 int propagate_blocks_per_sm(int block, bool peel);

@@ -290,7 +290,7 @@ __device__ __forceinline__ void pair_add(float& xh, float& xl, float d) {
 
 // resonant or fluorescent scattering on line IL (Sects. 3.2.1, 3.2.3, 3.3)
 template <int NL, bool PEEL, int IL>
-__device__ __forceinline__ void scatter_line(const Params& P, Packet<NL>& s, float x_in, Tallies& tl) {
+__device__ __forceinline__ void scatter_line(const Params& P, const Geo& G, Packet<NL>& s, float x_in, Tallies& tl) {
     const LineDev& L = P.line[IL];
     int ch = 0;
     double chnu = L.nu0;
@@ -329,8 +329,17 @@ __device__ __forceinline__ void scatter_line(const Params& P, Packet<NL>& s, flo
         s.status = RASCAS_PK_ERROR_;
         return;
     }
+    // u_perp pair (Sect. 3.2.1), polar form; core-skipping restricts the
+    // Gaussian to |u_perp| >= x_crit for core photons (|x_in| < x_crit)
     float r1 = s.rng.u23(), r2 = s.rng.u23();
-    float rho = sqrtf(-logf(r1));
+    float xc2 = 0.0f;
+    if (P.core_skip_on) {
+        float xc = P.core_skip;
+        if (P.core_skip_f > 0.0f)   // tau_cell: line-centre optical depth across the leaf
+            xc = P.core_skip_f * cbrtf(s.cc.a[IL] * (s.cc.kap0[IL] * ldexpf(G.box_cm_f, -s.w.level)));
+        if (fabsf(x_in) < xc) xc2 = xc * xc;
+    }
+    float rho = sqrtf(xc2 - logf(r1));
     float sn, cs;
     sincospif(2.0f * r2, &sn, &cs);
     float up1 = rho * cs, up2 = rho * sn;
@@ -466,8 +475,8 @@ __device__ __forceinline__ void finish_packet(const Params& P, const Geo& G, con
     tl.cap += s.status == RASCAS_PK_CAPPED_;
     tl.err += s.status == RASCAS_PK_ERROR_;
     if (s.status == RASCAS_PK_ESCAPED_ && G.spec != nullptr) {
-        double t = __dmul_rn(__dsub_rn(nu_ext, G.nu_lo), G.nu_inv_range);
-        double fb = floor(t * (double)G.nbin);
+        double t = __ddiv_rn(__dsub_rn(nu_ext, G.nu_lo), G.nu_range);
+        double fb = floor(__dmul_rn(t, (double)G.nbin));
         if (fb >= 0.0 && fb < (double)G.nbin) atomicAdd(G.spec + (int)fb, 1.0f);
     }
 }
@@ -600,10 +609,10 @@ __device__ __forceinline__ void advance(const Params& P, const Geo& G, Packet<NL
                     for (int j = 0; j <= i; ++j) ai += kl[j];
                     if (rk < ai) il = i;
                 }
-                if (il == 0) scatter_line<NL, PEEL, 0>(P, s, xin[0], tl);
-                if (NL > 1 && il == 1) scatter_line<NL, PEEL, (NL > 1 ? 1 : 0)>(P, s, xin[NL > 1 ? 1 : 0], tl);
-                if (NL > 2 && il == 2) scatter_line<NL, PEEL, (NL > 2 ? 2 : 0)>(P, s, xin[NL > 2 ? 2 : 0], tl);
-                if (NL > 3 && il == 3) scatter_line<NL, PEEL, (NL > 3 ? 3 : 0)>(P, s, xin[NL > 3 ? 3 : 0], tl);
+                if (il == 0) scatter_line<NL, PEEL, 0>(P, G, s, xin[0], tl);
+                if (NL > 1 && il == 1) scatter_line<NL, PEEL, (NL > 1 ? 1 : 0)>(P, G, s, xin[NL > 1 ? 1 : 0], tl);
+                if (NL > 2 && il == 2) scatter_line<NL, PEEL, (NL > 2 ? 2 : 0)>(P, G, s, xin[NL > 2 ? 2 : 0], tl);
+                if (NL > 3 && il == 3) scatter_line<NL, PEEL, (NL > 3 ? 3 : 0)>(P, G, s, xin[NL > 3 ? 3 : 0], tl);
             }
             if (s.status == RASCAS_PK_ACTIVE_) {
                 ++s.nscatt;
@@ -619,6 +628,29 @@ __device__ __forceinline__ void advance(const Params& P, const Geo& G, Packet<NL
         }
     }
     if (TRACE && evt && tr.nev) trace_record<NL>(s, tr, nu_ext_now<NL>(P, s));
+}
+
+// nanoseconds of the GPU's global timer
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded device work: true (for the whole warp) once this thread has run
+// max_iter loop iterations, the launch has run time_limit_ns, or another warp
+// has raised the abort flag; the first warp to stop raises it.  `iters` is
+// the same in every lane of the warp (the loops are warp-synchronous).
+__device__ __forceinline__ bool out_of_bounds(const Params& P, uint32_t& iters, unsigned long long t0) {
+    ++iters;
+    bool stop = P.max_iter != 0u && iters > P.max_iter;
+    if ((iters & 255u) == 0u) {
+        if (*(volatile unsigned int*)P.abort_flag != 0u) stop = true;
+        if (P.time_limit_ns != 0ull && global_ns() - t0 > P.time_limit_ns) stop = true;
+    }
+    if (!__any_sync(kFull, stop)) return false;
+    if ((threadIdx.x & 31u) == 0u) atomicExch(P.abort_flag, 1u);
+    return true;
 }
 
 __device__ __forceinline__ void flush(const Params& P, unsigned long long v, int which) {
@@ -638,8 +670,14 @@ __device__ __forceinline__ int model_of(const Params& P, long long idx) {
     return lo;
 }
 
+// resident blocks of 128 threads per SM the transport kernel is compiled for
+// (registers per thread <= 65536 / (128 x this))
+#ifndef RG_PROP_MINB
+#define RG_PROP_MINB 4
+#endif
+
 template <int NL, bool PEEL, bool BATCH, bool TRACE>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, RG_PROP_MINB)
 k_propagate(const __grid_constant__ Params P, PacketsIn in, PacketsOut out, TraceOut tr) {
     Packet<NL> s;
     extern __shared__ uint32_t s_dyn[];
@@ -648,6 +686,10 @@ k_propagate(const __grid_constant__ Params P, PacketsIn in, PacketsOut out, Trac
     const unsigned lane = threadIdx.x & 31u;
     bool have = false, drained = false;
     s.mi = 0;
+    uint32_t iters = 0;
+    const unsigned long long t0 = P.limits ? global_ns() : 0ull;
+    // batch runs: a lane reserves P.refill consecutive packets per queue grab
+    long long next = 0, end = 0;
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (PEEL && P.save_flag[gt]) {
         // a packet suspended by the previous round of this launch shape
@@ -659,6 +701,11 @@ k_propagate(const __grid_constant__ Params P, PacketsIn in, PacketsOut out, Trac
         have = true;
     }
     for (;;) {
+        if (P.limits && out_of_bounds(P, iters, t0)) {
+            // a limit was reached: the packet in flight stays unfinished
+            if (have && out.status) out.status[s.idx] = RASCAS_PK_ACTIVE_;
+            break;
+        }
         if (PEEL && __any_sync(kFull, have && s.halt)) {
             // the record buffer is nearly full: park this warp's packets for
             // the next round, after the peel kernel has drained the records
@@ -671,14 +718,29 @@ k_propagate(const __grid_constant__ Params P, PacketsIn in, PacketsOut out, Trac
             break;
         }
         bool want = !have && !drained;
+        if constexpr (BATCH) {
+            if (want && next < end) {
+                // the next packet of this lane's reservation
+                const long long idx = next++;
+                s.mi = model_of(P, idx);
+                begin_packet<NL, TRACE>(P, P.models[s.mi], in, idx, s, tl, tr);
+                have = true;
+                want = false;
+            }
+        }
         unsigned m = __ballot_sync(kFull, want);
         if (m) {
             int leader = __ffs(m) - 1;
+            const int grab = BATCH ? P.refill : 1;
             unsigned long long base = 0;
-            if ((int)lane == leader) base = atomicAdd(P.head, (unsigned long long)__popc(m));
+            if ((int)lane == leader) base = atomicAdd(P.head, (unsigned long long)__popc(m) * grab);
             base = __shfl_sync(kFull, base, leader);
             if (want) {
-                long long idx = in.first + (long long)base + __popc(m & ((1u << lane) - 1u));
+                long long idx = in.first + (long long)base + (long long)__popc(m & ((1u << lane) - 1u)) * grab;
+                if constexpr (BATCH) {
+                    next = idx + 1;
+                    end = min(idx + grab, in.n);
+                }
                 if (idx < in.n) {
                     if constexpr (BATCH) {
                         s.mi = model_of(P, idx);
@@ -741,7 +803,7 @@ __global__ void k_ray_prep(const Params* __restrict__ G, long long n, const doub
     RayInit r;
     if (!locate_point(P.g, p, k, w, loads)) w.leaf = -1, w.oct = w.level = w.i = w.j = w.k = 0;
     RayNu<NL> R;
-    ray_nu<NL>(P, nu[i], k, R);
+    ray_nu<NL>(P, nu ? nu[i] : 0.0, k, R);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         r.p[j] = p[j];
@@ -866,17 +928,21 @@ __device__ __forceinline__ void ray_from_rec(const Params& P, const PeelRec& q, 
 // spectrum channel (or -1) and image pixel (or -1) of a peeled contribution
 __device__ __forceinline__ void peel_bins(const Params& P, const PeelRec& q, int& ch, long long& px) {
     const int nbin = P.g.nbin;
-    const double t = __dmul_rn(__dsub_rn(q.nu_ext, P.g.nu_lo), P.g.nu_inv_range);
-    const double fb = floor(t * (double)nbin);
+    // the plain definitions' operations, unfused (exact ties bin as in the oracle)
+    const double t = __ddiv_rn(__dsub_rn(q.nu_ext, P.g.nu_lo), P.g.nu_range);
+    const double fb = floor(__dmul_rn(t, (double)nbin));
     ch = (fb >= 0.0 && fb < (double)nbin) ? (int)fb : -1;
     px = -1;
     if (P.npix > 0) {
         const int d = q.d;
-        const double r0 = q.p[0] - P.img_c[0], r1 = q.p[1] - P.img_c[1], r2 = q.p[2] - P.img_c[2];
-        const double u = r0 * P.eu[d][0] + r1 * P.eu[d][1] + r2 * P.eu[d][2];
-        const double v = r0 * P.ev[d][0] + r1 * P.ev[d][1] + r2 * P.ev[d][2];
-        const double fu = floor((u * P.inv_fov + 0.5) * (double)P.npix);
-        const double fv = floor((v * P.inv_fov + 0.5) * (double)P.npix);
+        const double r0 = __dsub_rn(q.p[0], P.img_c[0]), r1 = __dsub_rn(q.p[1], P.img_c[1]);
+        const double r2 = __dsub_rn(q.p[2], P.img_c[2]);
+        const double u = __dadd_rn(__dadd_rn(__dmul_rn(r0, P.eu[d][0]), __dmul_rn(r1, P.eu[d][1])),
+                                   __dmul_rn(r2, P.eu[d][2]));
+        const double v = __dadd_rn(__dadd_rn(__dmul_rn(r0, P.ev[d][0]), __dmul_rn(r1, P.ev[d][1])),
+                                   __dmul_rn(r2, P.ev[d][2]));
+        const double fu = floor(__dmul_rn(__dadd_rn(__ddiv_rn(u, P.fov), 0.5), (double)P.npix));
+        const double fv = floor(__dmul_rn(__dadd_rn(__ddiv_rn(v, P.fov), 0.5), (double)P.npix));
         if (fu >= 0.0 && fu < (double)P.npix && fv >= 0.0 && fv < (double)P.npix)
             px = (long long)fv * P.npix + (long long)fu;
     }
@@ -898,7 +964,10 @@ __global__ void __launch_bounds__(128) k_peel(const Params* __restrict__ G) {
     int phase = 0;           // 0: optical depth, 1: adjoint walk
     float scale = 0.0f;
     uint32_t sl = 0, nl = 0, steps = 0, cells = 0;
+    uint32_t iters = 0;
+    const unsigned long long t0 = P.limits ? global_ns() : 0ull;
     for (;;) {
+        if (P.limits && out_of_bounds(P, iters, t0)) break;
         const bool want = !active && !drained;
         const unsigned m = __ballot_sync(kFull, want);
         if (m) {
@@ -971,6 +1040,111 @@ __global__ void __launch_bounds__(128) k_peel(const Params* __restrict__ G) {
 }
 
 #if !RG_FADDEEVA
+// ---------------------------------------------------------------------------
+// Column densities along rays (the ray-tracing use of Sects. 5 and 6: optical
+// depths of ionising photons and sight-line columns): the walk of ray_step
+// with n_HI, n_dust and n_metal times the path length summed per leaf as FP32
+// pairs; no line profile, so the walk touches 12 of the record's 32 bytes.
+// ---------------------------------------------------------------------------
+struct ColRay {
+    double p[3], k[3], inv[3];
+    Where w;
+    f2 nh, nd, nm;
+    int n, zero_run;
+};
+
+__device__ __forceinline__ bool col_step(const Params& P, ColRay& r, uint32_t& sl, uint32_t& nl) {
+    const float4 r0 = __ldg(P.g.rec + 2 * r.w.leaf);
+    const float4 r1 = __ldg(P.g.rec + 2 * r.w.leaf + 1);
+    int axis;
+    const double tf = face_distance(r.p, r.k, r.inv, r.w, axis);
+    bool border = false;
+    double l = tf;
+    if (__float_as_int(r1.w) & kFlagBorder) {
+        const double tb = border_distance(P.g, r.p, r.k, r.inv);
+        border = order_key(tb) <= order_key(tf);
+        if (border) l = tb;
+    }
+    const float lc = (float)l * P.g.box_cm_f;
+    r.nh = f2_add_f(r.nh, r0.x * lc);
+    r.nd = f2_add_f(r.nd, r1.y * lc);
+    r.nm = f2_add_f(r.nm, r1.z * lc);
+    ++r.n;
+    if (border) return true;
+    r.zero_run = order_key(tf) > 0 ? 0 : r.zero_run + 1;
+    if (r.zero_run > 64) return true;
+    move_to_face(r.p, r.k, axis, tf, r.w);
+    wrap_periodic(P.g, r.p, r.k);
+    return !next_leaf(P.g, r.p, r.k, axis, r.w, sl, nl);
+}
+
+// persistent walk over the rays set up by k_ray_prep; the queue head P.head
+// must be zero on entry
+__global__ void __launch_bounds__(128, 8) k_ray_columns(const Params* __restrict__ G, long long n,
+                                                     const RayInit* __restrict__ init, double* cols, double* tau,
+                                                     double sig_hi, double sig_d, int32_t* ncell) {
+    const Params& P = *G;
+    const unsigned lane = threadIdx.x & 31u;
+    ColRay r;
+    long long i = -1;
+    bool active = false, drained = false;
+    uint32_t sl = 0, nl = 0, steps = 0;
+    for (;;) {
+        const bool want = !active && !drained;
+        const unsigned m = __ballot_sync(kFull, want);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            unsigned long long base = 0;
+            if ((int)lane == leader) base = atomicAdd(P.head, (unsigned long long)__popc(m));
+            base = __shfl_sync(kFull, base, leader);
+            if (want) {
+                i = (long long)base + __popc(m & ((1u << lane) - 1u));
+                if (i < n) {
+                    const RayInit& q = init[i];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        r.p[j] = q.p[j];
+                        r.k[j] = q.k[j];
+                        r.inv[j] = q.inv[j];
+                    }
+                    r.w.leaf = q.w[0]; r.w.oct = q.w[1]; r.w.level = q.w[2];
+                    r.w.i = q.w[3]; r.w.j = q.w[4]; r.w.k = q.w[5];
+                    r.nh = r.nd = r.nm = f2{0.0f, 0.0f};
+                    r.n = 0;
+                    r.zero_run = 0;
+                    if (r.w.leaf >= 0) {
+                        steps = 0;
+                        active = true;
+                    } else {
+                        cols[3 * i] = cols[3 * i + 1] = cols[3 * i + 2] = 0.0;
+                        if (tau) tau[i] = 0.0;
+                        if (ncell) ncell[i] = 0;
+                    }
+                } else {
+                    drained = true;
+                }
+            }
+        }
+        if (!__any_sync(kFull, active)) {
+            if (__all_sync(kFull, drained)) break;
+            continue;
+        }
+        if (active) {
+            bool done = col_step(P, r, sl, nl);
+            if (++steps >= (1u << 26)) done = true;
+            if (done) {
+                const double nh = f2_val(r.nh), nd = f2_val(r.nd);
+                cols[3 * i] = nh;
+                cols[3 * i + 1] = nd;
+                cols[3 * i + 2] = f2_val(r.nm);
+                if (tau) tau[i] = __fma_rn(sig_hi, nh, sig_d * nd);
+                if (ncell) ncell[i] = r.n;
+                active = false;
+            }
+        }
+    }
+}
+
 __global__ void k_pack_fields(long long n, const float* nh, const float* vx, const float* vy, const float* vz,
                               const float* T, const float* nd, const float* nm, float4* rec) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1129,6 +1303,21 @@ size_t packet_save_bytes(int nline) {
         case 3: return sizeof(Packet<3>);
         default: return sizeof(Packet<4>);
     }
+}
+
+cudaError_t launch_ray_columns(const Params& P, long long n, const double* pos, const double* dir, double* cols,
+                               double* tau, double sig_hi, double sig_d, int32_t* ncell, RayInit* init, int sms,
+                               cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int block = 128;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ray_columns, block, 0);
+    if (per_sm < 1) per_sm = 1;
+    const long long need = (n + block - 1) / block;
+    const unsigned grid = (unsigned)std::min<long long>(need, (long long)sms * per_sm);
+    k_ray_prep<1><<<(unsigned)need, block, 0, st>>>(P.self, n, pos, dir, nullptr, init);
+    k_ray_columns<<<grid, block, 0, st>>>(P.self, n, init, cols, tau, sig_hi, sig_d, ncell);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pack_fields(long long n, const float* nh, const float* vx, const float* vy, const float* vz,

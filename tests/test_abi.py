@@ -53,3 +53,32 @@ def test_binding_constants_match_header():
     enums = dict((k, int(v)) for k, v in re.findall(r"\b(RASCAS_[A-Z_0-9]+)\s*=\s*(-?\d+)", src))
     for name in ["DOMAIN_SPHERE", "DOMAIN_SLAB", "DOMAIN_CUBE", "DOMAIN_SHELL", "VOIGT_TASITSIOMI", "VOIGT_FADDEEVA"]:
         assert getattr(rg, name) == enums["RASCAS_" + name], name
+
+
+def test_binding_struct_layouts_match_header(tmp_path):
+    """Every struct the binding passes through the ABI has the header's size
+    and field offsets (a C program built against the header prints them)."""
+    from paper_2001_11252_gb300 import _native as N
+    structs = {"rascas_octree": N.Octree, "rascas_domain": N.Domain, "rascas_line": N.Line,
+               "rascas_dust": N.Dust, "rascas_physics": N.Physics, "rascas_detector": N.Detector,
+               "rascas_packets_in": N.PacketsIn, "rascas_packets_out": N.PacketsOut,
+               "rascas_run_stats": N.Stats, "rascas_event": N.Event, "rascas_model": N.Model,
+               "rascas_tune": N.Tune}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rascas_gb300.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('printf("%s __sizeof__ %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f in py._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f[0], cname, f[0]))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = {}
+    for ln in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        a, b, c = ln.split()
+        got[(a, b)] = int(c)
+    for cname, py in structs.items():
+        assert got[(cname, "__sizeof__")] == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])

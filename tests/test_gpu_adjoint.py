@@ -7,6 +7,7 @@ import pytest
 
 import oracle
 import synth
+from gpu_util import rebuild_peel_events
 
 pytestmark = pytest.mark.gpu
 
@@ -24,16 +25,6 @@ def _subset(pk, sel):
     return synth.Packets(pk.pos[sel], pk.dir[sel], pk.nu[sel], pk.ids[sel])
 
 
-def _state_from(o, rec, pid):
-    st = oracle.State()
-    st.p[:] = list(rec["p"]); st.k[:] = list(rec["k"]); st.nu = float(rec["nu"])
-    st.leaf, st.level = int(rec["leaf"]), int(rec["level"])
-    st.ijk[:] = [int(v) for v in rec["ijk"]]
-    st.pid = int(pid); st.ndraw = int(rec["ndraw"])
-    st.nscatt, st.nsteps, st.status = int(rec["nscatt"]), int(rec["nsteps"]), int(rec["status"])
-    return st
-
-
 @pytest.mark.parametrize("voigt", [0, 1])
 def test_gpu_adjoint_matches_oracle(voigt):
     """The GPU adjoint replays the GPU's own scattering record; the oracle
@@ -49,29 +40,9 @@ def test_gpu_adjoint_matches_oracle(voigt):
     ctx.setup(wl)
     o = oracle.Oracle(wl)
     pk = wl.packets
-    cap = 3000
-    ev, cnt = ctx.trace(pk.pos, pk.dir, pk.nu, pk.ids, cap)
-    chosen, events = [], []
-    for i in range(pk.n):
-        n = int(cnt[i])
-        if n >= cap or ev[i, n - 1]["status"] == 0:
-            continue
-        recs = [o.emission_events(_state_from(o, ev[i, 0], pk.ids[i]))]
-        ok = True
-        for j in range(n - 1):
-            st = _state_from(o, ev[i, j], pk.ids[i])
-            _, t = o.event(st, record_events=64)
-            b = ev[i, j + 1]
-            if st.ndraw != b["ndraw"] or st.status != b["status"] or st.leaf != b["leaf"]:
-                ok = False
-                break
-            recs.append(t["events"])
-        if ok:
-            chosen.append(i)
-            events.append(np.concatenate(recs))
+    chosen, events = rebuild_peel_events(ctx, o, pk, 3000)
     assert len(chosen) > 0.8 * pk.n, len(chosen)
-    sub = _subset(pk, np.array(chosen))
-    events = np.concatenate(events)
+    sub = _subset(pk, chosen)
     rng = np.random.default_rng(11)
     gs = [np.ones((3, 8, 8, 24), np.float32), rng.normal(size=(3, 8, 8, 24)).astype(np.float32)]
     for k, g in enumerate(gs):

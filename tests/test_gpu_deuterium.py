@@ -11,7 +11,8 @@ import pytest
 import oracle
 import synth
 from gpu_util import context, gpu_run, oracle_run
-from test_gpu_parity import _ks, _replay, _x
+from gpu_util import replay_steps as _replay
+from test_gpu_parity import _ks, _x
 
 pytestmark = pytest.mark.gpu
 

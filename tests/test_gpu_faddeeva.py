@@ -96,7 +96,7 @@ def test_faddeeva_mean_free_path_gpu():
 def test_faddeeva_replay_per_step():
     """GPU events replayed by the oracle (both with the Faddeeva H) land on
     the same leaf with the same draw count and status."""
-    from test_gpu_parity import _replay
+    from gpu_util import replay_steps as _replay
     wl = _fad(synth.sphere(tau0=1e4, T=100.0, tau_dust=1.0, n_packets=64))
     st = _replay(wl, 64, 200)
     print("Faddeeva replay", st)

@@ -24,7 +24,7 @@ def _bench_sphere():
 
 def test_sphere_bench_batch_sampled_packets():
     """Static sphere, tau0 = 1e6, tau_dust = 1: the whole batch on the GPU;
-    64 sampled packets rerun by the oracle on the same random streams."""
+    4096 sampled packets rerun by the oracle on the same random streams."""
     import torch
     wl, pk = _bench_sphere()
     ctx = context(wl)
@@ -42,12 +42,14 @@ def test_sphere_bench_batch_sampled_packets():
     assert st["nscatt_line"] + st["nscatt_dust"] == int(g["nscatt"].sum())
     assert int(ctx.get_tally(0).sum()) <= st["escaped"]
     # sampled packets, one by one on the oracle
-    sel = np.sort(np.random.default_rng(5).choice(P_BENCH, 64, replace=False))
+    sel = np.sort(np.random.default_rng(5).choice(P_BENCH, 4096, replace=False))
     sub = synth.Packets(pk.pos[sel], pk.dir[sel], pk.nu[sel], pk.ids[sel])
     r, _ = oracle.Oracle(wl).run(packets=sub, threads=16, chunk=1)
     same = (g["status"][sel] == r["status"]) & (g["nscatt"][sel] == r["nscatt"])
-    print("full-size sphere: identical histories %d / 64, <N> %.4g vs %.4g"
-          % (same.sum(), g["nscatt"][sel].mean(), r["nscatt"].mean()))
+    print("full-size sphere: identical histories %d / %d, <N> %.4g vs %.4g"
+          % (same.sum(), sel.size, g["nscatt"][sel].mean(), r["nscatt"].mean()))
+    # the mean scattering count of the sampled packets within 1 %
+    assert abs(g["nscatt"][sel].mean() / r["nscatt"].mean() - 1) < 0.01
     # Histories with the same decisions end at nearly the same frequency: the
     # FP32 velocity sampling differs from FP64 by ~1e-7 per scattering and the
     # difference random-walks over ~3e5 scatterings, except where a far-wing

@@ -14,7 +14,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import context, gpu_run, oracle_run
+from gpu_util import context, gpu_run, near_edge_events, oracle_run, rebuild_peel_events, replay_steps
 
 pytestmark = pytest.mark.gpu
 
@@ -108,40 +108,6 @@ def test_ray_walk_bit_exact(which):
 
 
 # ---------------------------------------------------------------- per-step replay
-def _replay(wl, n_packets, max_events):
-    ctx = context(wl)
-    o = oracle.Oracle(wl)
-    pk = wl.packets
-    ev, cnt = ctx.trace(pk.pos[:n_packets], pk.dir[:n_packets], pk.nu[:n_packets], pk.ids[:n_packets], max_events)
-    ln = wl.lines[0]
-    stats = {"steps": 0, "mismatch": 0, "pos": 0.0, "dir": 0.0, "x": 0.0}
-    for i in range(n_packets):
-        for j in range(cnt[i] - 1):
-            a, b = ev[i, j], ev[i, j + 1]
-            s = oracle.State()
-            s.p[:] = list(a["p"]); s.k[:] = list(a["k"]); s.nu = float(a["nu"])
-            s.leaf, s.level = int(a["leaf"]), int(a["level"])
-            s.ijk[:] = [int(v) for v in a["ijk"]]
-            s.pid = int(pk.ids[i]); s.ndraw = int(a["ndraw"])
-            s.nscatt, s.nsteps, s.status = int(a["nscatt"]), int(a["nsteps"]), 0
-            o.event(s)
-            stats["steps"] += 1
-            ok = (s.status == b["status"] and s.ndraw == b["ndraw"] and s.leaf == b["leaf"]
-                  and s.nscatt == b["nscatt"] and s.nsteps == b["nsteps"])
-            if not ok:
-                stats["mismatch"] += 1
-                continue
-            step = np.linalg.norm(np.array(b["p"]) - np.array(a["p"])) + 1e-300
-            stats["pos"] = max(stats["pos"], np.abs(np.array(s.p) - b["p"]).max() / step)
-            de = np.abs(np.array(s.k) - b["k"]).max()
-            if de > stats["dir"]:
-                stats["dir"] = de
-                stats["dir_case"] = (list(a["k"]), list(b["k"]), list(s.k), int(a["ndraw"]), int(b["ndraw"]))
-            dnu = synth.doppler_width(ln, float(wl.medium.T[b["leaf"]]))
-            stats["x"] = max(stats["x"], abs(s.nu - b["nu"]) / dnu)
-    return stats
-
-
 @pytest.mark.parametrize("which", ["slab", "sphere_dust", "expanding"])
 def test_trace_replay_per_step(which):
     """Each GPU event, replayed by the oracle from the GPU's state, lands on
@@ -155,7 +121,7 @@ def test_trace_replay_per_step(which):
         wl = synth.sphere(tau0=1e4, T=1e4, tau_dust=1.0, n_packets=64)
     else:
         wl = synth.expanding_sphere(n_packets=64, N_HI=1e18)
-    st = _replay(wl, 64, 200)
+    st = replay_steps(wl, 64, 200)
     print(which, st)
     assert st["steps"] > 1000
     assert st["mismatch"] <= 0.002 * st["steps"] + 2
@@ -192,53 +158,137 @@ def test_slab_run_matches_oracle():
 @pytest.mark.parametrize("tau_dust", [0.0, 1.0])
 def test_sphere_run_matches_oracle(tau_dust):
     """Static sphere with dust (the 3-level 8^3 -> 64^3 octree, Sect. 3.4.2),
-    centre-to-edge tau0 = 1e5 here to keep the oracle short."""
-    n = 400 if tau_dust else 150
-    wl = synth.sphere(tau0=1e5, T=1e4, tau_dust=tau_dust, n_packets=n)
+    centre-to-edge tau0 = 1e4 here to keep 3000 oracle packets short: escape
+    and absorption fractions within 4 sigma, <N_scatt> within 1 %, KS on the
+    escape spectrum."""
+    n = 3000
+    wl = synth.sphere(tau0=1e4, T=1e4, tau_dust=tau_dust, n_packets=n)
     ctx = context(wl)
     g, st = gpu_run(ctx, wl.packets, device=True)
-    r, tal = oracle_run(wl)
-    for s in (oracle.ESCAPED, oracle.ABSORBED):
-        assert abs((g["status"] == s).mean() - (r["status"] == s).mean()) < 4 * math.sqrt(0.25 / n) + 1e-9
-    assert st["escaped"] + st["absorbed"] + st["capped"] == n
+    r, tal = oracle_run(wl, threads=16)
+    for s_ in (oracle.ESCAPED, oracle.ABSORBED):
+        assert abs((g["status"] == s_).mean() - (r["status"] == s_).mean()) < 4 * math.sqrt(0.25 / n) + 1e-9
+    assert st["escaped"] + st["absorbed"] + st["capped"] == n and st["errors"] == 0
     same = (g["nscatt"] == r["nscatt"]).mean()
     mg, mr = g["nscatt"].mean(), r["nscatt"].mean()
-    print("sphere tau_d=%g: identical %.4f <N> %.1f vs %.1f" % (tau_dust, same, mg, mr))
-    assert abs(mg / mr - 1) < 0.01 or same > 0.9
+    print("sphere tau_d=%g: identical %.4f <N> %.2f vs %.2f" % (tau_dust, same, mg, mr))
+    assert abs(mg / mr - 1) < 0.01
     esc_g, esc_r = g["status"] == 1, r["status"] == 1
-    if esc_g.sum() > 20:
-        assert _ks(_x(wl, g["nu"][esc_g]), _x(wl, r["nu"][esc_r])) > 0.01
+    assert _ks(_x(wl, g["nu"][esc_g]), _x(wl, r["nu"][esc_r])) > 0.01
 
 
-def test_expanding_sphere_peeling_matches_oracle():
-    """Expanding sphere with dust, recoil and core/wing phase functions,
-    peeled into 3 directions (spectra, images, cubes).  Peeled totals are
-    Monte Carlo estimates: the oracle runs the packets in 8 groups of 100, and
-    the GPU total must lie within 4 sigma of the oracle's (sigma from the
-    spread of the group totals, x sqrt(2) for the difference of two
-    estimates)."""
-    n, groups = 800, 8
-    wl = synth.expanding_sphere(N_HI=1e19, n_packets=n, npix=16, nchan=40)
+def _box_sum(a, axes):
+    """Sum of a over the neighbours (offsets -1, 0, +1) along the given axes."""
+    out = a.copy()
+    for ax in axes:
+        pad = [(0, 0)] * a.ndim
+        pad[ax] = (1, 1)
+        b = np.pad(out, pad)
+        sl = lambda o: tuple(slice(o, o + a.shape[ax]) if k == ax else slice(None) for k in range(a.ndim))
+        out = b[sl(0)] + b[sl(1)] + b[sl(2)]
+    return out
+
+
+def _per_bin(gpu, ora, edge, axes, what, rtol=3e-4):
+    """Bin-by-bin agreement of FP32 GPU tallies with the FP64 oracle: relative
+    rtol (FP32 weights, exp(-tau) of FP32-pair optical depths, FP32 atomics)
+    plus 1e-6 of the largest bin, plus, next to a bin edge, the oracle's own
+    total of the events lying within rounding of that edge (FP32 frequencies
+    may bin them next door)."""
+    ora = np.asarray(ora, dtype=np.float64)
+    gpu = np.asarray(gpu, dtype=np.float64)
+    allow = _box_sum(np.asarray(edge, dtype=np.float64), axes)
+    tol = rtol * np.abs(ora) + 1e-6 * np.abs(ora).max() + allow
+    err = np.abs(gpu - ora)
+    bad = err > tol
+    assert ora.max() > 0, what   # the comparison has flux to compare
+    print("%s: %d bins, max |g-o|/o %.2e, edge allowance in %d bins" % (
+        what, ora.size, (err / (np.abs(ora) + 1e-300))[ora > 1e-3 * ora.max()].max(), int((allow > 0).sum())))
+    assert not bad.any(), (what, int(bad.sum()), err[bad][:4], ora[bad][:4], tol[bad][:4])
+
+
+def _peel_per_bin(wl, n_max=None, cap=3000):
+    """Peeled spectra, images and cubes of the GPU against the oracle's
+    deposit of the same peeling record, bin by bin (the record rebuilt by the
+    oracle from the GPU's trace, each event replayed from the GPU's state)."""
     ctx = context(wl)
-    g, st = gpu_run(ctx, wl.packets)
     o = oracle.Oracle(wl)
-    m = n // groups
-    parts = [o.run(lo=k * m, hi=(k + 1) * m, threads=8) for k in range(groups)]
-    r = {k: np.concatenate([p[0][k] for p in parts]) for k in ("nscatt", "status")}
-    tal = {k: sum(p[1][k] for p in parts) for k in ("pspec", "pimg", "pcube")}
-    same = (g["nscatt"] == r["nscatt"]).mean()
-    print("expanding: identical %.4f <N> %.1f vs %.1f" % (same, g["nscatt"].mean(), r["nscatt"].mean()))
-    ps = ctx.get_tally(1)
-    pi = ctx.get_tally(2)
-    pc = ctx.get_tally(3)
-    for d in range(3):
-        a, b = float(ps[d].sum()), float(tal["pspec"][d].sum())
-        sig = np.std([p[1]["pspec"][d].sum() for p in parts], ddof=1) * math.sqrt(groups)
-        print("direction %d: peeled %.4g vs %.4g (sigma %.3g)" % (d, a, b, sig))
-        assert abs(a - b) <= 4 * math.sqrt(2) * sig + 1e-3 * b, (d, a, b, sig)
-    assert np.allclose(pc.sum(-1), pi, rtol=1e-4, atol=1e-9) or pc.sum() <= pi.sum() * (1 + 1e-5)
-    if same > 0.95:
-        assert np.allclose(ps, tal["pspec"], rtol=2e-3, atol=1e-6 * ps.max())
+    pk = wl.packets
+    chosen, events = rebuild_peel_events(ctx, o, pk, cap)
+    assert len(chosen) > 0.8 * pk.n, len(chosen)
+    sub = synth.Packets(pk.pos[chosen], pk.dir[chosen], pk.nu[chosen], pk.ids[chosen])
+    ctx.zero_tallies()
+    st = ctx.propagate(sub.pos, sub.dir, sub.nu, sub.ids, out={})
+    assert st["npeel_rays"] == events.size, (st["npeel_rays"], events.size)
+    ref = o.peel_from_events(events)
+    near = near_edge_events(o, events)
+    edge = o.peel_from_events(events[near])
+    print("peeling record: %d packets, %d events, %d near a bin edge" % (len(chosen), events.size, near.sum()))
+    ps, pi = ctx.get_tally(1), ctx.get_tally(2)
+    _per_bin(ps, ref["pspec"], edge["pspec"], (1,), "spectra")
+    _per_bin(pi, ref["pimg"], edge["pimg"], (1, 2), "images")
+    if wl.detector.cube:
+        pc = ctx.get_tally(3)
+        _per_bin(pc, ref["pcube"], edge["pcube"], (1, 2, 3), "cubes")
+        # every cube voxel is also in its image pixel: the spectral sum of the
+        # cube never exceeds the image (equal where all channels are on the axis)
+        assert (pc.astype(np.float64).sum(-1) <= pi * (1 + 1e-5) + 1e-12 * pi.max()).all()
+    return ctx
+
+
+def test_peeling_per_bin_matches_oracle():
+    """Expanding sphere with dust, recoil and core/wing phase functions
+    (config 3 at a lower column), peeled into 3 directions: spectra, images
+    and cubes bin by bin against the oracle's deposit of the same record.
+    The GPU stops rays at tau > 50, the oracle does not."""
+    wl = synth.expanding_sphere(N_HI=3e17, tau_dust=0.3, n_packets=200, npix=8, nchan=24, base=3, max_level=5)
+    _peel_per_bin(wl)
+
+
+def test_peeling_uncoupled_chi_square():
+    """Independent GPU and oracle runs (different packet ids, so different
+    random streams) of 1e4 packets each: peeled spectra and images agree by a
+    chi-square test (p > 0.01) on batch means of 20 groups of 500 packets,
+    and the escape spectra by KS."""
+    from scipy import stats
+    n, K = 10_000, 20
+    wl = synth.expanding_sphere(N_HI=1e17, tau_dust=0.3, n_packets=n, npix=8, nchan=24, base=3, max_level=5)
+    ctx = context(wl)
+    o = oracle.Oracle(wl)
+    pk = wl.packets
+    other = synth.Packets(pk.pos, pk.dir, pk.nu, pk.ids + np.uint64(1 << 40))
+    m = n // K
+    g_sp, g_im, o_sp, o_im, g_nu, o_nu = [], [], [], [], [], []
+    for k in range(K):
+        sl = slice(k * m, (k + 1) * m)
+        ctx.zero_tallies()
+        out = {"status": np.zeros(m, np.int32), "nu": np.zeros(m)}
+        ctx.propagate(other.pos[sl], other.dir[sl], other.nu[sl], other.ids[sl], out=out)
+        g_sp.append(ctx.get_tally(1).astype(np.float64))
+        g_im.append(ctx.get_tally(2).astype(np.float64))
+        g_nu.append(out["nu"][out["status"] == 1])
+        r, t = o.run(lo=k * m, hi=(k + 1) * m, threads=16)
+        o_sp.append(t["pspec"])
+        o_im.append(t["pimg"])
+        o_nu.append(r["nu"][r["status"] == 1])
+
+    def chi2_p(ga, oa, what):
+        ga, oa = np.array(ga).reshape(K, -1), np.array(oa).reshape(K, -1)
+        mg, mo = ga.mean(0), oa.mean(0)
+        keep = (mg + mo) > 2e-3 * (mg + mo).max()
+        se = np.sqrt(ga.var(0, ddof=1) / K + oa.var(0, ddof=1) / K)[keep]
+        t = (mg[keep] - mo[keep]) / se
+        # each t is Student-t with 2K-2 degrees of freedom: map to chi2(1)
+        q = stats.chi2.isf(2 * stats.t.sf(np.abs(t), 2 * K - 2), 1)
+        p = stats.chi2.sf(q.sum(), keep.sum())
+        print("%s: %d bins, chi2 %.1f, p %.3f" % (what, keep.sum(), q.sum(), p))
+        return p
+
+    assert chi2_p(g_sp, o_sp, "peeled spectra") > 0.01
+    assert chi2_p([a.reshape(3, 4, 2, 4, 2).sum((2, 4)) for a in g_im],
+                  [a.reshape(3, 4, 2, 4, 2).sum((2, 4)) for a in o_im], "peeled images (2x2 rebinned)") > 0.01
+    gx, ox = np.concatenate(g_nu), np.concatenate(o_nu)
+    assert _ks(gx, ox) > 0.01
 
 
 def test_conservation_and_edge_cases():
@@ -322,10 +372,21 @@ def test_galaxy_run_matches_oracle():
     assert st["errors"] == 0
     # packets are born in the densest leaves: the peeled flux may vanish
     # (every peeling ray beyond tau = 50); both sides must agree either way
-    ps = ctx.get_tally(1)
-    a, b = float(ps.sum()), float(tal["pspec"].sum())
-    assert abs(a - b) <= 0.05 * max(a, b) + 1e-30, (a, b)
     assert st["npeel_rays"] == tal["npeel"]
+
+
+def test_galaxy_peeling_per_bin_matches_oracle():
+    """Synthetic galaxy with every density x 1e-12 (the rays of the sources
+    cross many leaves before tau = 50), 3 lines, dust, turbulence, 4
+    directions, packets capped at 64 scatterings: peeled tallies bin by bin
+    against the oracle's deposit of the GPU's own record."""
+    wl = synth.galaxy(n_leaf=150_000, grid_level=6, base_level=4, max_level=10, n_packets=150, npix=16,
+                      nchan=40)
+    m = wl.medium
+    for f in ("n_HI", "n_dust", "n_metal"):
+        setattr(m, f, (np.asarray(getattr(m, f), np.float32) * np.float32(1e-12)).astype(np.float32))
+    wl.physics.max_scatt = 64
+    _peel_per_bin(wl, cap=80)
 
 
 def test_shell_run_matches_oracle():

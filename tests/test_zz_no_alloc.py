@@ -2,10 +2,12 @@
 not allocate device memory while they run (for example an application whose
 framework owns all free HBM in its own pool, or a latency-critical loop where
 a cudaMalloc could synchronise the device).  Its scratch lives in a static
-device array, so the check here is that it returns exactly what the ordinary
-rascas_propagate returns on the same packets, on two calls in a row (the second
-call must not see the first call's counters or queue head), and that it
-rejects a packet count beyond RASCAS_NOALLOC_MAX_PACKETS.
+device array whose address rascas_create looks up, so the checks here are
+that it returns exactly what the ordinary rascas_propagate returns on the same
+packets, on two calls in a row (the second call must not see the first call's
+counters or queue head), that a call takes no device memory (the free bytes
+the driver reports do not change across it), and that it rejects a packet
+count beyond RASCAS_NOALLOC_MAX_PACKETS.
 
 This file is collected last on purpose."""
 import ctypes as C
@@ -26,6 +28,7 @@ def _outputs(n):
 
 
 def test_propagate_noalloc_matches_propagate():
+    import torch
     import paper_2001_11252_gb300 as rg
     from paper_2001_11252_gb300 import _native as N
 
@@ -46,8 +49,11 @@ def test_propagate_noalloc_matches_propagate():
         pin = N.PacketsIn(pos.ctypes.data, dr.ctypes.data, nu.ctypes.data, ids.ctypes.data)
         pout = N.PacketsOut(*[got[k].ctypes.data for k in ("status", "nscatt", "nu", "pos", "dir", "path")])
         st = N.Stats()
+        free0 = torch.cuda.mem_get_info(0)[0]
         r = f(ctx._h, C.byref(pin), n, C.byref(pout), C.byref(st))
+        free1 = torch.cuda.mem_get_info(0)[0]
         assert r == 0, L.rascas_last_error(ctx._h)
+        assert free1 == free0, (call, free0, free1)
         for k in ref:
             assert np.array_equal(ref[k], got[k]), (call, k)
         assert st.packets == n == st_ref["packets"]
