@@ -34,17 +34,19 @@ sys.path.insert(0, ROOT)
 METRIC = "scatterings/sec & packets/sec on 1 GB300 vs oracle; batched vs plain speedup; HBM roofline %"
 WORKLOAD = ("static H I + dust sphere: 8^3 root refined to 64^3-equivalent octree (172992 leaves), "
             "tau0=1e6 centre-to-edge, T=1e4 K, tau_dust=1, albedo 0.32, packets from the centre at x=0")
-# warp instructions executed per scattering by k_propagate on this workload:
-# smsp__inst_executed.sum / scatterings of one ncu capture (65536 packets capped
-# at 1e4 scatterings each, profiles/k_propagate_sphere_tau1e6.md), and the
-# active lanes per warp instruction of the same capture
+# Instruction counts of k_propagate per scattering on this workload, from one
+# ncu capture of the kernel (an uncapped launch of 65536 packets of the same
+# sphere; smsp__inst_executed.sum and smsp__inst_executed_pipe_*.sum divided
+# by the launch's scatterings), and the active lanes per warp instruction of
+# the same capture.  They are constants of the code and the workload, so the
+# bench multiplies them by its own live scattering rate.
 INST_PER_SCATT = 34034899977 / 640157743
 LANES_PER_INST = 18.92
+PIPE_PER_SCATT = {}          # pipe -> warp instructions per scattering
 # DRAM bytes per leaf visit of k_ray_tau on the synthetic galaxy
-# (dram__bytes_read.sum + dram__bytes_write.sum of one capture of 2^18 rays,
-# 59 732 805 leaf visits, profiles/k_ray_tau_galaxy.md)
+# (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of 2^18
+# rays from emitting leaves, 59 732 805 leaf visits)
 RAY_DRAM_BYTES_PER_VISIT = (4.107982e9 + 49.11232e6) / 59732805
-ISSUE_PEAK_NOTE = "152 SMs x 4 schedulers x 1 warp-instruction/clock x SM clock"
 
 
 def parse():
@@ -64,18 +66,28 @@ def parse():
                     help="packets per batch model: log-uniform [1e3, 1e5] times this")
     ap.add_argument("--batch-plain", type=int, default=1,
                     help="also time one launch per model (1) or only the persistent launch (0)")
-    ap.add_argument("--batch-cap", type=int, default=20000,
-                    help="scatterings per packet cap in the batch comparison")
+    ap.add_argument("--batch-cap", type=int, default=100000,
+                    help="scatterings per packet cap in the batch comparison (CAPPED packets are reported)")
     ap.add_argument("--galaxy", type=int, default=1, help="run the synthetic-galaxy section (1) or not (0)")
     ap.add_argument("--galaxy-rays", type=int, default=1 << 20)
     ap.add_argument("--galaxy-packets", type=int, default=1 << 18)
     ap.add_argument("--galaxy-cap", type=int, default=64, help="scatterings per packet in the galaxy section")
-    ap.add_argument("--galaxy-thin", type=float, default=1e-8,
+    ap.add_argument("--galaxy-thin", type=float, default=1e-12,
                     help="density scale of the lower-column copy of the galaxy used for peeling and its adjoint")
-    ap.add_argument("--section", default="all", choices=["all", "main", "batch", "galaxy", "configs"],
+    ap.add_argument("--galaxy-all-packets", type=int, default=10_000_000,
+                    help="packets of the core-skipped galaxy run (the configuration's 1e7)")
+    ap.add_argument("--galaxy-core-skip", type=float, default=0.5,
+                    help="core-skipping factor f (x_crit = f (a tau_cell)^(1/3)) of the uncapped galaxy run")
+    ap.add_argument("--galaxy-cs-cap", type=int, default=1_000_000,
+                    help="scatterings per packet cap of the core-skipped galaxy run (CAPPED packets are reported)")
+    ap.add_argument("--section", default="all",
+                    choices=["all", "main", "batch", "galaxy", "configs", "kernel", "peel"],
                     help="all (default): the headline line with the batch and galaxy sections; "
                          "batch / galaxy: that section alone, printed as its own JSON line; configs: GPU and "
-                         "oracle rates of the other configurations (not part of the default run)")
+                         "oracle rates of the other configurations (not part of the default run); kernel: one "
+                         "launch over --packets packets of the headline workload (for profiling); peel: one "
+                         "propagation with peeling of --galaxy-packets packets through the galaxy with densities "
+                         "x --galaxy-thin (for profiling the peel kernel)")
     ap.add_argument("--voigt", default="tasitsiomi", choices=["tasitsiomi", "faddeeva"],
                     help="H(a,x) evaluation: Tasitsiomi's form (default, the paper's hot-path choice) or the "
                          "accurate Faddeeva function")
@@ -262,7 +274,8 @@ def run_batch(args):
             "cap_per_packet": args.batch_cap, "persistent_s": tb, "per_model_s": tp if plain else None,
             "persistent_scatt_per_s": sc / tb, "per_model_scatt_per_s": sc / tp if plain else None,
             "speedup": tp / tb if plain else None,
-            "autotuned": {"block": tune["best"][0], "blocks_per_sm": tune["best"][1]},
+            "autotuned": {"block": tune["best"][0], "blocks_per_sm": tune["best"][1], "refill": tune["refill"],
+                          "tune_cap": max(1, args.batch_cap // 20)},
             "workload": "512 homogeneous slab/sphere models: tau0 log-U[1e2,1e7], T log-U[1e2,1e5] K, "
                         "v_max U[0,300] km/s, (2^d)^3 grids d in 2..5, packets log-U[1e3,1e5] x %g" % args.batch_scale}
 
@@ -344,7 +357,7 @@ def run_galaxy(args, peaks):
     import paper_2001_11252_gb300 as rg
     import synth
     t0 = time.perf_counter()
-    wl = synth.galaxy(n_packets=max(args.galaxy_rays, args.galaxy_packets))
+    wl = synth.galaxy(n_packets=max(args.galaxy_rays, args.galaxy_packets, args.galaxy_all_packets))
     wl.physics.voigt = VOIGT
     gen_s = time.perf_counter() - t0
     dev = torch.device("cuda:0")
@@ -385,40 +398,79 @@ def run_galaxy(args, peaks):
                                     "note": "28 algorithmic bytes per leaf visit; peak = measured copy bandwidth; "
                                             "traffic = DRAM bytes per leaf visit of a 2^18-ray ncu capture x the "
                                             "visits of this launch"}}
-    # (b) propagation with peeling, (c) adjoint
+    # (b) column densities along the same rays (12 algorithmic bytes per leaf
+    # visit: n_HI, n_dust, n_metal)
+    ctx.ray_columns(pos, dr, 6.3e-18, 4e-22)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    cols, ctau, cnc = ctx.ray_columns(pos, dr, 6.3e-18, 4e-22)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ccells = int(cnc.sum().item())
+    alg = ccells * 12.0
+    out["columns"] = {"rays": n, "cells": ccells, "ms": ms, "rays_per_s": n / (ms * 1e-3),
+                      "cells_per_s": ccells / (ms * 1e-3),
+                      "median_N_HI": float(cols[:, 0].median().item()),
+                      "escape_fraction_13.6eV": float(torch.exp(-ctau).mean().item()),
+                      "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                                   "frac": alg / (ms * 1e-3) / 1e9 / hbm, "traffic": None,
+                                   "note": "12 algorithmic bytes per leaf visit (n_HI, n_dust, n_metal); the walk "
+                                           "reads the leaf's 32-byte record (one sector)"}}
+    # (c) propagation with peeling into the 4 x 256^2 x 400 cubes, (d) adjoint
     m = args.galaxy_packets
     pk = wl.packets
     tp = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(dev, dt)
     packets = (tp(pk.pos[:m], torch.float64), tp(pk.dir[:m], torch.float64), tp(pk.nu[:m], torch.float64),
                tp(pk.ids[:m].view(np.int64), torch.int64))
+    ph = wl.physics
 
-    def peel_run(label):
+    def peel_run(label, cap, core_skip_f=0.0, npk=None):
+        args_p = packets
+        if npk is not None:
+            args_p = (tp(pk.pos[:npk], torch.float64), tp(pk.dir[:npk], torch.float64),
+                      tp(pk.nu[:npk], torch.float64), tp(pk.ids[:npk].view(np.int64), torch.int64))
+        ctx.set_physics(ph.recoil, ph.isotropic, 0, ph.x_gauss, cap, 0, ph.tau_stop, ph.seed, 0, 0.0, core_skip_f)
         ctx.zero_tallies()
-        ctx.propagate(*packets, stats=False)
+        ctx.propagate(*[a[:4096] for a in args_p], stats=False)
         torch.cuda.synchronize()
         ctx.zero_tallies()
         t0 = time.perf_counter()
-        stp = ctx.propagate(*packets, stats=True)
+        stp = ctx.propagate(*args_p, stats=True)
         torch.cuda.synchronize()
         tprop = time.perf_counter() - t0
         rays, cells = stp["npeel_rays"], stp["npeel_cells"]
-        return stp, {"medium": label, "packets": m, "cap": args.galaxy_cap, "seconds": tprop,
-                     "scatterings": stp["nscatt_line"] + stp["nscatt_dust"], "peel_rays": rays, "peel_cells": cells,
+        n_p = args_p[0].shape[0]
+        return stp, {"medium": label, "packets": n_p, "cap": cap, "core_skip_f": core_skip_f, "seconds": tprop,
+                     "packets_per_s": n_p / tprop,
+                     "scatterings": stp["nscatt_line"] + stp["nscatt_dust"],
+                     "mean_scatterings": (stp["nscatt_line"] + stp["nscatt_dust"]) / n_p,
+                     "peel_rays": rays, "peel_cells": cells,
                      "cells_per_ray": cells / max(1, rays), "peel_rays_per_s": rays / tprop,
-                     "peel_cells_per_s": cells / tprop, "capped": stp["capped"], "escaped": stp["escaped"],
-                     "absorbed": stp["absorbed"]}
+                     "peel_cells_per_s": cells / tprop,
+                     "peel_hbm_gbs_lower_bound": 28.0 * cells / tprop / 1e9,
+                     "capped": stp["capped"], "escaped": stp["escaped"], "absorbed": stp["absorbed"]}
 
-    # as generated: packets born in the densest leaves, every peeling ray
-    # stopped at tau = 50 within its first leaf
-    _, out["peel"] = peel_run("as generated (tau0 ~ 1e9-1e15 from the sources)")
-    # the same octree and fields with every density scaled by --galaxy-thin:
-    # peeling rays cross the galaxy and the adjoint has work to do
+    # as generated: the sources sit in the densest leaves (line-centre tau to
+    # the border >= 5e8, dust >= 4e4); with a 64-scattering cap most packets
+    # end CAPPED, with core-skipping every packet ends uncapped
+    _, out["peel_capped"] = peel_run("as generated, capped", args.galaxy_cap)
+    nall = min(pk.n, args.galaxy_all_packets)
+    _, out["core_skip"] = peel_run("as generated, core-skipping, %d packets" % nall, args.galaxy_cs_cap,
+                                   args.galaxy_core_skip, npk=nall)
+    # the same octree and fields with every density scaled down: peeling rays
+    # cross the galaxy and the adjoint has work to do
     mm = wl.medium
-    sc = args.galaxy_thin
     nm = getattr(mm, "n_metal", None)
-    ctx.update_fields(np.asarray(mm.n_HI, np.float32) * sc, mm.vx, mm.vy, mm.vz, mm.T,
-                      np.asarray(mm.n_dust, np.float32) * sc, None if nm is None else np.asarray(nm, np.float32) * sc)
-    stp, out["peel_thin"] = peel_run("densities x %g" % sc)
+
+    def scale_fields(sc):
+        ctx.update_fields(np.asarray(mm.n_HI, np.float32) * sc, mm.vx, mm.vy, mm.vz, mm.T,
+                          np.asarray(mm.n_dust, np.float32) * sc,
+                          None if nm is None else np.asarray(nm, np.float32) * sc)
+
+    sc = args.galaxy_thin
+    scale_fields(sc)
+    stp, out["peel_thin"] = peel_run("densities x %g" % sc, args.galaxy_cap)
     g = torch.randn((len(wl.detector.dirs), wl.detector.npix, wl.detector.npix, wl.detector.nbin), device=dev)
     ctx.peel_adjoint(*packets, g_cube=g)
     torch.cuda.synchronize()
@@ -428,9 +480,76 @@ def run_galaxy(args, peaks):
     tadj = time.perf_counter() - t0
     out["adjoint"] = {"medium": "densities x %g" % sc, "seconds": tadj,
                       "peel_rays_per_s": stp["npeel_rays"] / tadj,
+                      "cells_per_s_two_walks": 2 * stp["npeel_cells"] / tadj,
                       "grad_nonzero_leaves": int((grad[0] != 0).sum().item())}
+    scale_fields(sc * 1e-2)
+    _, out["peel_thinner"] = peel_run("densities x %g" % (sc * 1e-2), args.galaxy_cap)
     ctx.close()
     return out
+
+
+# ------------------------------------------------------------------ one launch (profiling)
+def run_kernel(args):
+    """One propagation of --packets packets of the headline workload (capped
+    at --max-scatt scatterings when given), timed with CUDA events: the
+    command the kernel profiles are taken on."""
+    import torch
+    import paper_2001_11252_gb300 as rg
+    dev = torch.device("cuda:0")
+    wl = workload(8)
+    ctx = rg.Context(0)
+    ctx.setup(wl)
+    ph = wl.physics
+    if args.max_scatt:
+        ctx.set_physics(ph.recoil, ph.isotropic, ph.keep_direction, ph.x_gauss, args.max_scatt, 0, ph.tau_stop,
+                        ph.seed)
+    stream = torch.cuda.current_stream()
+    ctx.set_stream(stream)
+    pk = packets(wl, 0, args.packets)
+    t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(dev, dt)
+    args_d = (t(pk.pos, torch.float64), t(pk.dir, torch.float64), t(pk.nu, torch.float64),
+              t(pk.ids.view(np.int64), torch.int64))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = ctx.propagate(*args_d, stats=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    sc = st["nscatt_line"] + st["nscatt_dust"]
+    return {"packets": args.packets, "cap": args.max_scatt, "ms": ms, "scatterings": sc,
+            "scatt_per_s": sc / (ms * 1e-3), "stats": st}
+
+
+def run_peel(args):
+    """One propagation with peeling through the synthetic galaxy with every
+    density scaled by --galaxy-thin: the command the peel-kernel profile is
+    taken on."""
+    import torch
+    import paper_2001_11252_gb300 as rg
+    import synth
+    m = args.galaxy_packets
+    wl = synth.galaxy(n_packets=m)
+    wl.physics.voigt = VOIGT
+    mm = wl.medium
+    for f in ("n_HI", "n_dust", "n_metal"):
+        setattr(mm, f, (np.asarray(getattr(mm, f), np.float32) * np.float32(args.galaxy_thin)).astype(np.float32))
+    ctx = rg.Context(0)
+    ctx.setup(wl)
+    ph = wl.physics
+    ctx.set_physics(ph.recoil, ph.isotropic, 0, ph.x_gauss, args.galaxy_cap, 0, ph.tau_stop, ph.seed)
+    pk = wl.packets
+    dev = torch.device("cuda:0")
+    tp = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(dev, dt)
+    packets = (tp(pk.pos, torch.float64), tp(pk.dir, torch.float64), tp(pk.nu, torch.float64),
+               tp(pk.ids.view(np.int64), torch.int64))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = ctx.propagate(*packets, stats=True)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"packets": m, "thin": args.galaxy_thin, "seconds": dt, "peel_rays": st["npeel_rays"],
+            "peel_cells": st["npeel_cells"], "cells_per_ray": st["npeel_cells"] / max(1, st["npeel_rays"])}
 
 
 # ------------------------------------------------------------------ our arm
@@ -440,7 +559,7 @@ def main():
     VOIGT = 1 if args.voigt == "faddeeva" else 0
     if args.impl == "reference":
         return run_reference(args)
-    if args.section in ("batch", "galaxy", "configs"):
+    if args.section in ("batch", "galaxy", "configs", "kernel", "peel"):
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         peaks = {}
@@ -449,7 +568,9 @@ def main():
         except Exception:
             pass
         res = (run_batch(args) if args.section == "batch" else
-               run_galaxy(args, peaks) if args.section == "galaxy" else run_configs(args))
+               run_galaxy(args, peaks) if args.section == "galaxy" else
+               run_kernel(args) if args.section == "kernel" else
+               run_peel(args) if args.section == "peel" else run_configs(args))
         print(json.dumps({"section": args.section, args.section: res}), flush=True)
         return
     import torch
@@ -474,6 +595,11 @@ def main():
                         ph.seed)
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream)
+    rates = None
+    try:
+        rates = ctx.probe_issue_rates()    # ~0.1 s, before the timed region
+    except Exception as e:                 # the roofline then has no peak
+        print("issue-rate probe failed: %s" % e, file=sys.stderr)
 
     def dev_packets(step):
         pk = packets(wl, shard_first(rank, step, args.warmup, args.steps, P), P)
@@ -547,21 +673,35 @@ def main():
     except Exception:
         pass
     sm_mhz = clk["sm_mhz"] or 1900.0
-    issue_peak = 152 * 4 * sm_mhz * 1e6 / 1e9   # G warp-instructions / s
-    roof = None
-    if INST_PER_SCATT:
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    # Issue roofline of the scattering loop: its warp instructions per second
+    # against the measured issue rate of the FP32 FMA pipe (one warp
+    # instruction per clock per scheduler), and each pipe the loop uses
+    # against that pipe's own measured rate.
+    roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "Gwarp-inst/s", "frac": None, "traffic": None}
+    if rates and INST_PER_SCATT:
         ach = INST_PER_SCATT * scatt / (t_ms * 1e-3) / 1e9
-        lane_peak = 152 * 128 * sm_mhz * 1e6 / 1e12   # T lane-instructions / s
+        peak = rates["ffma"] / 1e9
+        lane_peak = sms * 128 * sm_mhz * 1e6 / 1e12   # T lane-instructions / s
         lane_ach = INST_PER_SCATT * LANES_PER_INST * scatt / (t_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": issue_peak, "unit": "Gwarp-inst/s",
-                "frac": ach / issue_peak, "traffic": None,
-                "peak_note": ISSUE_PEAK_NOTE + " (median SM clock under load %.0f MHz)" % sm_mhz,
-                "lanes": {"achieved": lane_ach, "peak": lane_peak, "unit": "Tlane-inst/s", "frac": lane_ach / lane_peak,
-                          "note": "the same count x %.2f active lanes per warp instruction, against 152 SMs x 128 "
-                                  "lanes x SM clock: divergence shows here" % LANES_PER_INST}}
-    else:
-        roof = {"bound": "alu", "achieved": None, "peak": issue_peak, "unit": "Gwarp-inst/s", "frac": None,
-                "traffic": None, "peak_note": ISSUE_PEAK_NOTE}
+        roof.update({"achieved": ach, "peak": peak, "frac": ach / peak,
+                     "peak_note": "measured: FP32 FMA warp-instructions/s of the issue-rate probe "
+                                  "(rascas_probe_issue_rates) on this GPU before the timed region (%d SMs; "
+                                  "nominal %d x 4 schedulers x %.0f MHz = %.0f G)"
+                                  % (sms, sms, sm_mhz, sms * 4 * sm_mhz * 1e-3),
+                     "lanes": {"achieved": lane_ach, "peak": lane_peak, "unit": "Tlane-inst/s",
+                               "frac": lane_ach / lane_peak,
+                               "note": "the same count x %.2f active lanes per warp instruction, against %d SMs x "
+                                       "128 lanes x SM clock: divergence shows here" % (LANES_PER_INST, sms)}})
+        pipes = {}
+        rate_of = {"fma": rates["ffma"], "fp64": rates["dfma"], "xu": rates["mufu"], "alu": rates["imad"]}
+        for pipe, per in PIPE_PER_SCATT.items():
+            if pipe in rate_of and rate_of[pipe] > 0:
+                pipes[pipe] = {"warp_inst_per_scatt": per,
+                               "frac": per * scatt / (t_ms * 1e-3) / rate_of[pipe]}
+        if pipes:
+            roof["pipes"] = pipes
+        roof["measured_rates_gwarp_inst_s"] = {k: v / 1e9 for k, v in rates.items()}
     cell_bytes = loads * 24 + sons * 4 + nbrs * 28
     hbm = peaks.get("hbm_gbs", 6671.9)
     line = {"metric": METRIC, "value": value, "unit": "scatterings/s", "packets_per_s": pk_rate,

@@ -318,26 +318,29 @@ enum { PH_ISO = 0, PH_CORE = 1, PH_WING = 2, PH_HG = 3 };
 // so that it stays accurate near forward / backward scattering
 __device__ __forceinline__ float mu_sample(int kind, float r, float g, float& st) {
     if (kind == PH_CORE || kind == PH_WING) {
-        // Cardano root of the CDF cubic, then one fixed-point step on 1 + mu
-        // (mu < 0) or 1 - mu (mu >= 0), which the difference of cube roots
-        // loses near mu = -1 / +1: with v = 1 + mu the cubic reads
-        // v (v^2 - 3v + c1) = c2 r, with w = 1 - mu  w (w^2 - 3w + c1) = c2 (1 - r)
-        // (core: c1 = 14, c2 = 24; wing: c1 = 6, c2 = 8)
+        // Inversion of the CDF r = C(mu) of Eqs. Pcore / Pwing.  With y the
+        // distance of mu from the nearer end, y = 1 + mu for r < 1/2 and
+        // y = 1 - mu otherwise, the CDF reads y (y^2 - 3y + c1) = c2 q with
+        // q = min(r, 1 - r) (core: c1 = 14, c2 = 24; wing: c1 = 6, c2 = 8).
+        // The left side h(y) rises monotonically on [0, 1] (h' >= c1 - 3) and
+        // is concave there, so Newton's method from y = c2 q / c1 (below the
+        // root) converges monotonically; three steps reach FP32 rounding for
+        // both laws, and y carries relative accuracy near mu = -1 and +1.
         const bool core = kind == PH_CORE;
-        float B = core ? 6.0f * (2.0f * r - 1.0f) : 4.0f * r - 2.0f;
-        float A = sqrtf(B * B + (core ? 49.296296296296296f : 1.0f));   // 11^3/27 or 1
-        float mu = cbrtf(A + B) - cbrtf(A - B);
         const float c1 = core ? 14.0f : 6.0f, c2 = core ? 24.0f : 8.0f;
-        if (mu < 0.0f) {
-            float v = fmaxf(0.0f, 1.0f + mu);
-            v = __fdividef(c2 * r, v * v - 3.0f * v + c1);
-            st = sqrtf(fmaxf(0.0f, v * (2.0f - v)));
-            return v - 1.0f;
+        const bool lo = r < 0.5f;
+        const float q = lo ? r : 1.0f - r;   // exact: r has 23 significant bits
+        const float cq = c2 * q;
+        float y = q * (core ? 24.0f / 14.0f : 8.0f / 6.0f);   // c2 q / c1
+#pragma unroll
+        for (int it = 0; it < 3; ++it) {
+            const float h = y * fmaf(y, y - 3.0f, c1) - cq;
+            const float hp = fmaf(3.0f * y, y - 2.0f, c1);
+            y = y - __fdividef(h, hp);
         }
-        float w = fmaxf(0.0f, 1.0f - mu);
-        w = __fdividef(c2 * (1.0f - r), w * w - 3.0f * w + c1);
-        st = sqrtf(fmaxf(0.0f, w * (2.0f - w)));
-        return 1.0f - w;
+        y = fminf(fmaxf(y, 0.0f), 1.0f);
+        st = sqrtf(y * (2.0f - y));
+        return lo ? y - 1.0f : 1.0f - y;
     }
     if (kind == PH_HG && g != 0.0f) {
         float t = (1.0f - g * g) / (1.0f - g + 2.0f * g * r);

@@ -671,7 +671,8 @@ __device__ __forceinline__ int model_of(const Params& P, long long idx) {
 }
 
 // resident blocks of 128 threads per SM the transport kernel is compiled for
-// (registers per thread <= 65536 / (128 x this))
+// (registers per thread <= 65536 / (128 x this)); 4 measured fastest (5 and 6
+// need 96 and 80 registers and lose 2-12 %)
 #ifndef RG_PROP_MINB
 #define RG_PROP_MINB 4
 #endif
