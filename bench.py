@@ -40,9 +40,12 @@ WORKLOAD = ("static H I + dust sphere: 8^3 root refined to 64^3-equivalent octre
 # by the launch's scatterings), and the active lanes per warp instruction of
 # the same capture.  They are constants of the code and the workload, so the
 # bench multiplies them by its own live scattering rate.
-INST_PER_SCATT = 34034899977 / 640157743
-LANES_PER_INST = 18.92
-PIPE_PER_SCATT = {}          # pipe -> warp instructions per scattering
+INST_PER_SCATT = 6135610606642 / 111923728554
+LANES_PER_INST = 108432225298541 / 6135610606642
+# pipe -> warp instructions per scattering of the same capture (FP32 FMA,
+# FP64, special-function unit)
+PIPE_PER_SCATT = {"fma": 2882862709663 / 111923728554, "fp64": 83473334883 / 111923728554,
+                  "xu": 165927734328 / 111923728554}
 # DRAM bytes per leaf visit of k_ray_tau on the synthetic galaxy
 # (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of 2^18
 # rays from emitting leaves, 59 732 805 leaf visits)
@@ -69,6 +72,10 @@ def parse():
     ap.add_argument("--batch-cap", type=int, default=100000,
                     help="scatterings per packet cap in the batch comparison (CAPPED packets are reported)")
     ap.add_argument("--galaxy", type=int, default=1, help="run the synthetic-galaxy section (1) or not (0)")
+    ap.add_argument("--c3-packets", type=int, default=1 << 17,
+                    help="packets of the expanding-sphere configuration in --section configs")
+    ap.add_argument("--configs-only", default="",
+                    help="comma-separated prefixes of the configurations --section configs runs (default: all)")
     ap.add_argument("--galaxy-rays", type=int, default=1 << 20)
     ap.add_argument("--galaxy-packets", type=int, default=1 << 18)
     ap.add_argument("--galaxy-cap", type=int, default=64, help="scatterings per packet in the galaxy section")
@@ -257,7 +264,8 @@ def run_batch(args):
     ctx.set_physics(ph.recoil, ph.isotropic, 0, ph.x_gauss, args.batch_cap, 0, ph.tau_stop, ph.seed)
     ctx.set_voigt(VOIGT)
     ctx.load_batch(models, nbin=200)
-    tune = ctx.autotune_batch(max_scatt=max(1, args.batch_cap // 20))
+    tune_cap = max(1, min(args.batch_cap // 20, 20000))
+    tune = ctx.autotune_batch(max_scatt=tune_cap)
     ctx.propagate_batch(rg.BATCH_PERSISTENT)           # warm-up (graph capture)
     t0 = time.perf_counter()
     stb = ctx.propagate_batch(rg.BATCH_PERSISTENT)
@@ -275,7 +283,7 @@ def run_batch(args):
             "persistent_scatt_per_s": sc / tb, "per_model_scatt_per_s": sc / tp if plain else None,
             "speedup": tp / tb if plain else None,
             "autotuned": {"block": tune["best"][0], "blocks_per_sm": tune["best"][1], "refill": tune["refill"],
-                          "tune_cap": max(1, args.batch_cap // 20)},
+                          "tune_cap": tune_cap},
             "workload": "512 homogeneous slab/sphere models: tau0 log-U[1e2,1e7], T log-U[1e2,1e5] K, "
                         "v_max U[0,300] km/s, (2^d)^3 grids d in 2..5, packets log-U[1e3,1e5] x %g" % args.batch_scale}
 
@@ -309,12 +317,15 @@ def run_configs(args):
         ("C1 slab tau0=1e4, T=1e4 K, 2000 packets", lambda n: synth.slab(tau0=1e4, n_packets=n), 2000),
         ("C1-thick slab tau0=1e6, T=10 K, 2000 packets", lambda n: synth.slab(tau0=1e6, T=10.0, n_packets=n), 2000),
         ("C3 expanding sphere N_HI=1e20, v_max 200 km/s, tau_dust 0.5, peeling 3 x 100^2 x 200",
-         lambda n: synth.expanding_sphere(n_packets=n), 1 << 17),
+         lambda n: synth.expanding_sphere(n_packets=n), args.c3_packets),
         ("deuterium sphere N_HI=2e19, D/H 3e-5", lambda n: synth.deuterium_sphere(n_packets=n), 1 << 18),
         ("Fe II UV1 sphere tau0=1e4 (fluorescence)", lambda n: synth.feII_sphere(n_packets=n), 1 << 20),
     ]
     out = []
+    only = [c.strip() for c in args.configs_only.split(",") if c.strip()]
     for name, fn0, n in cfgs:
+        if only and not any(name.startswith(o) for o in only):
+            continue
         fn = (lambda f: (lambda k: _with_voigt(f(k))))(fn0)
         wl = fn(n)
         ctx = rg.Context(0)
@@ -694,7 +705,7 @@ def main():
                                "note": "the same count x %.2f active lanes per warp instruction, against %d SMs x "
                                        "128 lanes x SM clock: divergence shows here" % (LANES_PER_INST, sms)}})
         pipes = {}
-        rate_of = {"fma": rates["ffma"], "fp64": rates["dfma"], "xu": rates["mufu"], "alu": rates["imad"]}
+        rate_of = {"fma": rates["ffma"], "fp64": rates["dfma"], "xu": rates["mufu"]}
         for pipe, per in PIPE_PER_SCATT.items():
             if pipe in rate_of and rate_of[pipe] > 0:
                 pipes[pipe] = {"warp_inst_per_scatt": per,

@@ -281,16 +281,12 @@ __device__ __forceinline__ float sample_upar(Rng& rng, float x, float a, const U
     }
     float u0 = u0_eval(u0c, xa);
     float t = __fdividef(u0 - xa, a);
-    float A, B;
-    if (t < 0.0f) {
-        A = atanf(__fdividef(-1.0f, t));
-        B = kPiF - A;
-    } else if (t > 0.0f) {
-        B = atanf(__fdividef(1.0f, t));
-        A = kPiF - B;
-    } else {
-        A = B = 0.5f * kPiF;
-    }
+    // the pole nearer to theta0 gets atan(1/|t|) (no cancellation), the other
+    // pi minus it; one arctangent for both signs of t
+    const float at = atanf(__fdividef(1.0f, fabsf(t)));
+    const bool lo = t < 0.0f;
+    const float A = lo ? at : kPiF - at;
+    const float B = lo ? kPiF - at : at;
     float e0 = expf(-u0 * u0);
     float p = __fdividef(A, A + e0 * B);
     float u0sq = u0 * u0;
