@@ -37,8 +37,10 @@ constexpr float kTwoPiF = 6.2831853071795865f;
 // one Philox4x32-10 round of counter (c0, c1, c2, c3) under key (k0, k1)
 __device__ __forceinline__ void philox_round(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
                                              uint32_t k0, uint32_t k1) {
-    uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-    uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    // each 32x32 -> 64-bit product as one wide multiply
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
     uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
     c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
 }
@@ -84,18 +86,18 @@ struct Rng {
         }
         return slot(n++);
     }
-    // fill the ring to kRing - 3 .. kRing words ahead
-    __device__ __forceinline__ void top_up() {
+    // fill the ring to kRing - 3 .. kRing words ahead; the round keys come
+    // from the kernel parameters (the same for every lane), so each round's
+    // key XOR reads them directly instead of stepping the key per lane
+    __device__ __forceinline__ void top_up(const Params& P) {
         if (avail - n <= kRing - 8u) {
             const uint32_t blk = avail >> 2;
             uint32_t a0 = blk, a1 = 0u, a2 = id0, a3 = id1;
             uint32_t b0 = blk + 1u, b1 = 0u, b2 = id0, b3 = id1;
-            uint32_t q0 = k0, q1 = k1;
 #pragma unroll
             for (int r = 0; r < 10; ++r) {
-                if (r) { q0 += 0x9E3779B9u; q1 += 0xBB67AE85u; }
-                philox_round(a0, a1, a2, a3, q0, q1);
-                philox_round(b0, b1, b2, b3, q0, q1);
+                philox_round(a0, a1, a2, a3, P.round_key[r][0], P.round_key[r][1]);
+                philox_round(b0, b1, b2, b3, P.round_key[r][0], P.round_key[r][1]);
             }
             put(avail, make_uint4(a0, a1, a2, a3));
             put(avail + 4u, make_uint4(b0, b1, b2, b3));

@@ -503,6 +503,10 @@ int rascas_set_physics(rascas_ctx* ctx, const rascas_physics* ph) {
     P.tau_stop = ph->tau_stop;
     P.key0 = (uint32_t)ph->seed;
     P.key1 = (uint32_t)(ph->seed >> 32);
+    for (int r = 0; r < 10; ++r) {   // the Philox4x32-10 key schedule (Salmon et al. 2011)
+        P.round_key[r][0] = P.key0 + (uint32_t)r * 0x9E3779B9u;
+        P.round_key[r][1] = P.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
     P.core_skip = (float)ph->core_skip;
     P.core_skip_f = (float)ph->core_skip_f;
     P.core_skip_on = ph->core_skip > 0.0 || ph->core_skip_f > 0.0;

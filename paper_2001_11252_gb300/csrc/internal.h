@@ -99,6 +99,7 @@ struct Params {
     long long max_scatt, max_steps;
     double tau_stop;
     uint32_t key0, key1;
+    uint32_t round_key[10][2];   // Philox4x32-10 key of each round (key0, key1 bumped by the Weyl constants)
     // peeling detector (single-model runs)
     int ndir, npix, cube;
     double dirs[kMaxDirs][3];

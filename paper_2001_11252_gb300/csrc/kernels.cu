@@ -489,7 +489,7 @@ template <int NL, bool PEEL, bool TRACE>
 __device__ __forceinline__ void advance(const Params& P, const Geo& G, Packet<NL>& s, Tallies& tl,
                                         const TraceOut& tr) {
     bool evt = false;
-    s.rng.top_up();   // the warp is converged here: draw blocks for all lanes at once
+    s.rng.top_up(P);   // the warp is converged here: draw blocks for all lanes at once
     if (s.enter) {
         load_cell<NL>(P, G, s.w.leaf, s.cc);
         ++tl.leaf_loads;
