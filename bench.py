@@ -40,12 +40,12 @@ WORKLOAD = ("static H I + dust sphere: 8^3 root refined to 64^3-equivalent octre
 # by the launch's scatterings), and the active lanes per warp instruction of
 # the same capture.  They are constants of the code and the workload, so the
 # bench multiplies them by its own live scattering rate.
-INST_PER_SCATT = 6123010616830 / 111923728554
-LANES_PER_INST = 108100456372154 / 6123010616830
+INST_PER_SCATT = 6044032067435 / 111923728554
+LANES_PER_INST = 106529112851470 / 6044032067435
 # pipe -> warp instructions per scattering of the same capture (FP32 FMA,
 # FP64, special-function unit)
-PIPE_PER_SCATT = {"fma": 2886109307884 / 111923728554, "fp64": 83444432899 / 111923728554,
-                  "xu": 166222276926 / 111923728554}
+PIPE_PER_SCATT = {"fma": 2877856853460 / 111923728554, "fp64": 83386945512 / 111923728554,
+                  "xu": 166026282325 / 111923728554}
 # DRAM bytes per leaf visit of k_ray_tau on the synthetic galaxy
 # (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of 2^18
 # rays from emitting leaves, 59 732 805 leaf visits)

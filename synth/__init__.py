@@ -667,7 +667,7 @@ def grf(n, slope, rng):
     white = rng.normal(size=(n, n, n)).astype(np.float32)
     f = np.fft.rfftn(white) * amp
     del white
-    out = np.fft.irfftn(f, s=(n, n, n)).astype(np.float32)
+    out = np.fft.irfftn(f, s=(n, n, n), axes=(0, 1, 2)).astype(np.float32)
     out -= out.mean()
     out /= out.std()
     return out
