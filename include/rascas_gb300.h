@@ -364,8 +364,10 @@ int rascas_update_fields(rascas_ctx *ctx, const float *n_HI, const float *vx, co
  * (Sect. 3.1 opacities along each ray, Sect. 5.1 peeling) are differentiated:
  *     dL/dtheta_c = - sum_events G_e w_e exp(-tau_e) L l_(e,c) dkappa_c/dtheta_c.
  * Each ray is walked twice (tau first, then the gradients), so nothing per ray
- * is stored.  g_* follow the detector shapes of rascas_get_tally (any may be
- * NULL, not all); grad receives [6][nleaf] floats (n_HI, vx, vy, vz, T,
+ * is stored; the context keeps a device buffer of 32 bytes per leaf in which
+ * each leaf's six derivatives accumulate together (RASCAS_E_OOM if it cannot
+ * be allocated).  g_* follow the detector shapes of rascas_get_tally (any may
+ * be NULL, not all); grad receives [6][nleaf] floats (n_HI, vx, vy, vz, T,
  * n_dust), zeroed first.  Not in the paper: the adjoint is an addition.
  * All pointers follow `mem`; tallies are left untouched. */
 int rascas_peel_adjoint(rascas_ctx *ctx, const rascas_packets_in *in, int64_t n, const float *g_cube,

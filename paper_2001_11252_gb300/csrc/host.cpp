@@ -75,6 +75,7 @@ struct rascas_ctx {
     DevBuf d_spec, d_pspec, d_pimg, d_pcube, d_counters, d_params;
     DevBuf stage_in, stage_out, stage_aux, stage_adj, ray_init;
     DevBuf peel_rec, peel_save, peel_flag, peel_ctl;   // deferred peeling
+    DevBuf grad_vec;                                    // adjoint: per-leaf gradient vectors
     unsigned long long peel_cap = kPeelCap;
     // batch of independent models
     struct Batch {
@@ -337,7 +338,7 @@ int rascas_destroy(rascas_ctx* ctx) {
     for (DevBuf* b : {&ctx->d_rec, &ctx->d_son, &ctx->d_nbr, &ctx->d_top, &ctx->d_spec, &ctx->d_pspec,
                       &ctx->d_pimg, &ctx->d_pcube, &ctx->d_counters, &ctx->d_params, &ctx->stage_in,
                       &ctx->stage_out, &ctx->stage_aux, &ctx->stage_adj, &ctx->ray_init, &ctx->peel_rec,
-                      &ctx->peel_save, &ctx->peel_flag, &ctx->peel_ctl})
+                      &ctx->peel_save, &ctx->peel_flag, &ctx->peel_ctl, &ctx->grad_vec})
         b->release();
     auto& B = ctx->batch;
     for (DevBuf* b : {&B.d_rec, &B.d_son, &B.d_nbr, &B.d_top, &B.d_geo, &B.d_first, &B.d_pos, &B.d_dir, &B.d_nu,
@@ -1457,13 +1458,18 @@ int rascas_peel_adjoint(rascas_ctx* ctx, const rascas_packets_in* in, int64_t n,
     } else {
         P.adj_g_cube = g_cube; P.adj_g_img = g_img; P.adj_g_spec = g_spec;
     }
-    P.adj_grad = dgrad;
+    // the walks accumulate each leaf's six derivatives as two vectors in one
+    // 32-byte sector ([nleaf][8]); unpacked into the caller's [6][nleaf] after
+    const size_t nleaf = (size_t)ctx->mesh.nleaf;
+    CK(ctx->grad_vec.ensure(nleaf * 8 * sizeof(float)));
+    P.adj_grad = (float*)ctx->grad_vec.p;
     P.g.spec = nullptr;   // the replay leaves the escape spectrum alone
-    CK(cudaMemsetAsync(dgrad, 0, n_grad * 4, st));
+    CK(cudaMemsetAsync(ctx->grad_vec.p, 0, nleaf * 8 * sizeof(float), st));
     // replay of the propagation (same packets, same streams, hence the same
     // scattering and peeling record) with peeling accumulating gradients
     r = run_propagate(ctx, in, n, nullptr, mem, nullptr, nullptr, nullptr, 0, true, &P);
     if (r) return r;
+    CK(rg::launch_grad_unpack((long long)nleaf, (const float4*)ctx->grad_vec.p, dgrad, st));
     if (mem == RASCAS_HOST) {
         CK(cudaMemcpyAsync(grad, dgrad, n_grad * 4, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));

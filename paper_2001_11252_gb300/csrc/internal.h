@@ -114,7 +114,7 @@ struct Params {
     const float* adj_g_cube;   // dL/dcube [ndir][npix][npix][nbin] (or null)
     const float* adj_g_img;    // dL/dimage [ndir][npix][npix] (or null)
     const float* adj_g_spec;   // dL/dspectrum [ndir][nbin] (or null)
-    float* adj_grad;           // [6][nleaf]: n_HI, vx, vy, vz, T, n_dust
+    float* adj_grad;           // [nleaf][8]: n_HI, vx, vy, vz, T, n_dust, 0, 0 (two 16-byte vectors per leaf)
     // deferred peeling: the scattering kernel appends PeelRec records; a warp
     // whose reservation starts at or past peel_hw suspends its packets (state
     // to save[], flag in save_flag[], one slot per thread of the launch) so
@@ -217,6 +217,8 @@ cudaError_t launch_ray_tau_fad(const Params& P, long long n, const double* pos, 
 cudaError_t launch_ray_columns(const Params& P, long long n, const double* pos, const double* dir, double* cols,
                                double* tau, double sig_hi, double sig_d, int32_t* ncell, RayInit* init, int sms,
                                cudaStream_t st);
+// the adjoint's per-leaf gradient vectors [nleaf][8] into the caller's layout [6][nleaf]
+cudaError_t launch_grad_unpack(long long nleaf, const float4* src, float* dst, cudaStream_t st);
 cudaError_t launch_pack_fields(long long n, const float* nh, const float* vx, const float* vy, const float* vz,
                                const float* T, const float* nd, const float* nm, float4* rec, cudaStream_t st);
 cudaError_t launch_eval_voigt(long long n, const float* a, const double* x, float* H, int method, cudaStream_t st);

@@ -206,10 +206,10 @@ __device__ __forceinline__ bool ray_grad_step(const Params& P, Ray<NL>& r, float
     }
     const float f = scale * P.g.box_cm_f * (float)l;
     if (f != 0.0f) {
-        const long long nleaf = P.g.nleaf;
-#pragma unroll
-        for (int j = 0; j < 6; ++j)
-            if (dk[j] != 0.0f) atomicAdd(P.adj_grad + j * nleaf + r.w.leaf, f * dk[j]);
+        // the leaf's six derivatives sit in one 32-byte sector: two vector atomics
+        float4* g = reinterpret_cast<float4*>(P.adj_grad) + 2 * (long long)r.w.leaf;
+        atomicAdd(g, make_float4(f * dk[0], f * dk[1], f * dk[2], f * dk[3]));
+        atomicAdd(reinterpret_cast<float2*>(g + 1), make_float2(f * dk[4], f * dk[5]));
     }
     if (border) return true;
     r.zero_run = order_key(tf) > 0 ? 0 : r.zero_run + 1;
@@ -1146,6 +1146,18 @@ __global__ void __launch_bounds__(128, 8) k_ray_columns(const Params* __restrict
     }
 }
 
+__global__ void k_grad_unpack(long long n, const float4* __restrict__ src, float* __restrict__ dst) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 a = src[2 * i], b = src[2 * i + 1];
+    dst[i] = a.x;
+    dst[n + i] = a.y;
+    dst[2 * n + i] = a.z;
+    dst[3 * n + i] = a.w;
+    dst[4 * n + i] = b.x;
+    dst[5 * n + i] = b.y;
+}
+
 __global__ void k_pack_fields(long long n, const float* nh, const float* vx, const float* vy, const float* vz,
                               const float* T, const float* nd, const float* nm, float4* rec) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1318,6 +1330,12 @@ cudaError_t launch_ray_columns(const Params& P, long long n, const double* pos, 
     const unsigned grid = (unsigned)std::min<long long>(need, (long long)sms * per_sm);
     k_ray_prep<1><<<(unsigned)need, block, 0, st>>>(P.self, n, pos, dir, nullptr, init);
     k_ray_columns<<<grid, block, 0, st>>>(P.self, n, init, cols, tau, sig_hi, sig_d, ncell);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_unpack(long long nleaf, const float4* src, float* dst, cudaStream_t st) {
+    if (nleaf <= 0) return cudaSuccess;
+    k_grad_unpack<<<(unsigned)((nleaf + 255) / 256), 256, 0, st>>>(nleaf, src, dst);
     return cudaGetLastError();
 }
 
