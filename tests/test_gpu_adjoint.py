@@ -80,7 +80,7 @@ def test_autograd_function():
     packets = (t(pk.pos, torch.float64), t(pk.dir, torch.float64), t(pk.nu, torch.float64),
                t(pk.ids.view(np.int64), torch.int64))
     cube = PeeledCube.apply(ctx, packets, *fields)
-    assert cube.shape == (3, 8, 8, 24) and float(cube.sum()) > 0
+    assert cube.shape == (3, 8, 8, 24) and float(cube.detach().sum()) > 0
     w = torch.linspace(-1, 1, cube.numel(), device=dev).reshape(cube.shape)
     loss = (cube * w).sum()
     loss.backward()
