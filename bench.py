@@ -289,16 +289,18 @@ def run_batch(args):
 
 
 # ------------------------------------------------------------------ per-config rates
-def _oracle_rate(wl, seconds, threads):
+def _oracle_rate(wl, seconds, threads, chunk=1):
     """Oracle on the first packets of a workload, doubling the sample until
-    about `seconds` of work: (scatterings/s, packets/s, packets, seconds)."""
+    about `seconds` of work: (scatterings/s, packets/s, packets, seconds).
+    chunk: packets per task of the thread pool (None: n / (4 threads), for
+    short packets whose per-task tallies would cost more than the packets)."""
     import oracle
     o = oracle.Oracle(wl)
     n = max(threads, 2)
     while True:
         n = min(n, wl.packets.n)
         t0 = time.perf_counter()
-        out, _ = o.run(lo=0, hi=n, threads=threads, chunk=1)
+        out, _ = o.run(lo=0, hi=n, threads=threads, chunk=chunk)
         dt = time.perf_counter() - t0
         if dt >= seconds / 3 or n == wl.packets.n:
             return int(out["nscatt"].sum()) / dt, n / dt, n, dt
@@ -354,7 +356,149 @@ def run_configs(args):
                     "oracle_1_thread_scatt_per_s": o1[0], "oracle_threads": threads,
                     "oracle_all_threads_scatt_per_s": on[0], "oracle_sample_packets": [o1[2], on[2]],
                     "gpu_over_oracle_all_threads": (sc / sec) / on[0]})
+    if not only or any(o.startswith("C4") for o in only):
+        out.append(_config_batch(args, threads))
+    if not only or any(o.startswith("C5") for o in only):
+        out.extend(_config_galaxy(args, threads, adjoint=not only or "C5" in only or "C5-adjoint" in only))
     return out
+
+
+def _oracle_models_rate(models, seconds, threads):
+    """Oracle over several models, each on a bounded first sample of its
+    packets: (scatterings/s, packets/s, packets, seconds) summed over them."""
+    sc = dt = 0.0
+    npk = 0
+    for w in models:
+        r = _oracle_rate(w, seconds / len(models), threads)
+        sc += r[0] * r[3]
+        dt += r[3]
+        npk += r[2]
+    return sc / dt, npk / dt, npk, dt
+
+
+def _config_batch(args, threads):
+    """C4 at equal work: every 16th of the 512 batch models (1 % of their
+    packets, the bench's cap), one persistent launch on the GPU against the
+    oracle on bounded samples of the same models."""
+    import paper_2001_11252_gb300 as rg
+    import synth
+    cap = args.batch_cap
+    sub = synth.batch_models(args.batch_models, packet_scale=args.batch_scale, max_scatt=cap)[::16]
+    ctx = rg.Context(0)
+    w0 = sub[0]
+    ctx.set_lines(w0.lines, w0.dust)
+    ph = w0.physics
+    ctx.set_physics(ph.recoil, ph.isotropic, 0, ph.x_gauss, cap, 0, ph.tau_stop, ph.seed)
+    ctx.set_voigt(VOIGT)
+    ctx.load_batch(sub, nbin=200)
+    ctx.autotune_batch(max_scatt=max(1, min(cap // 20, 20000)))
+    ctx.propagate_batch(rg.BATCH_PERSISTENT)
+    t0 = time.perf_counter()
+    st = ctx.propagate_batch(rg.BATCH_PERSISTENT)
+    sec = time.perf_counter() - t0
+    ctx.close()
+    sc = st["nscatt_line"] + st["nscatt_dust"]
+    for w in sub:
+        w.physics.voigt = VOIGT
+    o1 = _oracle_models_rate(sub, args.cpu_seconds / 6, 1)
+    on = _oracle_models_rate(sub, args.cpu_seconds / 6, threads)
+    return {"config": "C4 batch: every 16th of the %d models (%d), %g of their packets, cap %d scatterings"
+                      % (args.batch_models, len(sub), args.batch_scale, cap),
+            "packets": st["packets"], "gpu_s": sec, "gpu_scatt_per_s": sc / sec,
+            "gpu_packets_per_s": st["packets"] / sec, "mean_scatterings": sc / st["packets"], "capped": st["capped"],
+            "oracle_1_thread_scatt_per_s": o1[0], "oracle_threads": threads, "oracle_all_threads_scatt_per_s": on[0],
+            "oracle_sample_packets": [o1[2], on[2]], "gpu_over_oracle_all_threads": (sc / sec) / on[0]}
+
+
+def _config_galaxy(args, threads, adjoint=True):
+    """C5 at equal work: (a) the galaxy as generated, packets capped at the
+    bench's cap, peeling into 4 directions; (b) the adjoint of the cube on a
+    150 000-leaf galaxy with every density x 1e-12 (peeling rays cross many
+    leaves).  The oracle's detector in (a) is 4 x 32^2 x 40: a peeling ray
+    adds into one bin either way, and the oracle keeps FP64 tallies per chunk
+    of packets, which at 256^2 x 400 would take 0.84 GB each."""
+    import torch
+    import paper_2001_11252_gb300 as rg
+    import synth
+    dev = torch.device("cuda:0")
+    tp = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a)).to(dev, dt)
+    rows = []
+    # (a) forward
+    m = args.galaxy_packets
+    wl = synth.galaxy(n_packets=m)
+    wl.physics.voigt = VOIGT
+    wl.physics.max_scatt = args.galaxy_cap
+    ctx = rg.Context(0)
+    ctx.setup(wl)
+    pk = wl.packets
+    packets = (tp(pk.pos, torch.float64), tp(pk.dir, torch.float64), tp(pk.nu, torch.float64),
+               tp(pk.ids.view(np.int64), torch.int64))
+    ctx.propagate(*[a[:4096] for a in packets], stats=False)
+    ctx.zero_tallies()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = ctx.propagate(*packets, stats=True)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    ctx.close()
+    d = wl.detector
+    wl.detector = synth.Detector(d.nu_lo, d.nu_hi, 40, dirs=d.dirs, npix=32, fov=d.fov, centre=d.centre, cube=d.cube)
+    o1 = _oracle_rate(wl, args.cpu_seconds / 6, 1)
+    on = _oracle_rate(wl, args.cpu_seconds / 6, threads, chunk=None)
+    sc = st["nscatt_line"] + st["nscatt_dust"]
+    rows.append({"config": "C5 galaxy as generated (%d leaves), cap %d scatterings, peeling 4 directions"
+                           % (wl.medium.tree.nleaf, args.galaxy_cap),
+                 "packets": m, "gpu_s": sec, "gpu_scatt_per_s": sc / sec, "gpu_packets_per_s": m / sec,
+                 "mean_scatterings": sc / m, "peel_rays": st["npeel_rays"], "capped": st["capped"],
+                 "oracle_1_thread_packets_per_s": o1[1], "oracle_threads": threads,
+                 "oracle_all_threads_packets_per_s": on[1], "oracle_1_thread_scatt_per_s": o1[0],
+                 "oracle_all_threads_scatt_per_s": on[0], "oracle_sample_packets": [o1[2], on[2]],
+                 "gpu_over_oracle_all_threads": (m / sec) / on[1]})
+    del wl
+    if not adjoint:
+        return rows
+    # (b) adjoint on a cut-out
+    import oracle
+    n = 4096
+    wl = synth.galaxy(n_leaf=150_000, grid_level=6, base_level=4, max_level=10, n_packets=n, npix=16, nchan=40)
+    md = wl.medium
+    for f in ("n_HI", "n_dust", "n_metal"):
+        setattr(md, f, (np.asarray(getattr(md, f), np.float32) * np.float32(1e-12)).astype(np.float32))
+    wl.physics.voigt = VOIGT
+    wl.physics.max_scatt = 64
+    ctx = rg.Context(0)
+    ctx.setup(wl)
+    pk = wl.packets
+    packets = (tp(pk.pos, torch.float64), tp(pk.dir, torch.float64), tp(pk.nu, torch.float64),
+               tp(pk.ids.view(np.int64), torch.int64))
+    st = ctx.propagate(*packets, stats=True)
+    g = torch.ones((len(wl.detector.dirs), wl.detector.npix, wl.detector.npix, wl.detector.nbin), device=dev)
+    ctx.peel_adjoint(*packets, g_cube=g)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.peel_adjoint(*packets, g_cube=g)
+    torch.cuda.synchronize()
+    gsec = time.perf_counter() - t0
+    ctx.close()
+    o = oracle.Oracle(wl)
+    k = 64
+    while True:
+        _, tal = o.run(lo=0, hi=k, threads=1, record_events=1 << 21)
+        ev = tal["events"]
+        t0 = time.perf_counter()
+        o.adjoint(ev, g_cube=np.ones((len(wl.detector.dirs), wl.detector.npix, wl.detector.npix,
+                                      wl.detector.nbin)))
+        osec = time.perf_counter() - t0
+        if osec >= args.cpu_seconds / 12 or k >= n:
+            break
+        k *= 2
+    rows.append({"config": "C5 adjoint of the 4 x 16^2 x 40 cube, 150 000-leaf galaxy, densities x 1e-12, cap 64",
+                 "packets": n, "gpu_s": gsec, "gpu_peel_rays_per_s": st["npeel_rays"] / gsec,
+                 "gpu_leaves_per_ray": st["npeel_cells"] / max(1, st["npeel_rays"]),
+                 "oracle_1_thread_peel_rays_per_s": ev.size / osec, "oracle_sample_packets": k,
+                 "oracle_events": int(ev.size),
+                 "gpu_over_oracle_1_thread": (st["npeel_rays"] / gsec) / (ev.size / osec)})
+    return rows
 
 
 # ------------------------------------------------------------------ galaxy section
