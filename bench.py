@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--galaxy", type=int, default=1, help="run the synthetic-galaxy section (1) or not (0)")
     ap.add_argument("--c3-packets", type=int, default=1 << 17,
                     help="packets of the expanding-sphere configuration in --section configs")
+    ap.add_argument("--peel-adjoint", action="store_true",
+                    help="--section peel: run the adjoint of the cube instead of the forward propagation")
     ap.add_argument("--configs-only", default="",
                     help="comma-separated prefixes of the configurations --section configs runs (default: all)")
     ap.add_argument("--galaxy-rays", type=int, default=1 << 20)
@@ -699,6 +701,15 @@ def run_peel(args):
     packets = (tp(pk.pos, torch.float64), tp(pk.dir, torch.float64), tp(pk.nu, torch.float64),
                tp(pk.ids.view(np.int64), torch.int64))
     torch.cuda.synchronize()
+    if args.peel_adjoint:
+        # the adjoint of the cube alone (its replay and the gradient walks)
+        g = torch.randn((len(wl.detector.dirs), wl.detector.npix, wl.detector.npix, wl.detector.nbin), device=dev)
+        t0 = time.perf_counter()
+        grad = ctx.peel_adjoint(*packets, g_cube=g)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        return {"packets": m, "thin": args.galaxy_thin, "adjoint_seconds": dt,
+                "grad_nonzero_leaves": int((grad[0] != 0).sum().item())}
     t0 = time.perf_counter()
     st = ctx.propagate(*packets, stats=True)
     torch.cuda.synchronize()
