@@ -158,25 +158,12 @@ __device__ __forceinline__ float tau_stop_f(double tau_stop) {
     return tau_stop >= 3.0e38 ? __int_as_float(0x7f800000) : (float)tau_stop;
 }
 
-// adjoint walk of one leaf: grad[j][leaf] += scale L l d kappa / d theta_j
-// (Sect. 3.1 opacities differentiated in n_HI, v, T and n_dust); true when
-// the ray is done
+// adjoint contribution of one leaf crossed over length l: grad[leaf][j] +=
+// scale L l d kappa / d theta_j (Sect. 3.1 opacities differentiated in n_HI,
+// v, T and n_dust)
 template <int NL>
-__device__ __forceinline__ bool ray_grad_step(const Params& P, Ray<NL>& r, float scale, uint32_t& sl, uint32_t& nl) {
-    const float4 r0 = __ldg(P.g.rec + 2 * r.w.leaf);
-    const float4 r1 = __ldg(P.g.rec + 2 * r.w.leaf + 1);
-    float kl[NL], xh[NL], xl[NL];
-    f2 beta;
-    ray_opacity<NL>(P, r.R, r0, r1, kl, xh, xl, beta);
-    int axis;
-    const double tf = face_distance(r.p, r.k, r.inv, r.w, axis);
-    bool border = false;
-    double l = tf;
-    if (__float_as_int(r1.w) & kFlagBorder) {
-        const double tb = border_distance(P.g, r.p, r.k, r.inv);
-        border = order_key(tb) <= order_key(tf);
-        if (border) l = tb;
-    }
+__device__ __forceinline__ void grad_add(const Params& P, const Ray<NL>& r, const float4& r0, const float4& r1,
+                                         const float xh[NL], const f2& beta, double l, float scale) {
     float dk[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, P.dust_sigma};
     const float Tm = fmaxf(r1.x, 1e-30f);
     const float rs = rsqrtf(Tm);
@@ -211,7 +198,38 @@ __device__ __forceinline__ bool ray_grad_step(const Params& P, Ray<NL>& r, float
         atomicAdd(g, make_float4(f * dk[0], f * dk[1], f * dk[2], f * dk[3]));
         atomicAdd(reinterpret_cast<float2*>(g + 1), make_float2(f * dk[4], f * dk[5]));
     }
-    if (border) return true;
+}
+
+// one leaf of a peeling ray's walk: its optical depth (grad false) or, on the
+// adjoint's second walk, its gradient contribution (grad true).  Both walks
+// share the leaf load, the opacity and the geometry, so the lanes of a warp
+// in different walks stay together; true when the ray is done (border, box
+// edge, tau beyond tstop on the first walk, or a stuck walk)
+template <int NL>
+__device__ __forceinline__ bool peel_step(const Params& P, Ray<NL>& r, bool grad, float scale, float tstop,
+                                          uint32_t& sl, uint32_t& nl) {
+    const float4 r0 = __ldg(P.g.rec + 2 * r.w.leaf);
+    const float4 r1 = __ldg(P.g.rec + 2 * r.w.leaf + 1);
+    float kl[NL], xh[NL], xl[NL];
+    f2 beta;
+    const float kap = ray_opacity<NL>(P, r.R, r0, r1, kl, xh, xl, beta);
+    int axis;
+    const double tf = face_distance(r.p, r.k, r.inv, r.w, axis);
+    bool border = false;
+    double l = tf;
+    if (__float_as_int(r1.w) & kFlagBorder) {
+        const double tb = border_distance(P.g, r.p, r.k, r.inv);
+        border = order_key(tb) <= order_key(tf);
+        if (border) l = tb;
+    }
+    if (grad) {
+        grad_add<NL>(P, r, r0, r1, xh, beta, l, scale);
+        if (border) return true;
+    } else {
+        r.tau = f2_add_f(r.tau, kap * (float)l * P.g.box_cm_f);
+        ++r.n;
+        if (border || r.tau.h > tstop) return true;
+    }
     r.zero_run = order_key(tf) > 0 ? 0 : r.zero_run + 1;
     if (r.zero_run > 64) return true;
     move_to_face(r.p, r.k, axis, tf, r.w);
@@ -949,14 +967,16 @@ __device__ __forceinline__ void peel_bins(const Params& P, const PeelRec& q, int
     }
 }
 
-template <int NL>
-__global__ void __launch_bounds__(128) k_peel(const Params* __restrict__ G) {
+template <int NL, bool ADJ>
+__global__ void __launch_bounds__(128, ADJ ? 3 : 4) k_peel(const Params* __restrict__ G) {
     const Params& P = *G;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long cnt = *P.peel_count;
     const unsigned long long n = cnt < P.peel_cap ? cnt : P.peel_cap;
     const float tstop = tau_stop_f(P.tau_stop);
-    const bool adj = P.adj_grad != nullptr;
+    // ADJ: the adjoint's launch (P.adj_grad set): each contributing ray is
+    // walked a second time for its gradient
+    const bool adj = ADJ;
     const long long npix2 = (long long)P.npix * P.npix;
     Ray<NL> r;
     PeelRec q;
@@ -995,8 +1015,8 @@ __global__ void __launch_bounds__(128) k_peel(const Params* __restrict__ G) {
         }
         if (active) {
             bool done;
-            if (phase == 0) done = ray_step<NL>(P, r, tstop, nullptr, nullptr, 0, sl, nl);
-            else done = ray_grad_step<NL>(P, r, scale, sl, nl);
+            if constexpr (ADJ) done = peel_step<NL>(P, r, phase != 0, scale, tstop, sl, nl);
+            else done = ray_step<NL>(P, r, tstop, nullptr, nullptr, 0, sl, nl);
             if (++steps >= (1u << 26)) done = true;
             if (done && phase == 0) {
                 cells += r.n;
@@ -1236,20 +1256,25 @@ static int ray_occ() {
     return nb > 0 ? nb : 1;
 }
 
-template <int NL>
+template <int NL, bool ADJ>
 static int peel_occ() {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_peel<NL>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_peel<NL, ADJ>, 128, 0);
     return nb > 0 ? nb : 1;
 }
 
 cudaError_t RG_SFX(launch_peel)(const Params& P, int sms, cudaStream_t st) {
     const Params* G = P.self;
-    switch (P.nline) {
-        case 1: k_peel<1><<<sms * peel_occ<1>(), 128, 0, st>>>(G); break;
-        case 2: k_peel<2><<<sms * peel_occ<2>(), 128, 0, st>>>(G); break;
-        case 3: k_peel<3><<<sms * peel_occ<3>(), 128, 0, st>>>(G); break;
-        case 4: k_peel<4><<<sms * peel_occ<4>(), 128, 0, st>>>(G); break;
+    const bool adj = P.adj_grad != nullptr;
+    switch (P.nline * 2 + (adj ? 1 : 0)) {
+        case 2: k_peel<1, false><<<sms * peel_occ<1, false>(), 128, 0, st>>>(G); break;
+        case 3: k_peel<1, true><<<sms * peel_occ<1, true>(), 128, 0, st>>>(G); break;
+        case 4: k_peel<2, false><<<sms * peel_occ<2, false>(), 128, 0, st>>>(G); break;
+        case 5: k_peel<2, true><<<sms * peel_occ<2, true>(), 128, 0, st>>>(G); break;
+        case 6: k_peel<3, false><<<sms * peel_occ<3, false>(), 128, 0, st>>>(G); break;
+        case 7: k_peel<3, true><<<sms * peel_occ<3, true>(), 128, 0, st>>>(G); break;
+        case 8: k_peel<4, false><<<sms * peel_occ<4, false>(), 128, 0, st>>>(G); break;
+        case 9: k_peel<4, true><<<sms * peel_occ<4, true>(), 128, 0, st>>>(G); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
