@@ -270,14 +270,15 @@ int rascas_set_voigt(rascas_ctx *ctx, int method);
 int rascas_set_detector(rascas_ctx *ctx, const rascas_detector *det);
 /* Zero every tally of the detector (asynchronous, on the context's stream). */
 int rascas_zero_tallies(rascas_ctx *ctx);
-/* Capacity, in 64-byte records, of the device buffer of peeling rays (one per
+/* Capacity, in records, of the device buffers of peeling rays (one per
  * emission or scattering and observer direction, Sect. 3.1 peeling) that the
- * scattering kernel appends and the peel kernel then walks and tallies.  When
- * it fills, the packets in flight are parked in device memory and resumed
- * once the records are walked: results do not depend on the capacity, only
- * the number of rounds does.  Default 2^23 records (512 MiB); a value below
- * the floor set by the launch shape (a few resident-thread multiples) is
- * raised to it.  RASCAS_E_ARG if records < 1. */
+ * scattering kernel appends and the peel kernel then walks and tallies; each
+ * record takes 128 bytes (the ray, and its frequency pairs and bins formed
+ * before the walk).  When the buffer fills, the packets in flight are parked
+ * in device memory and resumed once the records are walked: results do not
+ * depend on the capacity, only the number of rounds does.  Default 2^23
+ * records (1 GiB); a value below the floor set by the launch shape (a few
+ * resident-thread multiples) is raised to it.  RASCAS_E_ARG if records < 1. */
 int rascas_set_peel_capacity(rascas_ctx *ctx, int64_t records);
 
 /* ---- the hot path -------------------------------------------------------- */

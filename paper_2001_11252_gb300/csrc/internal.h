@@ -82,6 +82,21 @@ struct PeelRec {
 };
 static_assert(sizeof(PeelRec) == 64, "PeelRec is one 64-byte record");
 
+// set-up of a peeling ray formed from its PeelRec by a prep pass before the
+// walk (every lane busy): the frequency as FP32 pairs (hi, lo), the
+// detector bins and the weight, so that the walk kernel does no per-ray
+// FP64 work of its own
+struct alignas(16) PeelPrep {
+    float nu[2];             // nu_ext
+    float d[kMaxLines][2];   // nu_ext - nu0 of each line
+    int ch;                  // spectrum channel, -1 outside the frequency range
+    int dir;                 // observer direction
+    float wt;                // weight per sr
+    int pad;
+    long long px;            // image pixel, -1 outside the image
+};
+static_assert(sizeof(PeelPrep) == 64, "PeelPrep is one 64-byte record");
+
 struct Params {
     const Params* self;    // device-side copy of these parameters (read by the peeling walk)
     Geo g;                 // the medium of a single-model run
@@ -120,6 +135,7 @@ struct Params {
     // to save[], flag in save_flag[], one slot per thread of the launch) so
     // that the peel kernel can drain the records before the next round
     PeelRec* peel_rec;
+    PeelPrep* peel_prep;       // [peel_cap], written by the prep pass of each round
     unsigned long long* peel_count;   // records appended this round
     unsigned long long* peel_head;    // queue head of the peel kernel
     unsigned long long peel_cap, peel_hw;

@@ -925,8 +925,13 @@ __global__ void __launch_bounds__(128, 8) k_ray_tau(const Params* __restrict__ G
 // cube bins of the record.  Adjoint (P.adj_grad set): the ray is walked a
 // second time with the scale -G w exp(-tau), G the loss gradient at those bins.
 // ---------------------------------------------------------------------------
+// a peeling ray from its record i: start point and leaf from the PeelRec,
+// frequency pairs from the PeelPrep of the prep pass, direction terms from
+// the parameters
 template <int NL>
-__device__ __forceinline__ void ray_from_rec(const Params& P, const PeelRec& q, Ray<NL>& r) {
+__device__ __forceinline__ void ray_from_prep(const Params& P, unsigned long long i, Ray<NL>& r) {
+    const PeelRec& q = P.peel_rec[i];
+    const PeelPrep& pp = P.peel_prep[i];
     const int d = q.d;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -936,9 +941,9 @@ __device__ __forceinline__ void ray_from_rec(const Params& P, const PeelRec& q, 
         r.R.k[j] = f2{P.dir_kp[d][j][0], P.dir_kp[d][j][1]};
     }
     r.w.leaf = q.w[0]; r.w.oct = q.w[1]; r.w.level = q.w[2]; r.w.i = q.w[3]; r.w.j = q.w[4]; r.w.k = q.w[5];
-    r.R.nu = f2_of(q.nu_ext);
+    r.R.nu = f2{pp.nu[0], pp.nu[1]};
 #pragma unroll
-    for (int i = 0; i < NL; ++i) r.R.d[i] = f2_of(q.nu_ext - P.line[i].nu0);
+    for (int l = 0; l < NL; ++l) r.R.d[l] = f2{pp.d[l][0], pp.d[l][1]};
     r.tau = f2{0.0f, 0.0f};
     r.n = 0;
     r.zero_run = 0;
@@ -967,6 +972,40 @@ __device__ __forceinline__ void peel_bins(const Params& P, const PeelRec& q, int
     }
 }
 
+// prep pass of a round: the per-ray FP64 work of the peeling records (the
+// frequency pairs of the walk, the detector bins of the tally), one record
+// per thread with every lane busy, so that the walk kernel, where a lane
+// starts or ends a ray alone, does none of it
+template <int NL>
+__global__ void __launch_bounds__(256) k_peel_prep(const Params* __restrict__ G) {
+    const Params& P = *G;
+    const unsigned long long cnt = *P.peel_count;
+    const unsigned long long n = cnt < P.peel_cap ? cnt : P.peel_cap;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const PeelRec q = P.peel_rec[i];
+        PeelPrep o;
+        const f2 nu = f2_of(q.nu_ext);
+        o.nu[0] = nu.h;
+        o.nu[1] = nu.l;
+#pragma unroll
+        for (int l = 0; l < kMaxLines; ++l) {
+            const f2 dl = l < NL ? f2_of(q.nu_ext - P.line[l].nu0) : f2{0.0f, 0.0f};
+            o.d[l][0] = dl.h;
+            o.d[l][1] = dl.l;
+        }
+        int ch;
+        long long px;
+        peel_bins(P, q, ch, px);
+        o.ch = ch;
+        o.dir = q.d;
+        o.wt = q.wt;
+        o.pad = 0;
+        o.px = px;
+        P.peel_prep[i] = o;
+    }
+}
+
 template <int NL, bool ADJ>
 __global__ void __launch_bounds__(128, ADJ ? 3 : 4) k_peel(const Params* __restrict__ G) {
     const Params& P = *G;
@@ -979,7 +1018,6 @@ __global__ void __launch_bounds__(128, ADJ ? 3 : 4) k_peel(const Params* __restr
     const bool adj = ADJ;
     const long long npix2 = (long long)P.npix * P.npix;
     Ray<NL> r;
-    PeelRec q;
     unsigned long long i = 0;
     bool active = false, drained = false;
     int phase = 0;           // 0: optical depth, 1: adjoint walk
@@ -999,8 +1037,7 @@ __global__ void __launch_bounds__(128, ADJ ? 3 : 4) k_peel(const Params* __restr
             if (want) {
                 i = base + __popc(m & ((1u << lane) - 1u));
                 if (i < n) {
-                    q = P.peel_rec[i];
-                    ray_from_rec<NL>(P, q, r);
+                    ray_from_prep<NL>(P, i, r);
                     phase = 0;
                     steps = 0;
                     active = true;
@@ -1023,11 +1060,11 @@ __global__ void __launch_bounds__(128, ADJ ? 3 : 4) k_peel(const Params* __restr
                 active = false;
                 const double tau = f2_val(r.tau);
                 if (tau <= P.tau_stop) {
-                    const float f = q.wt * expf(-(float)tau);
-                    int ch;
-                    long long px;
-                    peel_bins(P, q, ch, px);
-                    const int nbin = P.g.nbin, d = q.d;
+                    const PeelPrep& pp = P.peel_prep[i];
+                    const float f = pp.wt * expf(-(float)tau);
+                    const int ch = pp.ch;
+                    const long long px = pp.px;
+                    const int nbin = P.g.nbin, d = pp.dir;
                     if (adj) {
                         float Gs = 0.0f;
                         if (ch >= 0 && P.adj_g_spec) Gs += __ldg(P.adj_g_spec + d * nbin + ch);
@@ -1035,7 +1072,7 @@ __global__ void __launch_bounds__(128, ADJ ? 3 : 4) k_peel(const Params* __restr
                         if (px >= 0 && ch >= 0 && P.cube && P.adj_g_cube)
                             Gs += __ldg(P.adj_g_cube + (d * npix2 + px) * nbin + ch);
                         if (Gs != 0.0f && f != 0.0f) {
-                            ray_from_rec<NL>(P, q, r);
+                            ray_from_prep<NL>(P, i, r);
                             scale = -Gs * f;
                             phase = 1;
                             steps = 0;
@@ -1266,6 +1303,13 @@ static int peel_occ() {
 cudaError_t RG_SFX(launch_peel)(const Params& P, int sms, cudaStream_t st) {
     const Params* G = P.self;
     const bool adj = P.adj_grad != nullptr;
+    switch (P.nline) {
+        case 1: k_peel_prep<1><<<sms * 8, 256, 0, st>>>(G); break;
+        case 2: k_peel_prep<2><<<sms * 8, 256, 0, st>>>(G); break;
+        case 3: k_peel_prep<3><<<sms * 8, 256, 0, st>>>(G); break;
+        case 4: k_peel_prep<4><<<sms * 8, 256, 0, st>>>(G); break;
+        default: return cudaErrorInvalidValue;
+    }
     switch (P.nline * 2 + (adj ? 1 : 0)) {
         case 2: k_peel<1, false><<<sms * peel_occ<1, false>(), 128, 0, st>>>(G); break;
         case 3: k_peel<1, true><<<sms * peel_occ<1, true>(), 128, 0, st>>>(G); break;
