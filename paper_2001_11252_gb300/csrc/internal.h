@@ -83,17 +83,17 @@ struct PeelRec {
 static_assert(sizeof(PeelRec) == 64, "PeelRec is one 64-byte record");
 
 // set-up of a peeling ray formed from its PeelRec by a prep pass before the
-// walk (every lane busy): the frequency as FP32 pairs (hi, lo), the
-// detector bins and the weight, so that the walk kernel does no per-ray
-// FP64 work of its own
+// walk (every lane busy): the frequency as FP32 pairs (hi, lo), the ray's
+// first leaf, and the detector bins of the rays that get past it, so that
+// the walk kernel does no per-ray FP64 work of its own
 struct alignas(16) PeelPrep {
     float nu[2];             // nu_ext
     float d[kMaxLines][2];   // nu_ext - nu0 of each line
-    int ch;                  // spectrum channel, -1 outside the frequency range
+    int ch;                  // spectrum channel, -1 outside the frequency range (or dark)
     int dir;                 // observer direction
     float wt;                // weight per sr
-    int pad;
-    long long px;            // image pixel, -1 outside the image
+    int dark;                // 1: the walk ends in the first leaf with tau beyond tau_stop
+    long long px;            // image pixel, -1 outside the image (or dark)
 };
 static_assert(sizeof(PeelPrep) == 64, "PeelPrep is one 64-byte record");
 

@@ -972,35 +972,72 @@ __device__ __forceinline__ void peel_bins(const Params& P, const PeelRec& q, int
     }
 }
 
+// true when a ray's walk ends in its first leaf without a contribution: the
+// first step of ray_step (same arithmetic) stops it with tau beyond tau_stop
+template <int NL>
+__device__ __forceinline__ bool first_leaf_dark(const Params& P, const Ray<NL>& r, float tstop) {
+    const float4 r0 = __ldg(P.g.rec + 2 * r.w.leaf);
+    const float4 r1 = __ldg(P.g.rec + 2 * r.w.leaf + 1);
+    float kl[NL], xh[NL], xl[NL];
+    f2 beta;
+    const float kap = ray_opacity<NL>(P, r.R, r0, r1, kl, xh, xl, beta);
+    int axis;
+    const double tf = face_distance(r.p, r.k, r.inv, r.w, axis);
+    bool border = false;
+    double l = tf;
+    if (__float_as_int(r1.w) & kFlagBorder) {
+        const double tb = border_distance(P.g, r.p, r.k, r.inv);
+        border = order_key(tb) <= order_key(tf);
+        if (border) l = tb;
+    }
+    const f2 tau = f2_add_f(r.tau, kap * (float)l * P.g.box_cm_f);
+    return (border || tau.h > tstop) && !(f2_val(tau) <= P.tau_stop);
+}
+
 // prep pass of a round: the per-ray FP64 work of the peeling records (the
-// frequency pairs of the walk, the detector bins of the tally), one record
-// per thread with every lane busy, so that the walk kernel, where a lane
-// starts or ends a ray alone, does none of it
+// frequency pairs of the walk; the first leaf, and the detector bins of the
+// rays that get past it), one record per thread with every lane busy, so
+// that the walk kernel, where a lane starts or ends a ray alone, does none of
+// it and skips the rays that end dark in their first leaf
 template <int NL>
 __global__ void __launch_bounds__(256) k_peel_prep(const Params* __restrict__ G) {
     const Params& P = *G;
     const unsigned long long cnt = *P.peel_count;
     const unsigned long long n = cnt < P.peel_cap ? cnt : P.peel_cap;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const float tstop = tau_stop_f(P.tau_stop);
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const PeelRec q = P.peel_rec[i];
         PeelPrep o;
-        const f2 nu = f2_of(q.nu_ext);
-        o.nu[0] = nu.h;
-        o.nu[1] = nu.l;
+        Ray<NL> r;
+        r.R.nu = f2_of(q.nu_ext);
+        o.nu[0] = r.R.nu.h;
+        o.nu[1] = r.R.nu.l;
 #pragma unroll
         for (int l = 0; l < kMaxLines; ++l) {
             const f2 dl = l < NL ? f2_of(q.nu_ext - P.line[l].nu0) : f2{0.0f, 0.0f};
+            if (l < NL) r.R.d[l] = dl;
             o.d[l][0] = dl.h;
             o.d[l][1] = dl.l;
         }
-        int ch;
-        long long px;
-        peel_bins(P, q, ch, px);
+        const int d = q.d;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            r.p[j] = q.p[j];
+            r.k[j] = P.dirs[d][j];
+            r.inv[j] = P.dir_inv[d][j];
+            r.R.k[j] = f2{P.dir_kp[d][j][0], P.dir_kp[d][j][1]};
+        }
+        r.w.leaf = q.w[0]; r.w.oct = q.w[1]; r.w.level = q.w[2]; r.w.i = q.w[3]; r.w.j = q.w[4]; r.w.k = q.w[5];
+        r.tau = f2{0.0f, 0.0f};
+        const bool dark = first_leaf_dark<NL>(P, r, tstop);
+        int ch = -1;
+        long long px = -1;
+        if (!dark) peel_bins(P, q, ch, px);
         o.ch = ch;
-        o.dir = q.d;
+        o.dir = d;
         o.wt = q.wt;
-        o.pad = 0;
+        o.dark = dark ? 1 : 0;
         o.px = px;
         P.peel_prep[i] = o;
     }
@@ -1037,10 +1074,14 @@ __global__ void __launch_bounds__(128, ADJ ? 3 : 4) k_peel(const Params* __restr
             if (want) {
                 i = base + __popc(m & ((1u << lane) - 1u));
                 if (i < n) {
-                    ray_from_prep<NL>(P, i, r);
-                    phase = 0;
-                    steps = 0;
-                    active = true;
+                    if (P.peel_prep[i].dark) {
+                        cells += 1;   // ends in its first leaf beyond tau_stop: nothing to walk or tally
+                    } else {
+                        ray_from_prep<NL>(P, i, r);
+                        phase = 0;
+                        steps = 0;
+                        active = true;
+                    }
                 } else {
                     drained = true;
                 }
