@@ -273,11 +273,11 @@ int rascas_zero_tallies(rascas_ctx *ctx);
 /* Capacity, in records, of the device buffers of peeling rays (one per
  * emission or scattering and observer direction, Sect. 3.1 peeling) that the
  * scattering kernel appends and the peel kernel then walks and tallies; each
- * record takes 128 bytes (the ray, and its frequency pairs and bins formed
- * before the walk).  When the buffer fills, the packets in flight are parked
+ * record takes 136 bytes (the ray; its frequency pairs and bins formed before
+ * the walk; its place in the list of rays to walk).  When the buffer fills, the packets in flight are parked
  * in device memory and resumed once the records are walked: results do not
  * depend on the capacity, only the number of rounds does.  Default 2^23
- * records (1 GiB); a value below the floor set by the launch shape (a few
+ * records (1.06 GiB); a value below the floor set by the launch shape (a few
  * resident-thread multiples) is raised to it.  RASCAS_E_ARG if records < 1. */
 int rascas_set_peel_capacity(rascas_ctx *ctx, int64_t records);
 

@@ -74,7 +74,7 @@ struct rascas_ctx {
     Params P{};
     DevBuf d_spec, d_pspec, d_pimg, d_pcube, d_counters, d_params;
     DevBuf stage_in, stage_out, stage_aux, stage_adj, ray_init;
-    DevBuf peel_rec, peel_prep, peel_save, peel_flag, peel_ctl;   // deferred peeling
+    DevBuf peel_rec, peel_prep, peel_live, peel_save, peel_flag, peel_ctl;   // deferred peeling
     DevBuf grad_vec;                                    // adjoint: per-leaf gradient vectors
     unsigned long long peel_cap = kPeelCap;
     // batch of independent models
@@ -338,7 +338,8 @@ int rascas_destroy(rascas_ctx* ctx) {
     for (DevBuf* b : {&ctx->d_rec, &ctx->d_son, &ctx->d_nbr, &ctx->d_top, &ctx->d_spec, &ctx->d_pspec,
                       &ctx->d_pimg, &ctx->d_pcube, &ctx->d_counters, &ctx->d_params, &ctx->stage_in,
                       &ctx->stage_out, &ctx->stage_aux, &ctx->stage_adj, &ctx->ray_init, &ctx->peel_rec,
-                      &ctx->peel_prep, &ctx->peel_save, &ctx->peel_flag, &ctx->peel_ctl, &ctx->grad_vec})
+                      &ctx->peel_prep, &ctx->peel_live, &ctx->peel_save, &ctx->peel_flag, &ctx->peel_ctl,
+                      &ctx->grad_vec})
         b->release();
     auto& B = ctx->batch;
     for (DevBuf* b : {&B.d_rec, &B.d_son, &B.d_nbr, &B.d_top, &B.d_geo, &B.d_first, &B.d_pos, &B.d_dir, &B.d_nu,
@@ -709,15 +710,18 @@ int run_propagate(rascas_ctx* ctx, const rascas_packets_in* in, int64_t n, const
         const unsigned long long cap = std::max<unsigned long long>(ctx->peel_cap, 4 * margin);
         CK(ctx->peel_rec.ensure(cap * sizeof(rg::PeelRec)));
         CK(ctx->peel_prep.ensure(cap * sizeof(rg::PeelPrep)));
+        CK(ctx->peel_live.ensure(cap * sizeof(unsigned long long)));
         CK(ctx->peel_save.ensure(threads * rg::packet_save_bytes(P.nline)));
         CK(ctx->peel_flag.ensure(threads * sizeof(int)));
         CK(ctx->peel_ctl.ensure(4 * sizeof(unsigned long long)));
         unsigned long long* ctl = (unsigned long long*)ctx->peel_ctl.p;
         P.peel_rec = (rg::PeelRec*)ctx->peel_rec.p;
         P.peel_prep = (rg::PeelPrep*)ctx->peel_prep.p;
+        P.peel_live = (unsigned long long*)ctx->peel_live.p;
         P.peel_count = ctl;
         P.peel_head = ctl + 1;
         P.suspended = (unsigned int*)(ctl + 2);
+        P.peel_nlive = ctl + 3;
         P.peel_cap = cap;
         P.peel_hw = cap - margin;
         P.save = ctx->peel_save.p;

@@ -92,7 +92,7 @@ struct alignas(16) PeelPrep {
     int ch;                  // spectrum channel, -1 outside the frequency range (or dark)
     int dir;                 // observer direction
     float wt;                // weight per sr
-    int dark;                // 1: the walk ends in the first leaf with tau beyond tau_stop
+    int dark;                // 1: the walk ends in the first leaf with tau beyond tau_stop (not listed)
     long long px;            // image pixel, -1 outside the image (or dark)
 };
 static_assert(sizeof(PeelPrep) == 64, "PeelPrep is one 64-byte record");
@@ -136,6 +136,8 @@ struct Params {
     // that the peel kernel can drain the records before the next round
     PeelRec* peel_rec;
     PeelPrep* peel_prep;       // [peel_cap], written by the prep pass of each round
+    unsigned long long* peel_live;    // [peel_cap]: records past their first leaf, listed by the prep pass
+    unsigned long long* peel_nlive;   // their number
     unsigned long long* peel_count;   // records appended this round
     unsigned long long* peel_head;    // queue head of the peel kernel
     unsigned long long peel_cap, peel_hw;

@@ -998,7 +998,9 @@ __device__ __forceinline__ bool first_leaf_dark(const Params& P, const Ray<NL>& 
 // frequency pairs of the walk; the first leaf, and the detector bins of the
 // rays that get past it), one record per thread with every lane busy, so
 // that the walk kernel, where a lane starts or ends a ray alone, does none of
-// it and skips the rays that end dark in their first leaf
+// it.  The rays that get past their first leaf are listed (one atomic per
+// warp) for the walk kernel; the others, dark after one leaf, are counted
+// here
 template <int NL>
 __global__ void __launch_bounds__(256) k_peel_prep(const Params* __restrict__ G) {
     const Params& P = *G;
@@ -1006,7 +1008,10 @@ __global__ void __launch_bounds__(256) k_peel_prep(const Params* __restrict__ G)
     const unsigned long long n = cnt < P.peel_cap ? cnt : P.peel_cap;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     const float tstop = tau_stop_f(P.tau_stop);
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned long long dark_cells = 0;
     for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const unsigned am = __activemask();
         const PeelRec q = P.peel_rec[i];
         PeelPrep o;
         Ray<NL> r;
@@ -1031,24 +1036,37 @@ __global__ void __launch_bounds__(256) k_peel_prep(const Params* __restrict__ G)
         r.w.leaf = q.w[0]; r.w.oct = q.w[1]; r.w.level = q.w[2]; r.w.i = q.w[3]; r.w.j = q.w[4]; r.w.k = q.w[5];
         r.tau = f2{0.0f, 0.0f};
         const bool dark = first_leaf_dark<NL>(P, r, tstop);
-        int ch = -1;
-        long long px = -1;
-        if (!dark) peel_bins(P, q, ch, px);
-        o.ch = ch;
-        o.dir = d;
-        o.wt = q.wt;
-        o.dark = dark ? 1 : 0;
-        o.px = px;
-        P.peel_prep[i] = o;
+        if (dark) {
+            ++dark_cells;
+        } else {
+            int ch = -1;
+            long long px = -1;
+            peel_bins(P, q, ch, px);
+            o.ch = ch;
+            o.dir = d;
+            o.wt = q.wt;
+            o.dark = 0;
+            o.px = px;
+            P.peel_prep[i] = o;
+        }
+        const unsigned m = __ballot_sync(am, !dark);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            unsigned long long base = 0;
+            if ((int)lane == leader) base = atomicAdd(P.peel_nlive, (unsigned long long)__popc(m));
+            base = __shfl_sync(am, base, leader);
+            if (!dark) P.peel_live[base + __popc(m & ((1u << lane) - 1u))] = i;
+        }
     }
+    flush(P, dark_cells, CNT_PEEL_CELLS);
+    flush(P, dark_cells, CNT_LEAF_LOADS);
 }
 
 template <int NL, bool ADJ>
 __global__ void __launch_bounds__(128, ADJ ? 3 : 4) k_peel(const Params* __restrict__ G) {
     const Params& P = *G;
     const unsigned lane = threadIdx.x & 31u;
-    const unsigned long long cnt = *P.peel_count;
-    const unsigned long long n = cnt < P.peel_cap ? cnt : P.peel_cap;
+    const unsigned long long n = *P.peel_nlive;   // the rays the prep pass listed
     const float tstop = tau_stop_f(P.tau_stop);
     // ADJ: the adjoint's launch (P.adj_grad set): each contributing ray is
     // walked a second time for its gradient
@@ -1072,16 +1090,13 @@ __global__ void __launch_bounds__(128, ADJ ? 3 : 4) k_peel(const Params* __restr
             if ((int)lane == leader) base = atomicAdd(P.peel_head, (unsigned long long)__popc(m));
             base = __shfl_sync(kFull, base, leader);
             if (want) {
-                i = base + __popc(m & ((1u << lane) - 1u));
-                if (i < n) {
-                    if (P.peel_prep[i].dark) {
-                        cells += 1;   // ends in its first leaf beyond tau_stop: nothing to walk or tally
-                    } else {
-                        ray_from_prep<NL>(P, i, r);
-                        phase = 0;
-                        steps = 0;
-                        active = true;
-                    }
+                const unsigned long long j = base + __popc(m & ((1u << lane) - 1u));
+                if (j < n) {
+                    i = P.peel_live[j];
+                    ray_from_prep<NL>(P, i, r);
+                    phase = 0;
+                    steps = 0;
+                    active = true;
                 } else {
                     drained = true;
                 }
