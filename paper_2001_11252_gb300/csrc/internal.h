@@ -92,7 +92,7 @@ struct alignas(16) PeelPrep {
     int ch;                  // spectrum channel, -1 outside the frequency range (or dark)
     int dir;                 // observer direction
     float wt;                // weight per sr
-    int dark;                // 1: the walk ends in the first leaf with tau beyond tau_stop (not listed)
+    int dark;                // 0 in every record written: a ray that ends dark in its first leaf gets none (and is not listed)
     long long px;            // image pixel, -1 outside the image (or dark)
 };
 static_assert(sizeof(PeelPrep) == 64, "PeelPrep is one 64-byte record");
